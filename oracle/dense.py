@@ -1,0 +1,162 @@
+"""The plain definition of the multitask GP quantities: dense Gram matrix and dense Cholesky.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Everything follows Sec. 3.1 of the paper directly, with no structure exploited:
+  * Gram matrix  K~_{tt'} = R_{tt'} Q(X_t, X_t') + delta_{tt'} xi I  (Eq. 3.1 and the text after Eq. 3.2),
+    a single noise xi = sigma2 for all tasks, gamma = 1.
+  * optimal means  (E K~^-1 E^T) tau = E K~^-1 y                        (Eq. 3.4, MLE)
+  * loss           L = (y - E^T tau)^T K~^-1 (y - E^T tau) + log|K~|    (Eq. 3.3, MLE)
+  * NLL            = (L + N log 2 pi) / 2
+  * gradient       dL/dtheta = tr(K~^-1 dK~) - a^T dK~ a, a = K~^-1 r, at tau fixed (tau minimises L)
+  * posterior      mean_t(x) = tau_t + k(t,x)^T K~^-1 r,  var_t(x) = K((t,x),(t,x)) - k^T K~^-1 k  (Eq. 3.2)
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+from .design import design_points, product_kernel, task_covariance, kernel_1d
+
+
+def all_points(kind, gen, shift, m):
+    """Design points of every task (Cond. 3.1: common generator, per-task shift)."""
+    return [design_points(kind, gen, shift[t], 1 << int(m[t])) for t in range(len(m))]
+
+
+def gram(kind, X_tasks, eta, R, sigma2):
+    """Dense K~ (N x N), tasks in the given order, each in radical-inverse order."""
+    T = len(X_tasks)
+    n = [len(X) for X in X_tasks]
+    off = np.concatenate([[0], np.cumsum(n)])
+    K = np.empty((off[-1], off[-1]))
+    for t in range(T):
+        for u in range(T):
+            Q = product_kernel(kind, X_tasks[t][:, None, :], X_tasks[u][None, :, :], eta)
+            K[off[t]:off[t + 1], off[u]:off[u + 1]] = R[t, u] * Q
+    K[np.diag_indices_from(K)] += sigma2
+    return K
+
+
+def summing_matrix(n):
+    """E in R^{T x N}: row t has ones on task t's block (text after Eq. 3.2)."""
+    T = len(n)
+    E = np.zeros((T, sum(n)))
+    off = 0
+    for t in range(T):
+        E[t, off:off + n[t]] = 1.0
+        off += n[t]
+    return E
+
+
+def nll(kind, X_tasks, y, eta, W, v, sigma2):
+    """Returns dict with L (Eq. 3.3), nll, quad, logdet, tau (Eq. 3.4) by dense Cholesky."""
+    R = task_covariance(W, v)
+    K = gram(kind, X_tasks, eta, R, sigma2)
+    n = [len(X) for X in X_tasks]
+    N = sum(n)
+    E = summing_matrix(n)
+    cf = sla.cho_factor(K, lower=True)
+    Kinv_Et = sla.cho_solve(cf, E.T)
+    Kinv_y = sla.cho_solve(cf, y)
+    Pi = E @ Kinv_Et
+    tau = np.linalg.solve(Pi, E @ Kinv_y)
+    r = y - E.T @ tau
+    a = sla.cho_solve(cf, r)
+    quad = float(r @ a)
+    logdet = float(2.0 * np.sum(np.log(np.diag(cf[0]))))
+    L = quad + logdet
+    return dict(L=L, nll=0.5 * (L + N * np.log(2 * np.pi)), quad=quad, logdet=logdet,
+                tau=tau, alpha=a, Pi=Pi)
+
+
+def nll_grad(kind, X_tasks, y, eta, W, v, sigma2):
+    """Analytic gradient of L (Eq. 3.3) w.r.t. eta (d), W (T x s), v (T), sigma2, at the optimal tau.
+
+    dL/dtheta = tr(K~^-1 dK~/dtheta) - a^T (dK~/dtheta) a, each dK~ written out densely:
+      dK~/d eta_j   = R_{tt'} K(x_j, x'_j) prod_{l != j} (1 + eta_l K(x_l, x'_l))
+      dK~/d W_{ts}  = (dR/dW_{ts})_{tt'} Q,   dR/dW_{ts} = e_t W_{:,s}^T + W_{:,s} e_t^T
+      dK~/d v_t     = (e_t e_t^T)_{tt'} Q
+      dK~/d sigma2  = I
+    Returns (out_dict_of_nll, g_eta, g_W, g_v, g_sigma2) for L (the NLL gradient is half of it).
+    """
+    out = nll(kind, X_tasks, y, eta, W, v, sigma2)
+    R = task_covariance(W, v)
+    K = gram(kind, X_tasks, eta, R, sigma2)
+    Kinv = np.linalg.inv(K)
+    Kinv = 0.5 * (Kinv + Kinv.T)
+    a = out["alpha"]
+    T = len(X_tasks)
+    n = [len(X) for X in X_tasks]
+    off = np.concatenate([[0], np.cumsum(n)])
+    d = len(eta)
+
+    def contract(dK):
+        return float(np.sum(Kinv * dK) - a @ dK @ a)
+
+    # univariate kernel blocks per dimension
+    K1 = [[None] * T for _ in range(T)]
+    for t in range(T):
+        for u in range(T):
+            K1[t][u] = [kernel_1d(kind, X_tasks[t][:, None, j], X_tasks[u][None, :, j]) for j in range(d)]
+    g_eta = np.zeros(d)
+    for j in range(d):
+        dK = np.zeros_like(K)
+        for t in range(T):
+            for u in range(T):
+                blk = K1[t][u][j].copy()
+                for l in range(d):
+                    if l != j:
+                        blk = blk * (1.0 + eta[l] * K1[t][u][l])
+                dK[off[t]:off[t + 1], off[u]:off[u + 1]] = R[t, u] * blk
+        g_eta[j] = contract(dK)
+    Qfull = gram(kind, X_tasks, eta, np.ones((T, T)), 0.0)
+
+    def blockwise(dR):
+        dK = np.empty_like(K)
+        for t in range(T):
+            for u in range(T):
+                dK[off[t]:off[t + 1], off[u]:off[u + 1]] = dR[t, u] * Qfull[off[t]:off[t + 1], off[u]:off[u + 1]]
+        return dK
+
+    s = W.shape[1]
+    g_W = np.zeros_like(W)
+    for t in range(T):
+        for k in range(s):
+            e = np.zeros(T)
+            e[t] = 1.0
+            dR = np.outer(e, W[:, k]) + np.outer(W[:, k], e)
+            g_W[t, k] = contract(blockwise(dR))
+    g_v = np.zeros(T)
+    for t in range(T):
+        dR = np.zeros((T, T))
+        dR[t, t] = 1.0
+        g_v[t] = contract(blockwise(dR))
+    g_s2 = contract(np.eye(K.shape[0]))
+    return out, g_eta, g_W, g_v, g_s2
+
+
+def posterior(kind, X_tasks, y, eta, W, v, sigma2, Xq, task_q):
+    """Posterior mean and variance of f(t, x) at fixed-point queries Xq (nq x d), Eq. 3.2.
+
+    tau is the MLE optimal mean (Eq. 3.4), plugged in as the prior mean.
+    """
+    out = nll(kind, X_tasks, y, eta, W, v, sigma2)
+    R = task_covariance(W, v)
+    K = gram(kind, X_tasks, eta, R, sigma2)
+    cf = sla.cho_factor(K, lower=True)
+    T = len(X_tasks)
+    nq = Xq.shape[0]
+    kq = np.empty((nq, K.shape[0]))
+    off = 0
+    Qs = []
+    for u in range(T):
+        Qs.append(product_kernel(kind, Xq[:, None, :], X_tasks[u][None, :, :], eta))
+    for i in range(nq):
+        row = np.concatenate([R[task_q[i], u] * Qs[u][i] for u in range(T)])
+        kq[i] = row
+    mean = out["tau"][task_q] + kq @ out["alpha"]
+    Kinv_kq = sla.cho_solve(cf, kq.T)
+    prior = np.array([R[task_q[i], task_q[i]] * product_kernel(kind, Xq[i], Xq[i], eta) for i in range(nq)])
+    var = prior - np.einsum("ij,ji->i", kq, Kinv_kq)
+    return mean, var, prior
