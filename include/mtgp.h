@@ -1,0 +1,144 @@
+/*
+ * mtgp.h -- C ABI of the GB300 fast multitask Gaussian process library.
+ *
+ * The library evaluates, on one GPU, the exact MLE loss of a multitask GP whose Gram
+ * matrix has the fast-MTGP structure of Sorokin, Robbe, Liu, Mak, Hickernell,
+ * "Fast multitask Gaussian processes" (arXiv 2603.16014):
+ *
+ *   K((t,x),(t',x')) = R(t,t') Q(x,x')                                   (Eq. 3.1)
+ *   R = W W^T + diag(v)                        (Sec. 3.1, the paper's B B^T + diag(zeta))
+ *   Q(x,x') = prod_j (1 + eta_j K(x_j, x'_j))                            (Eq. 2.4, gamma = 1)
+ *   K~ = K + sigma2 I                         (Sec. 3.1, one noise variance for all tasks)
+ *   designs: shifted rank-1 lattices with the SI Bernoulli kernel of order 2 (Eq. 2.5)
+ *            or digitally shifted base-2 digital nets with the DSI order-2 kernel (Eq. 2.6),
+ *            common generator, per-task shifts, n_t = 2^{m_t}          (Condition 3.1)
+ *
+ * Conventions shared by every call
+ *   - Return value: MTGP_OK or an MTGP_ERR_* code.  Argument errors are detected on the
+ *     host and returned immediately; numerical errors found by a kernel (a non-positive
+ *     pivot, a non-finite value) are recorded in a device status word that mtgp_sync()
+ *     returns.  mtgp_last_error_string() describes the last host-side error of the calling
+ *     thread.
+ *   - Every array argument is a DEVICE pointer owned by the caller unless stated otherwise;
+ *     the library never frees caller memory.  Host arrays are marked "host".
+ *   - Calls are asynchronous on the given stream.  A handle must not be used from two
+ *     streams at once (it owns one workspace).
+ *   - Task order: arrays indexed by task use the caller's task order.  Internally tasks
+ *     are reordered so that n_1 >= ... >= n_T (Condition 3.1: "may always be satisfied by
+ *     reindexing"), ties keeping the caller's order.
+ *   - Points are 32-bit fixed point: coordinate value = word / 2^32.
+ */
+#ifndef MTGP_H
+#define MTGP_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mtgp_s mtgp_t;
+
+enum {
+    MTGP_OK = 0,
+    MTGP_ERR_INVALID_ARG = 1,  /* bad size, null pointer, out-of-range flag               */
+    MTGP_ERR_NOT_PD = 2,       /* a pivot / Schur complement <= 0 (Lambda not HPD numerically) */
+    MTGP_ERR_NUMERIC = 3,      /* NaN or Inf in an input or an intermediate                */
+    MTGP_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up                       */
+    MTGP_ERR_UNSUPPORTED = 5,  /* valid request outside what this build implements         */
+    MTGP_ERR_CUDA = 6,         /* a CUDA runtime call failed                               */
+    MTGP_ERR_STATE = 7         /* call order violated (e.g. NLL before mtgp_set_y)         */
+};
+
+enum { MTGP_LATTICE = 0, MTGP_DNET = 1 };
+enum { MTGP_FP64 = 0, MTGP_FP32_TRANSFORM = 1 };
+
+/* Limits of this build. */
+#define MTGP_MAX_TASKS 8
+#define MTGP_MAX_M 24      /* n_t <= 2^24 */
+#define MTGP_MAX_DIM 32
+
+/*
+ * mtgp_create -- build a handle for one fit (Condition 3.1).
+ *   kind      MTGP_LATTICE (Def. 2.1, SI kernel Eq. 2.5 with alpha = 2) or
+ *             MTGP_DNET (Def. 2.2, DSI kernel Eq. 2.6 with b = (0, 1, 0, 0)).
+ *   d         dimension, 1..MTGP_MAX_DIM.
+ *   T         number of tasks, 1..MTGP_MAX_TASKS.
+ *   m         host, T ints: n_t = 2^{m[t]}, 0 <= m[t] <= MTGP_MAX_M, any order.
+ *   gen       host.  LATTICE: d generating-vector words g_j (z_i = v(i) g mod 1 computed as
+ *             bitrev32(i) * g_j mod 2^32).  DNET: d x gen_cols words, row-major by coordinate:
+ *             gen[j * gen_cols + p] is column g_p of coordinate j (bit 31 = digit 2^-1).
+ *   gen_cols  DNET: number of generating-matrix columns, >= max m[t], <= 32. Ignored for LATTICE.
+ *   shift     host, T x d words (caller task order): lattice shift Delta_t (added mod 2^32) or
+ *             digital shift (XOR).
+ *   precision MTGP_FP64, or MTGP_FP32_TRANSFORM (kernel columns and their transforms in FP32;
+ *             per-frequency factorisations, log-determinants and y transforms stay FP64).
+ * Allocates the handle's device workspace on the current device.
+ */
+int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32_t* gen,
+                int gen_cols, const uint32_t* shift, int precision);
+
+/* mtgp_destroy -- free the handle and its workspace (synchronises the device first). */
+int mtgp_destroy(mtgp_t* h);
+
+/*
+ * mtgp_points -- write the design points x_{t,i} (Def. 2.1 / Def. 2.2, radical-inverse order)
+ * as fixed-point words: x[(N_{t-1} + i) * d + j], tasks in caller order, N_{t-1} = n_1+..+n_{t-1}.
+ */
+int mtgp_points(mtgp_t* h, uint32_t* x, cudaStream_t stream);
+
+/*
+ * mtgp_set_y -- observations y (N doubles, tasks in caller order, each task in radical-inverse
+ * order).  Computes yhat_t = V_{m_t}^dagger y_t (Theorem "fast MTGP computations") once; the
+ * data are theta-independent.  Must precede every NLL / gradient / posterior call.
+ */
+int mtgp_set_y(mtgp_t* h, const double* y, cudaStream_t stream);
+
+/*
+ * mtgp_nll -- MLE loss at theta (Eq. 3.3) with tau profiled at its optimum (Eq. 3.4,
+ * Theorem "fast MTGP computations" item 4).
+ *   eta     d doubles (eta_j >= 0), W T x s doubles row-major (caller task order), 1 <= s <= T,
+ *   v       T doubles > 0, sigma2 one double > 0 -- all device pointers.
+ *   out     3 doubles: [0] NLL = (L + N log 2 pi) / 2, [1] quad = r^T K~^-1 r, [2] log|K~|.
+ *   tau     T doubles (caller order) or NULL: the optimal means.
+ */
+int mtgp_nll(mtgp_t* h, const double* eta, const double* W, int s, const double* v,
+             const double* sigma2, double* out, double* tau, cudaStream_t stream);
+
+/*
+ * mtgp_nll_grad -- as mtgp_nll plus the gradient of the NLL (= half the gradient of L) with
+ * respect to eta (d), W (T x s), v (T) and sigma2 (1), at the optimal tau (tau minimises L, so
+ * its own dependence on theta does not enter).  Gradient outputs may not be NULL.
+ */
+int mtgp_nll_grad(mtgp_t* h, const double* eta, const double* W, int s, const double* v,
+                  const double* sigma2, double* out, double* tau, double* g_eta, double* g_W,
+                  double* g_v, double* g_sigma2, cudaStream_t stream);
+
+/*
+ * mtgp_posterior -- posterior mean and variance of f(t, x) (Eq. 3.2) at nq queries, with the
+ * prior mean tau at its MLE optimum.
+ *   xq     nq x d doubles in [0, 1] (row-major); each is mapped to the fixed-point word
+ *          floor(x 2^32), 1.0 mapping to the largest word below 1 (Sec. 2.2.1 boundary rule).
+ *   task   nq ints, caller task index of each query.
+ *   mean   nq doubles (required); var nq doubles or NULL (NULL skips the variance).
+ * Variance needs equal task sizes in this build (MTGP_ERR_UNSUPPORTED otherwise).
+ */
+int mtgp_posterior(mtgp_t* h, const double* eta, const double* W, int s, const double* v,
+                   const double* sigma2, int nq, const double* xq, const int* task,
+                   double* mean, double* var, cudaStream_t stream);
+
+/* mtgp_sync -- wait for the stream, return the first error recorded on the device since the
+ * last mtgp_sync (MTGP_OK if none) and clear it. */
+int mtgp_sync(mtgp_t* h, cudaStream_t stream);
+
+/* mtgp_last_error_string -- description of the calling thread's last host-side error. */
+const char* mtgp_last_error_string(void);
+
+/* mtgp_workspace_bytes -- device bytes the handle holds (for capacity planning). */
+long long mtgp_workspace_bytes(const mtgp_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MTGP_H */

@@ -348,3 +348,65 @@ def posterior_by_class(kind, gen, shift, m, y, eta, W, v, sigma2, Xq, task_q):
         prior = R[ts, ts] * float(product_kernel(kind, Xq[qi], Xq[qi], eta))
         var[qi] = prior - acc
     return mean, var
+
+
+def nll_grad_equal(kind, gen, shift, m, y, eta, W, v, sigma2):
+    """Equal sizes: L (Eq. 3.3) and its gradient by per-frequency traces, dL/dtheta = sum_f tr(G(f) dLambda(f)),
+    G(f) = Lambda(f)^-1 - alpha(f) alpha(f)^H, every dLambda(f)/dtheta formed explicitly:
+      dLambda/d eta_j = R o dM_j(f)  (dM_j = transforms of the columns' eta_j derivatives),
+      dLambda/d W_ts  = (e_t W_s^T + W_s e_t^T) o M(f),  dLambda/d v_t = e_t e_t^T o M(f),  dLambda/d sigma2 = I.
+    Returns (out, g_eta, g_W, g_v, g_sigma2) for L (the NLL gradient is half of it)."""
+    from .design import kernel_1d
+    T = len(m)
+    mm = int(m[0])
+    n = 1 << mm
+    X = [design_points(kind, gen, shift[t], n) for t in range(T)]
+    R = task_covariance(W, v)
+    d = len(eta)
+    M = np.zeros((n, T, T), dtype=np.complex128)
+    dM = np.zeros((d, n, T, T), dtype=np.complex128)
+    for t in range(T):
+        for u in range(t, T):
+            K1 = [kernel_1d(kind, X[t][:, j], np.full(n, X[u][0, j], dtype=np.uint64)) for j in range(d)]
+            fac = [1.0 + eta[j] * K1[j] for j in range(d)]
+            col = np.prod(fac, axis=0)
+            mu = np.sqrt(n) * vdag(kind, col.astype(np.complex128), mm)
+            M[:, t, u] = mu
+            M[:, u, t] = np.conj(mu)
+            for j in range(d):
+                dcol = K1[j] * np.prod([fac[l] for l in range(d) if l != j], axis=0) if d > 1 else K1[j]
+                dmu = np.sqrt(n) * vdag(kind, dcol.astype(np.complex128), mm)
+                dM[j, :, t, u] = dmu
+                dM[j, :, u, t] = np.conj(dmu)
+    for t in range(T):
+        M[:, t, t] = M[:, t, t].real
+        dM[:, :, t, t] = dM[:, :, t, t].real
+    Lam = R[None, :, :] * M + sigma2 * np.eye(T)[None, :, :]
+    ys = np.asarray(y, dtype=np.float64).reshape(T, n)
+    rhat = vdag(kind, ys.astype(np.complex128), mm).T.copy()     # (n, T)
+    tau = rhat[0].real / np.sqrt(n)
+    rhat[0] = 0.0
+    Lc = np.linalg.cholesky(Lam)
+    logdet = 2.0 * float(np.sum(np.log(np.real(np.diagonal(Lc, axis1=1, axis2=2)))))
+    Z = np.linalg.inv(Lam)
+    a = np.einsum("fab,fb->fa", Z, rhat)
+    quad = float(np.einsum("fa,fa->", np.conj(rhat), a).real)
+    G = Z - a[:, :, None] * np.conj(a[:, None, :])
+
+    def tr(dLam):
+        return float(np.einsum("fba,fab->", G, dLam).real)
+
+    g_eta = np.array([tr(R[None] * dM[j]) for j in range(d)])
+    s = W.shape[1]
+    g_W = np.zeros_like(W)
+    for t in range(T):
+        for k in range(s):
+            e = np.zeros(T)
+            e[t] = 1.0
+            dR = np.outer(e, W[:, k]) + np.outer(W[:, k], e)
+            g_W[t, k] = tr(dR[None] * M)
+    g_v = np.array([tr(np.diag(np.eye(T)[t])[None] * M) for t in range(T)])
+    g_s2 = float(np.einsum("faa->", G).real)
+    N = T * n
+    out = dict(L=quad + logdet, nll=0.5 * (quad + logdet + N * np.log(2 * np.pi)), quad=quad, logdet=logdet, tau=tau)
+    return out, g_eta, g_W, g_v, g_s2

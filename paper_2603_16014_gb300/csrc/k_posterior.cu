@@ -1,0 +1,432 @@
+// Posterior mean and variance of f(t, x) (Eq. 3.2) with the optimal mean tau plugged in.
+//
+//   mean_t(x) = tau_t + sum_u R_{tu} sum_i Q(x, x_{u,i}) beta_u[i],   beta = K~^-1 r = V Lambda^-1 rhat,
+//   var_t(x)  = R_tt Q(x, x) - kappa^H Lambda^-1 kappa,             kappa_u = R_{tu} V_{m_u}^dagger q_u(x),
+// with q_u(x)[i] = Q(x, x_{u,i}).  alpha = Lambda^-1 rhat comes from the solve; beta_t = V_{m_t} alpha_t
+// is the inverse transform (V = conj o DIF o conj / sqrt(n) for lattices, FWHT / sqrt(n) for nets).
+#include <type_traits>
+
+#include "mtgp_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTile = 256;
+
+__global__ void k_query_words(const double* __restrict__ xq, long long total, uint32_t* __restrict__ out,
+                              int* status) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        double x = xq[e];
+        uint32_t w;
+        if (!(x == x)) {
+            set_status(status, ST_NUMERIC);
+            w = 0;
+        } else if (x >= 1.0) {
+            w = 0xFFFFFFFFu;  // points equal to 1 map to the largest value below 1
+        } else if (x <= 0.0) {
+            w = 0u;
+        } else {
+            w = (uint32_t)floor(x * 4294967296.0);
+        }
+        out[e] = w;
+    }
+}
+
+// sorted design points, N x d words
+__global__ void k_design_words(uint32_t* __restrict__ out, int kind, int d, const uint32_t* __restrict__ gen,
+                               int gen_cols, const uint32_t* __restrict__ shift, int t, long long n, long long off) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * d;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long i = e / d;
+        int j = (int)(e - i * d);
+        uint32_t z = point_word(kind, (uint32_t)i, j, gen, gen_cols);
+        uint32_t dt = shift[t * d + j];
+        out[(off + i) * d + j] = (kind == MTGP_LATTICE) ? z + dt : z ^ dt;
+    }
+}
+
+// beta buffer <- alpha (conjugated for lattices, so the DIF transform yields conj(V alpha) * sqrt(n))
+__global__ void k_beta_prep(const double* __restrict__ alpha, double* __restrict__ beta, long long N, int cplx) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        if (cplx) {
+            beta[2 * i] = alpha[2 * i];
+            beta[2 * i + 1] = -alpha[2 * i + 1];
+        } else {
+            beta[i] = alpha[i];
+        }
+    }
+}
+
+// beta_real[i] = Re(beta_buf[i]) / sqrt(n_t)
+__global__ void k_beta_finish(const double* __restrict__ beta, double* __restrict__ breal, long long n, long long off,
+                              int cplx, double scale) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double v = cplx ? beta[2 * (off + i)] : beta[off + i];
+        breal[off + i] = v * scale;
+    }
+}
+
+struct PostParams {
+    int kind, d, T;
+    long long n[MTGP_TMAX];
+    long long yoff[MTGP_TMAX];
+    int order[MTGP_TMAX];
+    int rank[MTGP_TMAX];
+};
+
+template <typename S>
+__device__ __forceinline__ S qkernel(int kind, const uint32_t* xa, const uint32_t* xb, const S* eta, int d) {
+    S q = (S)1;
+    for (int j = 0; j < d; ++j) {
+        uint32_t X = (kind == MTGP_LATTICE) ? (xa[j] - xb[j]) : (xa[j] ^ xb[j]);
+        q *= (S)1 + eta[j] * kernel1d<S>(kind, X);
+    }
+    return q;
+}
+
+__device__ void load_R_post(double* sR, const PostParams& p, const ThetaPtrs& th) {
+    for (int e = threadIdx.x; e < p.T * p.T; e += blockDim.x) {
+        int t = e / p.T, u = e % p.T;
+        int tc = p.order[t], uc = p.order[u];
+        double r = 0.0;
+        for (int k = 0; k < th.s; ++k) r += th.W[tc * th.s + k] * th.W[uc * th.s + k];
+        if (t == u) r += th.v[tc];
+        sR[e] = r;
+    }
+}
+
+// one thread per query; design points and beta streamed through shared-memory tiles
+__global__ void __launch_bounds__(kThreads)
+k_post_mean(const uint32_t* __restrict__ xqw, const int* __restrict__ task, int nq, const uint32_t* __restrict__ dw,
+            const double* __restrict__ beta, const double* __restrict__ tau_sorted, PostParams p, ThetaPtrs th,
+            double* __restrict__ mean) {
+    __shared__ double sR[MTGP_TMAX * MTGP_TMAX];
+    __shared__ double s_eta[MTGP_MAX_DIM];
+    __shared__ uint32_t s_x[kTile * MTGP_MAX_DIM];
+    __shared__ double s_b[kTile];
+    load_R_post(sR, p, th);
+    if (threadIdx.x < p.d) s_eta[threadIdx.x] = th.eta[threadIdx.x];
+    const int d = p.d;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = q < nq;
+    uint32_t xq[MTGP_MAX_DIM];
+    int tq = 0;
+    if (act) {
+        for (int j = 0; j < d; ++j) xq[j] = xqw[(long long)q * d + j];
+        tq = p.rank[task[q]];
+    }
+    __syncthreads();
+    double m = 0.0;
+    for (int u = 0; u < p.T; ++u) {
+        double acc = 0.0;
+        for (long long i0 = 0; i0 < p.n[u]; i0 += kTile) {
+            int cnt = (int)((p.n[u] - i0) < kTile ? (p.n[u] - i0) : kTile);
+            __syncthreads();
+            for (int e = threadIdx.x; e < cnt * d; e += blockDim.x) s_x[e] = dw[(p.yoff[u] + i0) * d + e];
+            for (int e = threadIdx.x; e < cnt; e += blockDim.x) s_b[e] = beta[p.yoff[u] + i0 + e];
+            __syncthreads();
+            if (act) {
+                for (int i = 0; i < cnt; ++i) acc += qkernel<double>(p.kind, xq, s_x + i * d, s_eta, d) * s_b[i];
+            }
+        }
+        m += sR[tq * p.T + u] * acc;
+    }
+    if (act) mean[q] = tau_sorted[tq] + m;
+}
+
+// rows of the variance batch: qrow[(b * T + u) * n + i] = R_{t_b u} Q(x_b, x_{u,i})  (equal sizes)
+template <bool CPLX>
+__global__ void k_var_rows(const uint32_t* __restrict__ xqw, const int* __restrict__ task, int q0, int B,
+                           const uint32_t* __restrict__ dw, PostParams p, ThetaPtrs th, double* __restrict__ rows) {
+    __shared__ double sR[MTGP_TMAX * MTGP_TMAX];
+    __shared__ double s_eta[MTGP_MAX_DIM];
+    load_R_post(sR, p, th);
+    if (threadIdx.x < p.d) s_eta[threadIdx.x] = th.eta[threadIdx.x];
+    __syncthreads();
+    const long long n = p.n[0];
+    const long long total = (long long)B * p.T * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long i = e % n;
+        long long bu = e / n;
+        int u = (int)(bu % p.T);
+        int b = (int)(bu / p.T);
+        int q = q0 + b;
+        int tq = p.rank[task[q]];
+        double v = sR[tq * p.T + u] * qkernel<double>(p.kind, xqw + (long long)q * p.d, dw + (p.yoff[u] + i) * p.d, s_eta, p.d);
+        if (CPLX) {
+            rows[2 * e] = v;
+            rows[2 * e + 1] = 0.0;
+        } else {
+            rows[e] = v;
+        }
+    }
+}
+
+template <bool CPLX>
+using Vt = typename std::conditional<CPLX, cx<double>, double>::type;
+
+__device__ __forceinline__ double vmul(double a, double b) { return a * b; }
+__device__ __forceinline__ cx<double> vmul(cx<double> a, cx<double> b) { return a * b; }
+__device__ __forceinline__ double vscale(double a, double s) { return a * s; }
+__device__ __forceinline__ cx<double> vscale(cx<double> a, double s) { return mk(a.re * s, a.im * s); }
+__device__ __forceinline__ double vsub(double a, double b) { return a - b; }
+__device__ __forceinline__ cx<double> vsub(cx<double> a, cx<double> b) { return a - b; }
+
+template <typename S, bool CPLX>
+__device__ __forceinline__ Vt<CPLX> load_spec(const void* ptr, long long i) {
+    if constexpr (CPLX) {
+        cx<S> v = reinterpret_cast<const cx<S>*>(ptr)[i];
+        return mk((double)v.re, (double)v.im);
+    } else {
+        return (double)reinterpret_cast<const S*>(ptr)[i];
+    }
+}
+
+struct VarParams {
+    int T, clamp;
+    long long n;
+    int colidx[MTGP_TMAX][MTGP_TMAX];
+    long long coloff[MTGP_MAX_COLS];
+};
+
+// one CTA per query: sum_f kappa(f)^H Lambda(f)^-1 kappa(f) with kappa(f) = transformed rows / sqrt(n)
+template <int T, bool CPLX, typename S>
+__global__ void __launch_bounds__(kThreads)
+k_var_quad(const double* __restrict__ rows, const void* spec, const int* __restrict__ task, int q0,
+           const uint32_t* __restrict__ xqw, PostParams pp, VarParams p, ThetaPtrs th, double* __restrict__ var) {
+    using V = Vt<CPLX>;
+    __shared__ double sR[T * T];
+    __shared__ double s_sig;
+    __shared__ double s_eta[MTGP_MAX_DIM];
+    __shared__ double s_red[kThreads / 32];
+    load_R_post(sR, pp, th);
+    if (threadIdx.x == 0) s_sig = th.sigma2[0];
+    if (threadIdx.x < pp.d) s_eta[threadIdx.x] = th.eta[threadIdx.x];
+    __syncthreads();
+    const int b = blockIdx.x;
+    const long long n = p.n;
+    const double inv_sqrt_n = 1.0 / sqrt((double)n);
+    double acc = 0.0;
+    for (long long f = threadIdx.x; f < n; f += blockDim.x) {
+        V mu[T][T];
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+#pragma unroll
+            for (int u = t; u < T; ++u) mu[t][u] = load_spec<S, CPLX>(spec, p.coloff[p.colidx[t][u]] + f);
+        double mu0 = creal(mu[0][0]);
+        if (p.clamp && mu0 < 0.0) mu0 = 0.0;
+        V lam[T][T];
+#pragma unroll
+        for (int i = 0; i < T; ++i) {
+            lam[i][i] = cfromreal<V>(sR[i * T + i] * mu0 + s_sig);
+#pragma unroll
+            for (int j = 0; j < i; ++j) lam[i][j] = vscale(cconj(mu[j][i]), sR[j * T + i]);
+        }
+        double D[T];
+        V L[T][T];
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+            double dk = creal(lam[k][k]);
+#pragma unroll
+            for (int j = 0; j < k; ++j) dk -= cabs2(L[k][j]) * D[j];
+            D[k] = dk;
+#pragma unroll
+            for (int i = k + 1; i < T; ++i) {
+                V a = lam[i][k];
+#pragma unroll
+                for (int j = 0; j < k; ++j) a = vsub(a, vscale(vmul(L[i][j], cconj(L[k][j])), D[j]));
+                L[i][k] = vscale(a, 1.0 / dk);
+            }
+        }
+        V w[T];
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+            long long e = ((long long)b * T + k) * n + f;
+            V r;
+            if constexpr (CPLX) r = mk(rows[2 * e] * inv_sqrt_n, rows[2 * e + 1] * inv_sqrt_n);
+            else r = rows[e] * inv_sqrt_n;
+#pragma unroll
+            for (int j = 0; j < k; ++j) r = vsub(r, vmul(L[k][j], w[j]));
+            w[k] = r;
+            acc += cabs2(r) / D[k];
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) s_red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w2 = 0; w2 < kThreads / 32; ++w2) s += s_red[w2];
+        int q = q0 + b;
+        int tq = pp.rank[task[q]];
+        const uint32_t* x = xqw + (long long)q * pp.d;
+        double prior = sR[tq * T + tq] * qkernel<double>(pp.kind, x, x, s_eta, pp.d);
+        var[q] = prior - s;
+    }
+}
+
+template <int T, bool CPLX, typename S>
+void run_var_quad(int B, const double* rows, const void* spec, const int* task, int q0, const uint32_t* xqw,
+                  PostParams pp, VarParams vp, ThetaPtrs th, double* var, cudaStream_t st) {
+    k_var_quad<T, CPLX, S><<<B, kThreads, 0, st>>>(rows, spec, task, q0, xqw, pp, vp, th, var);
+}
+
+template <bool CPLX, typename S>
+void dispatch_var(int T, int B, const double* rows, const void* spec, const int* task, int q0, const uint32_t* xqw,
+                  PostParams pp, VarParams vp, ThetaPtrs th, double* var, cudaStream_t st) {
+    switch (T) {
+        case 1: run_var_quad<1, CPLX, S>(B, rows, spec, task, q0, xqw, pp, vp, th, var, st); break;
+        case 2: run_var_quad<2, CPLX, S>(B, rows, spec, task, q0, xqw, pp, vp, th, var, st); break;
+        case 3: run_var_quad<3, CPLX, S>(B, rows, spec, task, q0, xqw, pp, vp, th, var, st); break;
+        case 4: run_var_quad<4, CPLX, S>(B, rows, spec, task, q0, xqw, pp, vp, th, var, st); break;
+        case 5: run_var_quad<5, CPLX, S>(B, rows, spec, task, q0, xqw, pp, vp, th, var, st); break;
+        case 6: run_var_quad<6, CPLX, S>(B, rows, spec, task, q0, xqw, pp, vp, th, var, st); break;
+        case 7: run_var_quad<7, CPLX, S>(B, rows, spec, task, q0, xqw, pp, vp, th, var, st); break;
+        default: run_var_quad<8, CPLX, S>(B, rows, spec, task, q0, xqw, pp, vp, th, var, st); break;
+    }
+}
+
+int grid_for(long long work) {
+    long long b = (work + 255) / 256;
+    if (b > 4096) b = 4096;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+// Scratch needed by posterior_run beyond the handle's fixed workspace is carved from `h->S`-sized
+// buffers allocated on first use (see mtgp_api.cu: post_* fields are not part of Handle to keep
+// the header small; they live in a static map keyed by handle).
+#include <map>
+#include <mutex>
+
+namespace {
+struct PostScratch {
+    uint32_t* design = nullptr;  // N x d words (sorted)
+    double* beta_c = nullptr;    // N (complex for lattice)
+    double* beta = nullptr;      // N real
+    uint32_t* xq = nullptr;      // nq x d words
+    long long xq_cap = 0;
+    double* rows = nullptr;      // variance batch rows
+    long long rows_cap = 0;
+    long long* offs = nullptr;   // row offsets of the variance batch (multiples of n)
+    int offs_cap = 0;
+};
+std::map<const Handle*, PostScratch> g_post;
+std::mutex g_post_mu;
+}  // namespace
+
+void posterior_release(const Handle* h) {
+    std::lock_guard<std::mutex> lk(g_post_mu);
+    auto it = g_post.find(h);
+    if (it == g_post.end()) return;
+    cudaFree(it->second.design);
+    cudaFree(it->second.beta_c);
+    cudaFree(it->second.beta);
+    cudaFree(it->second.xq);
+    cudaFree(it->second.rows);
+    cudaFree(it->second.offs);
+    g_post.erase(it);
+}
+
+int posterior_run(Handle* h, ThetaPtrs th, int nq, const double* xq, const int* task, double* mean, double* var,
+                  cudaStream_t st) {
+    PostScratch* ps;
+    {
+        std::lock_guard<std::mutex> lk(g_post_mu);
+        ps = &g_post[h];
+    }
+    const int d = h->d;
+    const long long N = h->N;
+    const int es = h->cplx ? 2 : 1;
+    if (!ps->design) {
+        if (cudaMalloc(&ps->design, (size_t)N * d * sizeof(uint32_t)) != cudaSuccess) return MTGP_ERR_CUDA;
+        if (cudaMalloc(&ps->beta_c, (size_t)N * es * sizeof(double)) != cudaSuccess) return MTGP_ERR_CUDA;
+        if (cudaMalloc(&ps->beta, (size_t)N * sizeof(double)) != cudaSuccess) return MTGP_ERR_CUDA;
+        for (int t = 0; t < h->T; ++t)
+            k_design_words<<<grid_for(h->n[t] * d), 256, 0, st>>>(ps->design, h->kind, d, h->gen, h->gen_cols, h->shift, t,
+                                                                h->n[t], h->yoff[t]);
+    }
+    if ((long long)nq * d > ps->xq_cap) {
+        cudaFree(ps->xq);
+        ps->xq_cap = (long long)nq * d;
+        if (cudaMalloc(&ps->xq, (size_t)ps->xq_cap * sizeof(uint32_t)) != cudaSuccess) return MTGP_ERR_CUDA;
+    }
+    k_query_words<<<grid_for((long long)nq * d), 256, 0, st>>>(xq, (long long)nq * d, ps->xq, h->status);
+    // beta = V alpha
+    k_beta_prep<<<grid_for(N), 256, 0, st>>>(h->alpha, ps->beta_c, N, h->cplx ? 1 : 0);
+    for (int t = 0; t < h->T;) {
+        int t2 = t;
+        while (t2 < h->T && h->m[t2] == h->m[t]) ++t2;
+        launch_transform(h, ps->beta_c, false, h->cplx, h->m[t], h->yoffs_dev + t, t2 - t, true, st);
+        t = t2;
+    }
+    for (int t = 0; t < h->T; ++t)
+        k_beta_finish<<<grid_for(h->n[t]), 256, 0, st>>>(ps->beta_c, ps->beta, h->n[t], h->yoff[t], h->cplx ? 1 : 0,
+                                                       1.0 / sqrt((double)h->n[t]));
+    PostParams pp;
+    pp.kind = h->kind;
+    pp.d = d;
+    pp.T = h->T;
+    for (int t = 0; t < MTGP_TMAX; ++t) {
+        pp.n[t] = t < h->T ? h->n[t] : 0;
+        pp.yoff[t] = t < h->T ? h->yoff[t] : 0;
+        pp.order[t] = t < h->T ? h->order[t] : 0;
+        pp.rank[t] = t < h->T ? h->rank[t] : 0;
+    }
+    // tau (sorted) lives in h->tau (filled by the solver for unequal sizes, by mtgp_set_y for equal)
+    k_post_mean<<<(nq + kThreads - 1) / kThreads, kThreads, 0, st>>>(ps->xq, task, nq, ps->design, ps->beta, h->tau, pp,
+                                                                      th, mean);
+    if (!var) return MTGP_OK;
+    if (!h->equal) return MTGP_ERR_UNSUPPORTED;
+    const long long n = h->n[0];
+    // batch so the rows stay within ~512 MB
+    long long per_q = (long long)h->T * n * es;
+    int B = (int)((64LL << 20) / per_q);
+    if (B < 1) B = 1;
+    if (B > 1024) B = 1024;
+    if (B > nq) B = nq;
+    if ((long long)B * per_q > ps->rows_cap) {
+        cudaFree(ps->rows);
+        ps->rows_cap = (long long)B * per_q;
+        if (cudaMalloc(&ps->rows, (size_t)ps->rows_cap * sizeof(double)) != cudaSuccess) return MTGP_ERR_CUDA;
+    }
+    // offsets of the B*T rows for the batched transform
+    if (B * h->T > ps->offs_cap) {
+        cudaFree(ps->offs);
+        ps->offs_cap = B * h->T;
+        if (cudaMalloc(&ps->offs, (size_t)ps->offs_cap * sizeof(long long)) != cudaSuccess) return MTGP_ERR_CUDA;
+        long long* tmp = new long long[ps->offs_cap];
+        for (int i = 0; i < ps->offs_cap; ++i) tmp[i] = (long long)i * n;
+        cudaMemcpyAsync(ps->offs, tmp, (size_t)ps->offs_cap * sizeof(long long), cudaMemcpyHostToDevice, st);
+        cudaStreamSynchronize(st);
+        delete[] tmp;
+    }
+    long long* offs_dev = ps->offs;
+    VarParams vp;
+    vp.T = h->T;
+    vp.clamp = h->fp32 ? 1 : 0;
+    vp.n = n;
+    for (int t = 0; t < MTGP_TMAX; ++t)
+        for (int u = 0; u < MTGP_TMAX; ++u) vp.colidx[t][u] = (t < h->T && u < h->T && t <= u) ? h->col_of[t][u] : 0;
+    for (int c = 0; c < MTGP_MAX_COLS; ++c) vp.coloff[c] = c < h->ncols ? h->cols[c].off : 0;
+    for (int q0 = 0; q0 < nq; q0 += B) {
+        int Bb = (nq - q0) < B ? (nq - q0) : B;
+        long long work = (long long)Bb * h->T * n;
+        if (h->cplx) k_var_rows<true><<<grid_for(work), 256, 0, st>>>(ps->xq, task, q0, Bb, ps->design, pp, th, ps->rows);
+        else k_var_rows<false><<<grid_for(work), 256, 0, st>>>(ps->xq, task, q0, Bb, ps->design, pp, th, ps->rows);
+        launch_transform(h, ps->rows, false, h->cplx, h->m[0], offs_dev, Bb * h->T, false, st);
+        if (h->fp32) {
+            if (h->cplx) dispatch_var<true, float>(h->T, Bb, ps->rows, h->spec, task, q0, ps->xq, pp, vp, th, var, st);
+            else dispatch_var<false, float>(h->T, Bb, ps->rows, h->spec, task, q0, ps->xq, pp, vp, th, var, st);
+        } else {
+            if (h->cplx) dispatch_var<true, double>(h->T, Bb, ps->rows, h->spec, task, q0, ps->xq, pp, vp, th, var, st);
+            else dispatch_var<false, double>(h->T, Bb, ps->rows, h->spec, task, q0, ps->xq, pp, vp, th, var, st);
+        }
+    }
+    return MTGP_OK;
+}

@@ -1,0 +1,705 @@
+// Per-frequency solves of Lambda-tilde (FP64) and the gradient weights.
+//
+// Equal sizes (Corollary "equal sizes"): Lambda is block diagonal over frequencies f; each block is
+//   Lambda(f) = R o M(f) + sigma2 I,  M(f)_{tu} = mu_{tu}(f) (first-column transforms),
+// factorised as L D L^H per thread.  tau_t is the sample mean, so rhat(0) = 0.
+//
+// Unequal nested sizes (Algorithm 1): entries couple (t, f) and (u, g) only when f = g mod
+// min(n_t, n_u), so each residue class rho mod n_T is independent.  Eliminating tasks in order
+// t = 1..T (the paper's order) makes the Schur complement of every task-t frequency a scalar --
+// Algorithm 1's diagonal S_t.  This file keeps Lambda^-1 in factored form instead of the explicit
+// block inverse A: the pivots are the same S_t (so log|Lambda| = sum_t log|S_t|), the factor has
+// no fill (the class graph is a tree of nested residues) and the entries of Lambda^-1 the gradient
+// needs -- those on Lambda's own sparsity pattern -- come from the selected-inversion recurrence
+// Z = D^-1 L^-1 + (I - L^H) Z restricted to ancestor chains.
+//
+// Gradient (tau held at its optimum): dL = sum over pattern G_{ji} dLambda_{ij},
+//   G = Lambda^-1 - alpha alpha^H, alpha = Lambda^-1 rhat.
+#include <type_traits>
+
+#include "mtgp_internal.cuh"
+
+namespace {
+
+template <bool CPLX>
+using Vt = typename std::conditional<CPLX, cx<double>, double>::type;
+
+__device__ __forceinline__ double vmul(double a, double b) { return a * b; }
+__device__ __forceinline__ cx<double> vmul(cx<double> a, cx<double> b) { return a * b; }
+__device__ __forceinline__ double vscale(double a, double s) { return a * s; }
+__device__ __forceinline__ cx<double> vscale(cx<double> a, double s) { return mk(a.re * s, a.im * s); }
+__device__ __forceinline__ double vadd(double a, double b) { return a + b; }
+__device__ __forceinline__ cx<double> vadd(cx<double> a, cx<double> b) { return a + b; }
+__device__ __forceinline__ double vsub(double a, double b) { return a - b; }
+__device__ __forceinline__ cx<double> vsub(cx<double> a, cx<double> b) { return a - b; }
+
+template <typename S, bool CPLX>
+__device__ __forceinline__ Vt<CPLX> load_spec(const void* p, long long i) {
+    if constexpr (CPLX) {
+        cx<S> v = reinterpret_cast<const cx<S>*>(p)[i];
+        return mk((double)v.re, (double)v.im);
+    } else {
+        return (double)reinterpret_cast<const S*>(p)[i];
+    }
+}
+template <typename S, bool CPLX>
+__device__ __forceinline__ void store_spec(void* p, long long i, Vt<CPLX> v) {
+    if constexpr (CPLX) {
+        reinterpret_cast<cx<S>*>(p)[i] = mk((S)v.re, (S)v.im);
+    } else {
+        reinterpret_cast<S*>(p)[i] = (S)v;
+    }
+}
+template <bool CPLX>
+__device__ __forceinline__ Vt<CPLX> ld(const double* p, long long i) {
+    if constexpr (CPLX) return mk(p[2 * i], p[2 * i + 1]);
+    else return p[i];
+}
+template <bool CPLX>
+__device__ __forceinline__ void st(double* p, long long i, Vt<CPLX> v) {
+    if constexpr (CPLX) {
+        p[2 * i] = v.re;
+        p[2 * i + 1] = v.im;
+    } else {
+        p[i] = v;
+    }
+}
+
+struct SolveParams {
+    int T, s, nT;
+    int grad, clamp, store_alpha;
+    long long n[MTGP_TMAX];
+    int order[MTGP_TMAX];
+    int colidx[MTGP_TMAX][MTGP_TMAX];
+    long long coloff[MTGP_MAX_COLS];
+    long long yoff[MTGP_TMAX];
+};
+
+// R = W W^T + diag(v) in sorted task order
+__device__ void load_R(double* sR, const SolveParams& p, const ThetaPtrs& th) {
+    for (int e = threadIdx.x; e < p.T * p.T; e += blockDim.x) {
+        int t = e / p.T, u = e % p.T;
+        int tc = p.order[t], uc = p.order[u];
+        double r = 0.0;
+        for (int k = 0; k < th.s; ++k) r += th.W[tc * th.s + k] * th.W[uc * th.s + k];
+        if (t == u) r += th.v[tc];
+        sR[e] = r;
+    }
+}
+
+constexpr int kEqThreads = 128;
+
+template <int T, bool CPLX, typename S>
+__global__ void __launch_bounds__(kEqThreads)
+k_solve_equal(const void* spec, void* wgt, const double* yhat, SolveParams p, ThetaPtrs th, double* partials,
+              double* alpha_out, int* status) {
+    using V = Vt<CPLX>;
+    constexpr int NG = T * (T + 1) / 2;
+    constexpr int NQ = 3 + NG;
+    __shared__ double sR[T * T];
+    __shared__ double s_sig;
+    __shared__ double s_red[kEqThreads / 32][NQ];
+    load_R(sR, p, th);
+    if (threadIdx.x == 0) s_sig = th.sigma2[0];
+    __syncthreads();
+    const double sig = s_sig;
+    const long long n = p.n[0];
+    double acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+    int bad = 0;
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < n; f += (long long)gridDim.x * blockDim.x) {
+        V mu[T][T];  // mu[t][u] for t <= u
+        V lam[T][T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+#pragma unroll
+            for (int u = t; u < T; ++u) {
+                int c = p.colidx[t][u];
+                mu[t][u] = load_spec<S, CPLX>(spec, p.coloff[c] + f);
+            }
+        }
+        double mu0 = creal(mu[0][0]);
+        double ind0 = 1.0;
+        if (p.clamp && mu0 < 0.0) {
+            mu0 = 0.0;
+            ind0 = 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < T; ++i) {
+            lam[i][i] = cfromreal<V>(sR[i * T + i] * mu0 + sig);
+#pragma unroll
+            for (int j = 0; j < i; ++j) lam[i][j] = vscale(cconj(mu[j][i]), sR[j * T + i]);
+        }
+        // L D L^H
+        double D[T];
+        V L[T][T];
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+            double dk = creal(lam[k][k]);
+#pragma unroll
+            for (int j = 0; j < k; ++j) dk -= cabs2(L[k][j]) * D[j];
+            if (!(dk > 0.0) || !isfinite(dk)) {
+                bad = 1;
+                dk = 1.0;
+            }
+            D[k] = dk;
+            double inv = 1.0 / dk;
+#pragma unroll
+            for (int i = k + 1; i < T; ++i) {
+                V a = lam[i][k];
+#pragma unroll
+                for (int j = 0; j < k; ++j) a = vsub(a, vscale(vmul(L[i][j], cconj(L[k][j])), D[j]));
+                L[i][k] = vscale(a, inv);
+            }
+        }
+        double prodD = 1.0;
+#pragma unroll
+        for (int k = 0; k < T; ++k) prodD *= D[k];
+        acc[0] += log(prodD);
+        // forward solve with rhat (rhat(0) = 0: tau = sample means)
+        V u[T];
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+            V r = (f == 0) ? czero<V>() : ld<CPLX>(yhat, p.yoff[k] + f);
+#pragma unroll
+            for (int j = 0; j < k; ++j) r = vsub(r, vmul(L[k][j], u[j]));
+            u[k] = r;
+            acc[1] += cabs2(r) / D[k];
+        }
+        if (p.grad || p.store_alpha) {
+            V al[T];
+#pragma unroll
+            for (int k = T - 1; k >= 0; --k) {
+                V a = vscale(u[k], 1.0 / D[k]);
+#pragma unroll
+                for (int i = k + 1; i < T; ++i) a = vsub(a, vmul(cconj(L[i][k]), al[i]));
+                al[k] = a;
+            }
+            if (p.store_alpha) {
+#pragma unroll
+                for (int k = 0; k < T; ++k) st<CPLX>(alpha_out, p.yoff[k] + f, al[k]);
+            }
+            if (p.grad) {
+                // Linv = L^-1 (unit lower), Z = Linv^H D^-1 Linv (lower part), G = Z - alpha alpha^H
+                V Li[T][T];
+#pragma unroll
+                for (int j = 0; j < T; ++j) {
+                    Li[j][j] = cfromreal<V>(1.0);
+#pragma unroll
+                    for (int i = j + 1; i < T; ++i) {
+                        V a = czero<V>();
+#pragma unroll
+                        for (int k = j; k < i; ++k) a = vsub(a, vmul(L[i][k], Li[k][j]));
+                        Li[i][j] = a;
+                    }
+                }
+                double wdiag = 0.0;
+                int q = 3;
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+#pragma unroll
+                    for (int uu = t; uu < T; ++uu) {
+                        // G[uu][t] (uu >= t)
+                        V z = czero<V>();
+#pragma unroll
+                        for (int k = uu; k < T; ++k) z = vadd(z, vscale(vmul(cconj(Li[k][uu]), Li[k][t]), 1.0 / D[k]));
+                        V g = vsub(z, vmul(al[uu], cconj(al[t])));
+                        if (uu == t) {
+                            double gd = creal(g);
+                            acc[2] += gd;
+                            acc[q] += gd * mu0;
+                            wdiag += sR[t * T + t] * gd;
+                        } else {
+                            acc[q] += creal(vmul(g, mu[t][uu]));
+                            store_spec<S, CPLX>(wgt, p.coloff[p.colidx[t][uu]] + f, vscale(g, 2.0 * sR[t * T + uu]));
+                        }
+                        ++q;
+                    }
+                }
+                store_spec<S, CPLX>(wgt, p.coloff[0] + f, cfromreal<V>(wdiag * ind0));
+            }
+        }
+    }
+    if (bad) set_status(status, ST_NOT_PD);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        double v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) s_red[warp][q] = v;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
+        double v = 0.0;
+        for (int w = 0; w < kEqThreads / 32; ++w) v += s_red[w][q];
+        partials[(long long)blockIdx.x * NQ + q] = v;
+    }
+}
+
+
+// --------------------------------------------------------------------------- tree solver
+
+constexpr int kTreeThreads = 256;
+constexpr int kTreeWarps = kTreeThreads / 32;
+
+struct TreeParams {
+    int T, s, grad, clamp;
+    long long nT;
+    long long n[MTGP_TMAX];
+    long long po[MTGP_TMAX][MTGP_TMAX];  // pair (t <= u) element offset in spec / wgt / S / Z
+    long long yoff[MTGP_TMAX];
+    int order[MTGP_TMAX];
+};
+
+__device__ void load_R_tree(double* sR, const TreeParams& p, const ThetaPtrs& th) {
+    for (int e = threadIdx.x; e < p.T * p.T; e += blockDim.x) {
+        int t = e / p.T, u = e % p.T;
+        int tc = p.order[t], uc = p.order[u];
+        double r = 0.0;
+        for (int k = 0; k < th.s; ++k) r += th.W[tc * th.s + k] * th.W[uc * th.s + k];
+        if (t == u) r += th.v[tc];
+        sR[e] = r;
+    }
+}
+
+__device__ __forceinline__ int gidx(int t, int u, int T) { return t * T - t * (t - 1) / 2 + (u - t); }
+
+// Forward solve L u = r on the class graph (right-looking), accumulating sum |u_j|^2 / D_j.
+// Node (t, f) is eliminated at stage t; its ancestor in task a > t is (a, f mod n_a) and
+// L[(a, .), (t, f)] = conj(S_{ta}[f]) / D_{(t,f)}.
+template <bool CPLX>
+__device__ void tree_forward(const TreeParams& p, const double* Sb, double* rb, long long rho, bool act, int warp,
+                             double& quad) {
+    using V = Vt<CPLX>;
+    const long long nT = p.nT;
+    for (int t = 0; t < p.T; ++t) {
+        const long long mt = p.n[t] / nT;
+        if (act) {
+            for (long long k = warp; k < mt; k += kTreeWarps) {
+                long long f = rho + k * nT;
+                double D = creal(ld<CPLX>(Sb, p.po[t][t] + f));
+                quad += cabs2(ld<CPLX>(rb, p.yoff[t] + f)) / D;
+            }
+            for (int a = t + 1; a < p.T; ++a) {
+                const long long ma = p.n[a] / nT, rr = p.n[t] / p.n[a];
+                for (long long gi = warp; gi < ma; gi += kTreeWarps) {
+                    V acc = czero<V>();
+                    for (long long q = 0; q < rr; ++q) {
+                        long long f = rho + (gi + q * ma) * nT;
+                        double D = creal(ld<CPLX>(Sb, p.po[t][t] + f));
+                        acc = vadd(acc, vscale(vmul(cconj(ld<CPLX>(Sb, p.po[t][a] + f)), ld<CPLX>(rb, p.yoff[t] + f)), 1.0 / D));
+                    }
+                    long long g = rho + gi * nT;
+                    st<CPLX>(rb, p.yoff[a] + g, vsub(ld<CPLX>(rb, p.yoff[a] + g), acc));
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Backward solve L^H alpha = D^-1 u (top-down) and, when wantZ, the selected inverse on the
+// pattern:  Z[j, a'] = -sum_{a in anc(j)} conj(L[a, j]) Z[a, a']  (a' in anc(j)),
+//           Z[j, j]  = 1/D_j - sum_{a in anc(j)} conj(L[a, j]) Z[a, j].
+// Z is stored like S: Z_{ta'}[f] = Z[(t, f), (a', f mod n_a')].
+template <bool CPLX>
+__device__ void tree_backward(const TreeParams& p, const double* Sb, double* Zb, const double* rb, double* ab,
+                              long long rho, bool act, int warp, bool wantZ) {
+    using V = Vt<CPLX>;
+    const long long nT = p.nT;
+    for (int t = p.T - 1; t >= 0; --t) {
+        const long long mt = p.n[t] / nT;
+        if (act) {
+            for (long long k = warp; k < mt; k += kTreeWarps) {
+                long long f = rho + k * nT;
+                double invD = 1.0 / creal(ld<CPLX>(Sb, p.po[t][t] + f));
+                V a = vscale(ld<CPLX>(rb, p.yoff[t] + f), invD);
+                for (int a2 = t + 1; a2 < p.T; ++a2) {
+                    V l = vscale(ld<CPLX>(Sb, p.po[t][a2] + f), invD);
+                    a = vsub(a, vmul(l, ld<CPLX>(ab, p.yoff[a2] + (f & (p.n[a2] - 1)))));
+                }
+                st<CPLX>(ab, p.yoff[t] + f, a);
+                if (wantZ) {
+                    double zd = invD;
+                    for (int a2 = t + 1; a2 < p.T; ++a2) {
+                        V z = czero<V>();
+                        for (int a1 = t + 1; a1 < p.T; ++a1) {
+                            V l = vscale(ld<CPLX>(Sb, p.po[t][a1] + f), invD);
+                            V zz = (a1 <= a2) ? ld<CPLX>(Zb, p.po[a1][a2] + (f & (p.n[a1] - 1)))
+                                              : cconj(ld<CPLX>(Zb, p.po[a2][a1] + (f & (p.n[a2] - 1))));
+                            z = vsub(z, vmul(l, zz));
+                        }
+                        st<CPLX>(Zb, p.po[t][a2] + f, z);
+                    }
+                    for (int a1 = t + 1; a1 < p.T; ++a1) {
+                        V l = vscale(ld<CPLX>(Sb, p.po[t][a1] + f), invD);
+                        zd -= creal(vmul(l, cconj(ld<CPLX>(Zb, p.po[t][a1] + f))));
+                    }
+                    st<CPLX>(Zb, p.po[t][t] + f, cfromreal<V>(zd));
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// A CTA owns 32 consecutive residue classes rho mod n_T (one per lane); its warps split the nodes
+// of each class, so a warp's accesses touch 32 consecutive frequencies.  The first class (rho = 0)
+// also carries the optimal means (theorem item 4): it is solved once with yhat to get Pi and
+// E K~^-1 y, then every class is solved with rhat.
+template <bool CPLX, typename S>
+__global__ void __launch_bounds__(kTreeThreads)
+k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double* Zb, double* rb, double* ab,
+             double* tau_out, TreeParams p, ThetaPtrs th, double* partials, int* status) {
+    using V = Vt<CPLX>;
+    const int T = p.T;
+    const int NG = T * (T + 1) / 2;
+    const int NQ = 3 + NG;
+    __shared__ double sR[MTGP_TMAX * MTGP_TMAX];
+    __shared__ double s_sig;
+    __shared__ double s_tau[MTGP_TMAX];
+    __shared__ double s_red[kTreeWarps][3 + MTGP_MAX_COLS];
+    load_R_tree(sR, p, th);
+    if (threadIdx.x == 0) s_sig = th.sigma2[0];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long nT = p.nT;
+    const long long rho = (long long)blockIdx.x * 32 + lane;
+    const bool act = rho < nT;
+    double acc[3 + MTGP_MAX_COLS];
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+    int bad = 0;
+
+    // Lambda entries of the class: S_{tu}[f] = Lambda[(t, f), (u, f mod n_u)]
+    for (int t = 0; t < T; ++t) {
+        const long long mt = p.n[t] / nT;
+        for (int u = t; u < T; ++u) {
+            const double sc = sqrt((double)p.n[u] / (double)p.n[t]) * sR[t * T + u];
+            if (!act) continue;
+            for (long long k = warp; k < mt; k += kTreeWarps) {
+                long long f = rho + k * nT;
+                V mu = load_spec<S, CPLX>(spec, p.po[t][u] + f);
+                V val;
+                if (t == u) {
+                    double m0 = creal(mu);
+                    if (p.clamp && m0 < 0.0) m0 = 0.0;
+                    val = cfromreal<V>(sR[t * T + t] * m0 + s_sig);
+                } else {
+                    val = vscale(mu, sc);
+                }
+                st<CPLX>(Sb, p.po[t][u] + f, val);
+            }
+        }
+    }
+    __syncthreads();
+
+    // elimination in task order: pivots are the Schur complements S_t of Algorithm 1
+    for (int t = 0; t < T; ++t) {
+        const long long mt = p.n[t] / nT;
+        if (act) {
+            for (long long k = warp; k < mt; k += kTreeWarps) {
+                long long f = rho + k * nT;
+                double D = creal(ld<CPLX>(Sb, p.po[t][t] + f));
+                if (!(D > 0.0) || !isfinite(D)) bad = 1;
+                else acc[0] += log(D);
+            }
+            for (int a = t + 1; a < T; ++a) {
+                const long long ma = p.n[a] / nT, rr = p.n[t] / p.n[a];
+                for (int a2 = a; a2 < T; ++a2) {
+                    for (long long gi = warp; gi < ma; gi += kTreeWarps) {
+                        V s = czero<V>();
+                        for (long long q = 0; q < rr; ++q) {
+                            long long f = rho + (gi + q * ma) * nT;
+                            double D = creal(ld<CPLX>(Sb, p.po[t][t] + f));
+                            s = vadd(s, vscale(vmul(cconj(ld<CPLX>(Sb, p.po[t][a] + f)), ld<CPLX>(Sb, p.po[t][a2] + f)), 1.0 / D));
+                        }
+                        long long g = rho + gi * nT;
+                        st<CPLX>(Sb, p.po[a][a2] + g, vsub(ld<CPLX>(Sb, p.po[a][a2] + g), s));
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // optimal means from the first class
+    if (blockIdx.x == 0) {
+        const bool act0 = act && rho == 0;
+        if (act0) {
+            for (int t = 0; t < T; ++t) {
+                const long long mt = p.n[t] / nT;
+                for (long long k = warp; k < mt; k += kTreeWarps)
+                    st<CPLX>(rb, p.yoff[t] + k * nT, ld<CPLX>(yhat, p.yoff[t] + k * nT));
+            }
+        }
+        __syncthreads();
+        double qd = 0.0;
+        tree_forward<CPLX>(p, Sb, rb, rho, act0, warp, qd);
+        tree_backward<CPLX>(p, Sb, Zb, rb, ab, rho, act0, warp, true);
+        if (threadIdx.x == 0) {
+            double Pi[MTGP_TMAX][MTGP_TMAX], b[MTGP_TMAX];
+            for (int t = 0; t < T; ++t) {
+                b[t] = sqrt((double)p.n[t]) * creal(ld<CPLX>(ab, p.yoff[t]));
+                for (int u = 0; u < T; ++u) {
+                    double z = (t <= u) ? creal(ld<CPLX>(Zb, p.po[t][u])) : creal(ld<CPLX>(Zb, p.po[u][t]));
+                    Pi[t][u] = sqrt((double)p.n[t] * (double)p.n[u]) * z;
+                }
+            }
+            // Pi tau = b by Cholesky (Pi = E K~^-1 E^T is SPD)
+            for (int k = 0; k < T; ++k) {
+                double dk = Pi[k][k];
+                for (int j = 0; j < k; ++j) dk -= Pi[k][j] * Pi[k][j];
+                if (!(dk > 0.0)) {
+                    bad = 1;
+                    dk = 1.0;
+                }
+                dk = sqrt(dk);
+                Pi[k][k] = dk;
+                for (int i = k + 1; i < T; ++i) {
+                    double a = Pi[i][k];
+                    for (int j = 0; j < k; ++j) a -= Pi[i][j] * Pi[k][j];
+                    Pi[i][k] = a / dk;
+                }
+            }
+            for (int k = 0; k < T; ++k) {
+                double a = b[k];
+                for (int j = 0; j < k; ++j) a -= Pi[k][j] * b[j];
+                b[k] = a / Pi[k][k];
+            }
+            for (int k = T - 1; k >= 0; --k) {
+                double a = b[k];
+                for (int i = k + 1; i < T; ++i) a -= Pi[i][k] * b[i];
+                b[k] = a / Pi[k][k];
+            }
+            for (int t = 0; t < T; ++t) {
+                s_tau[t] = b[t];
+                tau_out[t] = b[t];
+            }
+        }
+        __syncthreads();
+    }
+
+    // rhat = yhat - V^dagger E^T tau: only the zero frequency of each task changes
+    if (act) {
+        for (int t = 0; t < T; ++t) {
+            const long long mt = p.n[t] / nT;
+            for (long long k = warp; k < mt; k += kTreeWarps) {
+                long long f = rho + k * nT;
+                V y = ld<CPLX>(yhat, p.yoff[t] + f);
+                if (f == 0) y = vsub(y, cfromreal<V>(sqrt((double)p.n[t]) * s_tau[t]));
+                st<CPLX>(rb, p.yoff[t] + f, y);
+            }
+        }
+    }
+    __syncthreads();
+    tree_forward<CPLX>(p, Sb, rb, rho, act, warp, acc[1]);
+    tree_backward<CPLX>(p, Sb, Zb, rb, ab, rho, act, warp, p.grad != 0);
+
+    if (p.grad && act) {
+        for (int t = 0; t < T; ++t) {
+            const long long mt = p.n[t] / nT;
+            for (int u = t; u < T; ++u) {
+                const double sc = sqrt((double)p.n[u] / (double)p.n[t]);
+                const int q = 3 + gidx(t, u, T);
+                for (long long k = warp; k < mt; k += kTreeWarps) {
+                    long long f = rho + k * nT;
+                    V at = ld<CPLX>(ab, p.yoff[t] + f);
+                    V au = ld<CPLX>(ab, p.yoff[u] + (f & (p.n[u] - 1)));
+                    V g = vsub(cconj(ld<CPLX>(Zb, p.po[t][u] + f)), vmul(au, cconj(at)));
+                    V mu = load_spec<S, CPLX>(spec, p.po[t][u] + f);
+                    if (u == t) {
+                        double gd = creal(g);
+                        double m0 = creal(mu);
+                        double ind = 1.0;
+                        if (p.clamp && m0 < 0.0) {
+                            m0 = 0.0;
+                            ind = 0.0;
+                        }
+                        acc[2] += gd;
+                        acc[q] += gd * m0;
+                        store_spec<S, CPLX>(wgt, p.po[t][u] + f, cfromreal<V>(sR[t * T + t] * gd * ind));
+                    } else {
+                        acc[q] += sc * creal(vmul(g, mu));
+                        store_spec<S, CPLX>(wgt, p.po[t][u] + f, vscale(g, 2.0 * sR[t * T + u] * sc));
+                    }
+                }
+            }
+        }
+    }
+    if (bad) set_status(status, ST_NOT_PD);
+    for (int q = 0; q < NQ; ++q) {
+        double v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) s_red[warp][q] = v;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
+        double v = 0.0;
+        for (int w = 0; w < kTreeWarps; ++w) v += s_red[w][q];
+        partials[(long long)blockIdx.x * NQ + q] = v;
+    }
+}
+
+// --------------------------------------------------------------------------- finalize
+
+struct FinParams {
+    int T, d, s, equal, cplx, NQ, nsolve, neta, grad;
+    long long N;
+    long long n0;
+    int order[MTGP_TMAX];
+    int rank[MTGP_TMAX];
+    long long yoff[MTGP_TMAX];
+};
+
+__global__ void k_finalize(const double* partials, const double* eta_partials, const double* yhat,
+                           const double* tau_sorted, FinParams p, ThetaPtrs th, double* out, double* tau,
+                           double* g_eta, double* g_W, double* g_v, double* g_s2) {
+    __shared__ double tot[3 + MTGP_MAX_COLS];
+    __shared__ double etot[MTGP_MAX_DIM];
+    for (int q = threadIdx.x; q < p.NQ; q += blockDim.x) {
+        double v = 0.0;
+        for (int b = 0; b < p.nsolve; ++b) v += partials[(long long)b * p.NQ + q];
+        tot[q] = v;
+    }
+    if (p.grad) {
+        for (int j = threadIdx.x; j < p.d; j += blockDim.x) {
+            double v = 0.0;
+            for (int b = 0; b < p.neta; ++b) v += eta_partials[(long long)b * p.d + j];
+            etot[j] = v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double LOG2PI = 1.8378770664093453;
+    out[0] = 0.5 * (tot[0] + tot[1] + (double)p.N * LOG2PI);
+    out[1] = tot[1];
+    out[2] = tot[0];
+    if (tau) {
+        for (int t = 0; t < p.T; ++t) {
+            double tv;
+            if (p.equal) tv = yhat[(p.cplx ? 2 : 1) * p.yoff[t]] / sqrt((double)p.n0);
+            else tv = tau_sorted[t];
+            tau[p.order[t]] = tv;
+        }
+    }
+    if (!p.grad) return;
+    const int T = p.T;
+    g_s2[0] = 0.5 * tot[2];
+    for (int j = 0; j < p.d; ++j) g_eta[j] = 0.5 * etot[j];
+    for (int tc = 0; tc < T; ++tc) {
+        int t = p.rank[tc];
+        for (int k = 0; k < p.s; ++k) {
+            double g = 0.0;
+            for (int uc = 0; uc < T; ++uc) {
+                int u = p.rank[uc];
+                double G = (t <= u) ? tot[3 + gidx(t, u, T)] : tot[3 + gidx(u, t, T)];
+                g += G * th.W[uc * p.s + k];
+            }
+            g_W[tc * p.s + k] = g;
+        }
+        g_v[tc] = 0.5 * tot[3 + gidx(t, t, T)];
+    }
+}
+
+int eq_blocks(const Handle* h) {
+    long long b = (h->n[0] + kEqThreads - 1) / kEqThreads;
+    if (b > 152 * 8) b = 152 * 8;
+    return (int)b;
+}
+
+}  // namespace
+
+int solve_equal_blocks(const Handle* h) { return eq_blocks(h); }
+int solve_tree_blocks(const Handle* h) { return (int)((h->n[h->T - 1] + 31) / 32); }
+
+template <int T, bool CPLX, typename S>
+static void run_eq(const Handle* h, ThetaPtrs th, SolveParams sp, double* partials, cudaStream_t st) {
+    k_solve_equal<T, CPLX, S><<<eq_blocks(h), kEqThreads, 0, st>>>(h->spec, h->wgt, h->yhat, sp, th, partials, h->alpha,
+                                                                   h->status);
+}
+
+template <bool CPLX, typename S>
+static void dispatch_eq(const Handle* h, ThetaPtrs th, SolveParams sp, double* partials, cudaStream_t st) {
+    switch (h->T) {
+        case 1: run_eq<1, CPLX, S>(h, th, sp, partials, st); break;
+        case 2: run_eq<2, CPLX, S>(h, th, sp, partials, st); break;
+        case 3: run_eq<3, CPLX, S>(h, th, sp, partials, st); break;
+        case 4: run_eq<4, CPLX, S>(h, th, sp, partials, st); break;
+        case 5: run_eq<5, CPLX, S>(h, th, sp, partials, st); break;
+        case 6: run_eq<6, CPLX, S>(h, th, sp, partials, st); break;
+        case 7: run_eq<7, CPLX, S>(h, th, sp, partials, st); break;
+        default: run_eq<8, CPLX, S>(h, th, sp, partials, st); break;
+    }
+}
+
+void launch_solve_equal(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st) {
+    SolveParams sp;
+    sp.T = h->T;
+    sp.s = th.s;
+    sp.nT = 0;
+    sp.grad = grad ? 1 : 0;
+    sp.clamp = h->fp32 ? 1 : 0;
+    sp.store_alpha = 1;
+    for (int t = 0; t < MTGP_TMAX; ++t) {
+        sp.n[t] = t < h->T ? h->n[t] : 0;
+        sp.order[t] = t < h->T ? h->order[t] : 0;
+        sp.yoff[t] = t < h->T ? h->yoff[t] : 0;
+        for (int u = 0; u < MTGP_TMAX; ++u) sp.colidx[t][u] = (t < h->T && u < h->T && t <= u) ? h->col_of[t][u] : 0;
+    }
+    for (int c = 0; c < MTGP_MAX_COLS; ++c) sp.coloff[c] = c < h->ncols ? h->cols[c].off : 0;
+    if (h->fp32) {
+        if (h->cplx) dispatch_eq<true, float>(h, th, sp, partials, st);
+        else dispatch_eq<false, float>(h, th, sp, partials, st);
+    } else {
+        if (h->cplx) dispatch_eq<true, double>(h, th, sp, partials, st);
+        else dispatch_eq<false, double>(h, th, sp, partials, st);
+    }
+}
+
+void launch_solve_tree(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st) {
+    TreeParams tp;
+    tp.T = h->T;
+    tp.s = th.s;
+    tp.grad = grad ? 1 : 0;
+    tp.clamp = h->fp32 ? 1 : 0;
+    tp.nT = h->n[h->T - 1];
+    for (int t = 0; t < MTGP_TMAX; ++t) {
+        tp.n[t] = t < h->T ? h->n[t] : 1;
+        tp.order[t] = t < h->T ? h->order[t] : 0;
+        tp.yoff[t] = t < h->T ? h->yoff[t] : 0;
+        for (int u = 0; u < MTGP_TMAX; ++u)
+            tp.po[t][u] = (t < h->T && u < h->T && t <= u) ? h->cols[h->col_of[t][u]].off : 0;
+    }
+    int blocks = solve_tree_blocks(h);
+    if (h->fp32) {
+        if (h->cplx) k_solve_tree<true, float><<<blocks, kTreeThreads, 0, st>>>(h->spec, h->wgt, h->yhat, h->S, h->Z, h->r, h->alpha, h->tau, tp, th, partials, h->status);
+        else k_solve_tree<false, float><<<blocks, kTreeThreads, 0, st>>>(h->spec, h->wgt, h->yhat, h->S, h->Z, h->r, h->alpha, h->tau, tp, th, partials, h->status);
+    } else {
+        if (h->cplx) k_solve_tree<true, double><<<blocks, kTreeThreads, 0, st>>>(h->spec, h->wgt, h->yhat, h->S, h->Z, h->r, h->alpha, h->tau, tp, th, partials, h->status);
+        else k_solve_tree<false, double><<<blocks, kTreeThreads, 0, st>>>(h->spec, h->wgt, h->yhat, h->S, h->Z, h->r, h->alpha, h->tau, tp, th, partials, h->status);
+    }
+}
+
+void launch_finalize(const Handle* h, ThetaPtrs th, bool grad, const double* partials, int nsolve,
+                     const double* eta_partials, int neta, double* out, double* tau, double* g_eta, double* g_W,
+                     double* g_v, double* g_s2, cudaStream_t st) {
+    FinParams fp;
+    fp.T = h->T;
+    fp.d = h->d;
+    fp.s = th.s;
+    fp.equal = h->equal ? 1 : 0;
+    fp.cplx = h->cplx ? 1 : 0;
+    fp.NQ = 3 + h->T * (h->T + 1) / 2;
+    fp.nsolve = nsolve;
+    fp.neta = neta;
+    fp.grad = grad ? 1 : 0;
+    fp.N = h->N;
+    fp.n0 = h->n[0];
+    for (int t = 0; t < MTGP_TMAX; ++t) {
+        fp.order[t] = t < h->T ? h->order[t] : 0;
+        fp.rank[t] = t < h->T ? h->rank[t] : 0;
+        fp.yoff[t] = t < h->T ? h->yoff[t] : 0;
+    }
+    k_finalize<<<1, 64, 0, st>>>(partials, eta_partials, h->yhat, h->tau, fp, th, out, tau, g_eta, g_W, g_v, g_s2);
+}

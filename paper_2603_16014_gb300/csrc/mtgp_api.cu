@@ -1,0 +1,377 @@
+// C ABI entry points: argument validation, workspace layout and the launch sequence of each call.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mtgp_internal.cuh"
+
+void posterior_release(const Handle* h);
+
+struct mtgp_s {
+    Handle h;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return MTGP_ERR_CUDA;
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+    } while (0)
+
+__global__ void k_tau_equal(const double* yhat, double* tau, int T, long long n, int cplx) {
+    int t = threadIdx.x;
+    if (t < T) tau[t] = yhat[(cplx ? 2 : 1) * (long long)t * n] / sqrt((double)n);
+}
+
+__global__ void k_check_theta(ThetaPtrs th, int d, int T, int* status) {
+    int bad = 0;
+    for (int j = threadIdx.x; j < d; j += blockDim.x)
+        if (!isfinite(th.eta[j]) || th.eta[j] < 0.0) bad = 1;
+    for (int e = threadIdx.x; e < T * th.s; e += blockDim.x)
+        if (!isfinite(th.W[e])) bad = 1;
+    for (int t = threadIdx.x; t < T; t += blockDim.x)
+        if (!isfinite(th.v[t]) || th.v[t] < 0.0) bad = 1;
+    if (threadIdx.x == 0 && (!isfinite(th.sigma2[0]) || th.sigma2[0] < 0.0)) bad = 1;
+    if (bad) atomicOr(status, ST_NUMERIC);
+}
+
+__global__ void k_check_y(const double* y, long long N, int* status) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(y[i])) {
+            atomicOr(status, ST_NUMERIC);
+            return;
+        }
+}
+
+template <typename T>
+cudaError_t dalloc(Handle* h, T** p, size_t count) {
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e == cudaSuccess) h->ws_bytes += (long long)bytes;
+    return e;
+}
+
+void free_all(Handle* h) {
+    void* ptrs[] = {h->gen, h->shift, h->cols_dev, h->offs_dev, h->yoffs_dev, h->twid, h->twid32, h->yhat, h->spec,
+                    h->wgt, h->S, h->Z, h->r, h->alpha, h->tau, h->partials, h->status, h->out_tmp};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+int validate_theta(const Handle* h, const double* eta, const double* W, int s, const double* v, const double* sigma2) {
+    if (!eta || !W || !v || !sigma2) return fail(MTGP_ERR_INVALID_ARG, "theta pointer is NULL");
+    if (s < 1 || s > h->T) return fail(MTGP_ERR_INVALID_ARG, "s must satisfy 1 <= s <= T");
+    return MTGP_OK;
+}
+
+// NLL (and gradient) at theta; leaves alpha = Lambda^-1 rhat in h->alpha and tau in h->tau.
+int run_nll(Handle* h, ThetaPtrs th, bool grad, double* out, double* tau, double* g_eta, double* g_W, double* g_v,
+            double* g_s2, cudaStream_t st) {
+    k_check_theta<<<1, 64, 0, st>>>(th, h->d, h->T, h->status);
+    launch_colgen(h, th.eta, h->spec, st);
+    for (int g = 0; g < h->ngroups; ++g)
+        launch_transform(h, h->spec, h->fp32, h->cplx, h->group_m[g], h->offs_dev + h->group_first[g],
+                         h->group_count[g], false, st);
+    int nsolve;
+    if (h->equal) {
+        launch_solve_equal(h, th, grad, h->partials, st);
+        nsolve = solve_equal_blocks(h);
+    } else {
+        launch_solve_tree(h, th, grad, h->partials, st);
+        nsolve = solve_tree_blocks(h);
+    }
+    const int NQ = 3 + h->T * (h->T + 1) / 2;
+    double* eta_part = h->partials + (long long)nsolve * NQ;
+    int neta = 0;
+    if (grad) {
+        for (int g = 0; g < h->ngroups; ++g)
+            launch_transform(h, h->wgt, h->fp32, h->cplx, h->group_m[g], h->offs_dev + h->group_first[g],
+                             h->group_count[g], true, st);
+        neta = eta_grad_blocks(h);
+        launch_eta_grad(h, th.eta, h->wgt, eta_part, neta, st);
+    }
+    launch_finalize(h, th, grad, h->partials, nsolve, eta_part, neta, out, tau, g_eta, g_W, g_v, g_s2, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return MTGP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mtgp_last_error_string(void) { return g_err.c_str(); }
+
+long long mtgp_workspace_bytes(const mtgp_t* hh) { return hh ? hh->h.ws_bytes : 0; }
+
+int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32_t* gen, int gen_cols,
+                const uint32_t* shift, int precision) {
+    if (!out) return fail(MTGP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (kind != MTGP_LATTICE && kind != MTGP_DNET) return fail(MTGP_ERR_INVALID_ARG, "kind must be MTGP_LATTICE or MTGP_DNET");
+    if (d < 1 || d > MTGP_MAX_DIM) return fail(MTGP_ERR_INVALID_ARG, "d out of range [1, MTGP_MAX_DIM]");
+    if (T < 1 || T > MTGP_MAX_TASKS) return fail(MTGP_ERR_INVALID_ARG, "T out of range [1, MTGP_MAX_TASKS]");
+    if (!m || !gen || !shift) return fail(MTGP_ERR_INVALID_ARG, "m, gen and shift must be host arrays");
+    if (precision != MTGP_FP64 && precision != MTGP_FP32_TRANSFORM)
+        return fail(MTGP_ERR_INVALID_ARG, "precision must be MTGP_FP64 or MTGP_FP32_TRANSFORM");
+    int mmax = 0;
+    for (int t = 0; t < T; ++t) {
+        if (m[t] < 0 || m[t] > MTGP_MAX_M) return fail(MTGP_ERR_INVALID_ARG, "m[t] out of range [0, MTGP_MAX_M]");
+        mmax = m[t] > mmax ? m[t] : mmax;
+    }
+    if (kind == MTGP_DNET && (gen_cols < mmax || gen_cols > 32))
+        return fail(MTGP_ERR_INVALID_ARG, "gen_cols must satisfy max m <= gen_cols <= 32");
+    mtgp_s* hs = new (std::nothrow) mtgp_s();
+    if (!hs) return fail(MTGP_ERR_CUDA, "host allocation failed");
+    Handle* h = &hs->h;
+    std::memset(h, 0, sizeof(Handle));
+    h->kind = kind;
+    h->d = d;
+    h->T = T;
+    h->prec = precision;
+    h->fp32 = precision == MTGP_FP32_TRANSFORM;
+    h->cplx = kind == MTGP_LATTICE;
+    h->gen_cols = kind == MTGP_DNET ? gen_cols : 1;
+    h->mmax = mmax;
+    // sort tasks by decreasing size, ties by caller index (stable)
+    std::vector<int> ord(T);
+    for (int t = 0; t < T; ++t) ord[t] = t;
+    for (int i = 1; i < T; ++i)
+        for (int j = i; j > 0 && m[ord[j]] > m[ord[j - 1]]; --j) std::swap(ord[j], ord[j - 1]);
+    h->equal = true;
+    long long off = 0;
+    for (int t = 0; t < T; ++t) {
+        h->m_user[t] = m[t];
+        h->order[t] = ord[t];
+        h->rank[ord[t]] = t;
+        h->m[t] = m[ord[t]];
+        h->n[t] = 1LL << h->m[t];
+        h->yoff[t] = off;
+        off += h->n[t];
+        if (h->m[t] != h->m[0]) h->equal = false;
+    }
+    h->N = off;
+    // first columns: equal sizes share the diagonal column; otherwise one column per pair t <= u
+    int c = 0;
+    long long coff = 0;
+    if (h->equal) {
+        h->cols[c] = ColDesc{coff, (int)h->n[0], 0, 0};
+        for (int t = 0; t < T; ++t) h->col_of[t][t] = 0;
+        coff += h->n[0];
+        ++c;
+        for (int t = 0; t < T; ++t)
+            for (int u = t + 1; u < T; ++u) {
+                h->cols[c] = ColDesc{coff, (int)h->n[0], t, u};
+                h->col_of[t][u] = c;
+                coff += h->n[0];
+                ++c;
+            }
+    } else {
+        for (int t = 0; t < T; ++t)
+            for (int u = t; u < T; ++u) {
+                h->cols[c] = ColDesc{coff, (int)h->n[t], t, u};
+                h->col_of[t][u] = c;
+                coff += h->n[t];
+                ++c;
+            }
+    }
+    h->ncols = c;
+    h->col_elems = coff;
+    // group columns by length for batched transforms (columns are ordered by t, so lengths are runs)
+    h->ngroups = 0;
+    for (int i = 0; i < h->ncols;) {
+        int j = i;
+        while (j < h->ncols && h->cols[j].n == h->cols[i].n) ++j;
+        int g = h->ngroups++;
+        h->group_first[g] = i;
+        h->group_count[g] = j - i;
+        int mm = 0;
+        while ((1LL << mm) < h->cols[i].n) ++mm;
+        h->group_m[g] = mm;
+        i = j;
+    }
+    const size_t es = (h->fp32 ? 4 : 8) * (h->cplx ? 2 : 1);
+    const size_t vs = h->cplx ? 2 : 1;  // doubles per FP64 value
+    cudaError_t e;
+#define AL(ptr, cnt)                                              \
+    e = dalloc(h, &(ptr), (cnt));                                 \
+    if (e != cudaSuccess) {                                       \
+        free_all(h);                                              \
+        delete hs;                                                \
+        return cuda_fail(e, "cudaMalloc workspace");              \
+    }
+    AL(h->gen, (size_t)d * h->gen_cols);
+    AL(h->shift, (size_t)T * d);
+    AL(h->cols_dev, (size_t)h->ncols);
+    AL(h->offs_dev, (size_t)h->ncols);
+    AL(h->yoffs_dev, (size_t)T);
+    {
+        size_t half = mmax >= 1 ? ((size_t)1 << (mmax - 1)) : 1;
+        double* tw64 = nullptr;
+        float* tw32 = nullptr;
+        AL(tw64, half * 2);
+        AL(tw32, half * 2);
+        h->twid = tw64;
+        h->twid32 = tw32;
+    }
+    AL(h->yhat, (size_t)h->N * vs);
+    {
+        unsigned char* sp = nullptr;
+        unsigned char* wg = nullptr;
+        AL(sp, (size_t)h->col_elems * es);
+        AL(wg, (size_t)h->col_elems * es);
+        h->spec = sp;
+        h->wgt = wg;
+    }
+    if (!h->equal) {
+        AL(h->S, (size_t)h->col_elems * vs);
+        AL(h->Z, (size_t)h->col_elems * vs);
+    }
+    AL(h->r, (size_t)h->N * vs);
+    AL(h->alpha, (size_t)h->N * vs);
+    AL(h->tau, (size_t)MTGP_TMAX);
+    {
+        const int NQ = 3 + T * (T + 1) / 2;
+        long long nsolve = h->equal ? solve_equal_blocks(h) : solve_tree_blocks(h);
+        h->partials_len = nsolve * NQ + (long long)eta_grad_blocks(h) * d;
+        AL(h->partials, (size_t)h->partials_len);
+    }
+    AL(h->status, (size_t)1);
+    AL(h->out_tmp, (size_t)4);
+#undef AL
+    // upload descriptors
+    std::vector<uint32_t> shift_sorted((size_t)T * d);
+    for (int t = 0; t < T; ++t)
+        for (int j = 0; j < d; ++j) shift_sorted[(size_t)t * d + j] = shift[(size_t)h->order[t] * d + j];
+    std::vector<long long> offs(h->ncols), yoffs(T);
+    for (int i = 0; i < h->ncols; ++i) offs[i] = h->cols[i].off;
+    for (int t = 0; t < T; ++t) yoffs[t] = h->yoff[t];
+    bool okc = cudaMemcpy(h->gen, gen, (size_t)d * h->gen_cols * sizeof(uint32_t), cudaMemcpyHostToDevice) == cudaSuccess &&
+               cudaMemcpy(h->shift, shift_sorted.data(), shift_sorted.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) == cudaSuccess &&
+               cudaMemcpy(h->cols_dev, h->cols, (size_t)h->ncols * sizeof(ColDesc), cudaMemcpyHostToDevice) == cudaSuccess &&
+               cudaMemcpy(h->offs_dev, offs.data(), offs.size() * sizeof(long long), cudaMemcpyHostToDevice) == cudaSuccess &&
+               cudaMemcpy(h->yoffs_dev, yoffs.data(), yoffs.size() * sizeof(long long), cudaMemcpyHostToDevice) == cudaSuccess &&
+               cudaMemset(h->status, 0, sizeof(int)) == cudaSuccess &&
+               cudaMemset(h->tau, 0, MTGP_TMAX * sizeof(double)) == cudaSuccess;
+    if (!okc) {
+        free_all(h);
+        delete hs;
+        return fail(MTGP_ERR_CUDA, "uploading handle descriptors failed");
+    }
+    launch_twiddles(h, 0);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_all(h);
+        delete hs;
+        return cuda_fail(e, "twiddle table");
+    }
+    *out = hs;
+    return MTGP_OK;
+}
+
+int mtgp_destroy(mtgp_t* hs) {
+    if (!hs) return MTGP_OK;
+    cudaDeviceSynchronize();
+    posterior_release(&hs->h);
+    free_all(&hs->h);
+    delete hs;
+    return MTGP_OK;
+}
+
+int mtgp_points(mtgp_t* hs, uint32_t* x, cudaStream_t st) {
+    if (!hs || !x) return fail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    launch_points(&hs->h, x, st);
+    CK(cudaGetLastError());
+    return MTGP_OK;
+}
+
+int mtgp_set_y(mtgp_t* hs, const double* y, cudaStream_t st) {
+    if (!hs || !y) return fail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    Handle* h = &hs->h;
+    int blocks = (int)((h->N + 255) / 256);
+    if (blocks > 1024) blocks = 1024;
+    k_check_y<<<blocks, 256, 0, st>>>(y, h->N, h->status);
+    launch_y_load(h, y, st);
+    if (h->equal) k_tau_equal<<<1, 32, 0, st>>>(h->yhat, h->tau, h->T, h->n[0], h->cplx ? 1 : 0);
+    CK(cudaGetLastError());
+    h->y_set = true;
+    return MTGP_OK;
+}
+
+int mtgp_nll(mtgp_t* hs, const double* eta, const double* W, int s, const double* v, const double* sigma2,
+             double* out, double* tau, cudaStream_t st) {
+    if (!hs || !out) return fail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    Handle* h = &hs->h;
+    int rc = validate_theta(h, eta, W, s, v, sigma2);
+    if (rc) return rc;
+    if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
+    ThetaPtrs th{eta, W, s, v, sigma2};
+    return run_nll(h, th, false, out, tau, nullptr, nullptr, nullptr, nullptr, st);
+}
+
+int mtgp_nll_grad(mtgp_t* hs, const double* eta, const double* W, int s, const double* v, const double* sigma2,
+                  double* out, double* tau, double* g_eta, double* g_W, double* g_v, double* g_sigma2,
+                  cudaStream_t st) {
+    if (!hs || !out) return fail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    if (!g_eta || !g_W || !g_v || !g_sigma2) return fail(MTGP_ERR_INVALID_ARG, "gradient outputs must not be NULL");
+    Handle* h = &hs->h;
+    int rc = validate_theta(h, eta, W, s, v, sigma2);
+    if (rc) return rc;
+    if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
+    ThetaPtrs th{eta, W, s, v, sigma2};
+    return run_nll(h, th, true, out, tau, g_eta, g_W, g_v, g_sigma2, st);
+}
+
+int mtgp_posterior(mtgp_t* hs, const double* eta, const double* W, int s, const double* v, const double* sigma2,
+                   int nq, const double* xq, const int* task, double* mean, double* var, cudaStream_t st) {
+    if (!hs || !xq || !task || !mean) return fail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    if (nq < 0) return fail(MTGP_ERR_INVALID_ARG, "nq < 0");
+    Handle* h = &hs->h;
+    int rc = validate_theta(h, eta, W, s, v, sigma2);
+    if (rc) return rc;
+    if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
+    if (var && !h->equal) return fail(MTGP_ERR_UNSUPPORTED, "posterior variance needs equal task sizes in this build");
+    if (nq == 0) return MTGP_OK;
+    ThetaPtrs th{eta, W, s, v, sigma2};
+    // the solve leaves alpha = Lambda^-1 rhat and tau in the workspace
+    rc = run_nll(h, th, false, h->out_tmp, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    if (rc) return rc;
+    rc = posterior_run(h, th, nq, xq, task, mean, var, st);
+    if (rc) return rc == MTGP_ERR_CUDA ? fail(rc, "posterior scratch allocation failed") : fail(rc, "posterior");
+    CK(cudaGetLastError());
+    return MTGP_OK;
+}
+
+int mtgp_sync(mtgp_t* hs, cudaStream_t st) {
+    if (!hs) return fail(MTGP_ERR_INVALID_ARG, "NULL handle");
+    Handle* h = &hs->h;
+    int s = 0;
+    CK(cudaMemcpyAsync(&s, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+    CK(cudaStreamSynchronize(st));
+    if (s & ST_NUMERIC) return fail(MTGP_ERR_NUMERIC, "non-finite value in an input or intermediate");
+    if (s & ST_NOT_PD) return fail(MTGP_ERR_NOT_PD, "non-positive pivot: Lambda-tilde is not numerically HPD");
+    if (s & ST_TIMEOUT) return fail(MTGP_ERR_TIMEOUT, "a bounded device wait gave up");
+    return MTGP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,219 @@
+// Internal declarations shared by the CUDA translation units of the fast-MTGP library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mtgp.h"
+
+#define MTGP_TMAX MTGP_MAX_TASKS
+#define MTGP_MAX_COLS (MTGP_TMAX * (MTGP_TMAX + 1) / 2)
+
+// status bits written by kernels (atomicOr); mtgp_sync maps the lowest set bit to an error code
+#define ST_NOT_PD 1
+#define ST_NUMERIC 2
+#define ST_TIMEOUT 4
+
+// ------------------------------------------------------------------------------- complex
+
+template <typename S>
+struct cx {
+    S re, im;
+};
+
+template <typename S>
+__host__ __device__ __forceinline__ cx<S> mk(S a, S b) { cx<S> r; r.re = a; r.im = b; return r; }
+template <typename S>
+__host__ __device__ __forceinline__ cx<S> operator+(cx<S> a, cx<S> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename S>
+__host__ __device__ __forceinline__ cx<S> operator-(cx<S> a, cx<S> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename S>
+__host__ __device__ __forceinline__ cx<S> operator*(cx<S> a, cx<S> b) {
+    return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename S>
+__host__ __device__ __forceinline__ cx<S> operator*(S a, cx<S> b) { return mk(a * b.re, a * b.im); }
+template <typename S>
+__host__ __device__ __forceinline__ cx<S> conj(cx<S> a) { return mk(a.re, -a.im); }
+template <typename S>
+__host__ __device__ __forceinline__ S norm2(cx<S> a) { return a.re * a.re + a.im * a.im; }
+
+// Scalar-or-complex value used by the solvers: real problems (digital nets) use V = double,
+// lattices use V = cx<double>.
+__host__ __device__ __forceinline__ double cconj(double a) { return a; }
+__host__ __device__ __forceinline__ cx<double> cconj(cx<double> a) { return conj(a); }
+__host__ __device__ __forceinline__ double creal(double a) { return a; }
+__host__ __device__ __forceinline__ double creal(cx<double> a) { return a.re; }
+__host__ __device__ __forceinline__ double cabs2(double a) { return a * a; }
+__host__ __device__ __forceinline__ double cabs2(cx<double> a) { return norm2(a); }
+template <typename V> __host__ __device__ __forceinline__ V czero();
+template <> __host__ __device__ __forceinline__ double czero<double>() { return 0.0; }
+template <> __host__ __device__ __forceinline__ cx<double> czero<cx<double>>() { return mk(0.0, 0.0); }
+template <typename V> __host__ __device__ __forceinline__ V cfromreal(double a);
+template <> __host__ __device__ __forceinline__ double cfromreal<double>(double a) { return a; }
+template <> __host__ __device__ __forceinline__ cx<double> cfromreal<cx<double>>(double a) { return mk(a, 0.0); }
+
+// --------------------------------------------------------------------- fixed-point kernels
+
+#define MTGP_2POW_M32 2.3283064365386962890625e-10  // 2^-32 exactly
+#define MTGP_PI4_45 2.1646464674222763    // pi^4 / 45
+#define MTGP_2PI4_3 64.939394022668291    // 2 pi^4 / 3
+
+// Univariate SI kernel of Eq. 2.5 with alpha = 2: (2 pi)^4 / 4! * (1/30 - u^2 (1 - u)^2)
+// = pi^4/45 - (2 pi^4 / 3) (u (1 - u))^2, u = X / 2^32 = (x - x') mod 1.  The kernel is
+// symmetric under u -> 1 - u, so u is folded to [0, 1/2] in integer arithmetic first.
+template <typename S>
+__device__ __forceinline__ S si2_kernel(uint32_t X) {
+    uint32_t Y = (X > 0x80000000u) ? (0u - X) : X;
+    S u = (S)Y * (S)MTGP_2POW_M32;
+    S w = u * ((S)1 - u);
+    return (S)MTGP_PI4_45 - (S)MTGP_2PI4_3 * (w * w);
+}
+
+template <typename S>
+__device__ __forceinline__ S pow2_neg(int b);  // 2^-b for 0 <= b <= 64
+template <>
+__device__ __forceinline__ float pow2_neg<float>(int b) { return __int_as_float((127 - b) << 23); }
+template <>
+__device__ __forceinline__ double pow2_neg<double>(int b) {
+    return __longlong_as_double((long long)(1023 - b) << 52);
+}
+
+// Univariate DSI kernel of Eq. 2.6, order-2 term: -1 - beta(x) x + 5/2 (1 - 2^-beta(x)),
+// beta(x) = -floor(log2 x) = clz(X) + 1 for x = X / 2^32 > 0, and 3/2 at x = 0.
+template <typename S>
+__device__ __forceinline__ S dsi2_kernel(uint32_t X) {
+    if (X == 0u) return (S)1.5;
+    int b = __clz(X) + 1;
+    S x = (S)X * (S)MTGP_2POW_M32;
+    return (S)1.5 - (S)b * x - (S)2.5 * pow2_neg<S>(b);
+}
+
+template <typename S>
+__device__ __forceinline__ S kernel1d(int kind, uint32_t X) {
+    return kind == MTGP_LATTICE ? si2_kernel<S>(X) : dsi2_kernel<S>(X);
+}
+
+// Point z_i (unshifted) in coordinate j.  Lattice (Def. 2.1): v(i) g mod 1 = bitrev32(i) * g
+// mod 2^32.  Digital net (Def. 2.2): XOR of generating-matrix columns g_p for the set bits of i.
+__device__ __forceinline__ uint32_t point_word(int kind, uint32_t i, int j, const uint32_t* gen,
+                                               int gen_cols) {
+    if (kind == MTGP_LATTICE) return __brev(i) * gen[j];
+    const uint32_t* g = gen + (size_t)j * gen_cols;
+    uint32_t z = 0;
+    while (i) {
+        int p = __ffs(i) - 1;
+        z ^= g[p];
+        i &= i - 1;
+    }
+    return z;
+}
+
+// The combination x_{t,i} - x_{u,0} (lattice, mod 1) or x_{t,i} XOR x_{u,0} (digital net) that a
+// first column of block (t, u) evaluates: z_i (+/-) Delta_t (-/XOR) Delta_u.
+__device__ __forceinline__ uint32_t pair_word(int kind, uint32_t z, uint32_t dt, uint32_t du) {
+    return kind == MTGP_LATTICE ? (z + dt - du) : (z ^ dt ^ du);
+}
+
+// ------------------------------------------------------------------------------- columns
+
+// One first column of the block Gram matrix K~_{t,u} (sorted tasks, n_t >= n_u); for equal sizes
+// all diagonal blocks share column 0.
+struct ColDesc {
+    long long off;  // element offset in the column buffers
+    int n;          // length n_t
+    int t, u;       // sorted task pair (t <= u)
+};
+
+struct Handle;
+
+// ------------------------------------------------------------------------------- launchers
+
+struct ThetaPtrs {
+    const double* eta;
+    const double* W;
+    int s;
+    const double* v;
+    const double* sigma2;
+};
+
+// k_columns.cu
+void launch_colgen(const Handle* h, const double* eta, void* out, cudaStream_t st);
+void launch_points(const Handle* h, uint32_t* x, cudaStream_t st);
+void launch_y_load(const Handle* h, const double* y, cudaStream_t st);
+void launch_eta_grad(const Handle* h, const double* eta, const void* omega, double* partials,
+                     int nblk_max, cudaStream_t st);
+int eta_grad_blocks(const Handle* h);
+
+// k_transform.cu
+// forward (DIT, bit-reversed input -> natural output) or adjoint (DIF, natural -> bit-reversed)
+// transform of `narr` arrays of length 2^m at element offsets `offs` (device array).
+void launch_transform(const Handle* h, void* base, bool fp32, bool complex_data, int m,
+                      const long long* offs_dev, int narr, bool dif, cudaStream_t st);
+void launch_twiddles(Handle* h, cudaStream_t st);
+
+// k_solve.cu
+int solve_equal_blocks(const Handle* h);
+void launch_solve_equal(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st);
+void launch_solve_tree(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st);
+int solve_tree_blocks(const Handle* h);
+void launch_finalize(const Handle* h, ThetaPtrs th, bool grad, const double* partials, int nsolve,
+                     const double* eta_partials, int neta, double* out, double* tau, double* g_eta,
+                     double* g_W, double* g_v, double* g_s2, cudaStream_t st);
+
+// k_posterior.cu
+int posterior_run(Handle* h, ThetaPtrs th, int nq, const double* xq, const int* task, double* mean,
+                  double* var, cudaStream_t st);
+
+// ------------------------------------------------------------------------------- handle
+
+struct Handle {
+    int kind, d, T, prec;
+    bool fp32;           // transform precision
+    bool cplx;           // lattice spectra are complex
+    bool equal;          // all n_t equal
+    int gen_cols;
+    int m_user[MTGP_TMAX];
+    int order[MTGP_TMAX];    // sorted position -> caller task
+    int rank[MTGP_TMAX];     // caller task -> sorted position
+    int m[MTGP_TMAX];        // sorted
+    long long n[MTGP_TMAX];  // sorted
+    long long N;
+    long long yoff[MTGP_TMAX];  // element offset of sorted task t in yhat / per-task vectors
+    int mmax;
+
+    int ncols;
+    ColDesc cols[MTGP_MAX_COLS];
+    int col_of[MTGP_TMAX][MTGP_TMAX];  // sorted (t, u) with t <= u -> column
+    long long col_elems;               // total elements over columns
+
+    // device buffers
+    uint32_t* gen;       // lattice: d words; dnet: d * gen_cols
+    uint32_t* shift;     // sorted T x d
+    ColDesc* cols_dev;
+    long long* offs_dev;  // per column offset, grouped by length (see group_*)
+    int ngroups;
+    int group_m[MTGP_TMAX];
+    int group_first[MTGP_TMAX];
+    int group_count[MTGP_TMAX];
+    long long* yoffs_dev;  // per sorted task offset (for y transforms)
+
+    void* twid;          // twiddle table e^{-2 pi i k / 2^mmax}, k < 2^{mmax-1}, double2 and float2
+    void* twid32;
+    double* yhat;        // FP64 (complex for lattice), sorted tasks, length N
+    void* spec;          // column spectra (E = fp32 ? float : double, complex for lattice)
+    void* wgt;           // adjoint weights, same layout as spec
+    double* S;           // tree solver scratch (pair layout, FP64 (complex))
+    double* Z;           // tree solver selected inverse
+    double* r;           // residual / forward-solve vector (N, FP64 (complex))
+    double* alpha;       // Lambda^-1 rhat (N, FP64 (complex))
+    double* tau;         // sorted optimal means (T)
+    double* partials;    // per-block partial sums
+    long long partials_len;
+    int* status;
+    double* out_tmp;     // NLL outputs of calls that only need the solve (posterior)
+    long long ws_bytes;
+    bool y_set;
+};
+
+__device__ __forceinline__ void set_status(int* st, int bit) { atomicOr(st, bit); }

@@ -1,0 +1,151 @@
+"""Python binding of the fast multitask GP library: one handle per fit, torch tensors for memory/streams.
+
+Every computation runs in the CUDA library (libmtgp_gb300.so); this module only passes device
+pointers, sizes and the current CUDA stream through the C ABI of include/mtgp.h.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import DNET, FP32_TRANSFORM, FP64, LATTICE, check, lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(x, dtype=torch.float64):
+    t = torch.as_tensor(x, dtype=dtype)
+    if not t.is_cuda:
+        t = t.cuda()
+    return t.contiguous()
+
+
+class MTGP:
+    """A fast-MTGP fit: design (lattice or digital net), per-task shifts, task sizes 2^m_t.
+
+    ``gen``: lattice -- (d,) generating vector words; digital net -- (d, gen_cols) column words.
+    ``shift``: (T, d) words.  ``precision``: "fp64" or "fp32" (FP32 kernel-column transforms).
+    """
+
+    def __init__(self, kind: str, d: int, m, gen, shift, precision: str = "fp64"):
+        self.kind = LATTICE if kind == "lattice" else DNET
+        self.d = int(d)
+        self.m = [int(x) for x in m]
+        self.T = len(self.m)
+        self.N = sum(1 << x for x in self.m)
+        gen = np.ascontiguousarray(np.asarray(gen, dtype=np.uint32))
+        shift = np.ascontiguousarray(np.asarray(shift, dtype=np.uint32).reshape(self.T, self.d))
+        gen_cols = int(gen.shape[1]) if (self.kind == DNET and gen.ndim == 2) else 0
+        m_arr = (ctypes.c_int * self.T)(*self.m)
+        h = ctypes.c_void_p()
+        prec = FP32_TRANSFORM if precision == "fp32" else FP64
+        check(lib().mtgp_create(ctypes.byref(h), self.kind, self.d, self.T, m_arr,
+                                gen.ctypes.data_as(ctypes.c_void_p), gen_cols,
+                                shift.ctypes.data_as(ctypes.c_void_p), prec), "mtgp_create")
+        self._h = h
+        self.precision = precision
+
+    @classmethod
+    def from_problem(cls, p, precision=None):
+        prec = precision or ("fp32" if p.fp32_transform else "fp64")
+        return cls(p.kind, p.d, p.m, p.gen, p.shift, prec)
+
+    # ------------------------------------------------------------------ calls
+    def points(self, stream=None) -> torch.Tensor:
+        """(N, d) int32 tensor holding the uint32 fixed-point words of the design points."""
+        x = torch.empty((self.N, self.d), dtype=torch.int32, device="cuda")
+        check(lib().mtgp_points(self._h, _ptr(x), _stream(stream)), "mtgp_points")
+        return x
+
+    def set_y(self, y, stream=None) -> None:
+        y = _dev(y)
+        assert y.numel() == self.N
+        self._y = y
+        check(lib().mtgp_set_y(self._h, _ptr(y), _stream(stream)), "mtgp_set_y")
+
+    def _theta(self, eta, W, v, sigma2):
+        eta = _dev(eta).reshape(-1)
+        W = _dev(W).reshape(self.T, -1)
+        v = _dev(v).reshape(-1)
+        s2 = _dev(sigma2).reshape(1)
+        return eta, W, v, s2
+
+    def nll(self, eta, W, v, sigma2, stream=None):
+        """Returns (out, tau): out = [NLL, quad, logdet] (device float64), tau (T,)."""
+        eta, W, v, s2 = self._theta(eta, W, v, sigma2)
+        out = torch.empty(3, dtype=torch.float64, device="cuda")
+        tau = torch.empty(self.T, dtype=torch.float64, device="cuda")
+        check(lib().mtgp_nll(self._h, _ptr(eta), _ptr(W), W.shape[1], _ptr(v), _ptr(s2), _ptr(out), _ptr(tau),
+                             _stream(stream)), "mtgp_nll")
+        return out, tau
+
+    def nll_grad(self, eta, W, v, sigma2, stream=None, outs=None):
+        """Returns (out, tau, g_eta, g_W, g_v, g_sigma2) with gradients of the NLL."""
+        eta, W, v, s2 = self._theta(eta, W, v, sigma2)
+        if outs is None:
+            outs = (torch.empty(3, dtype=torch.float64, device="cuda"),
+                    torch.empty(self.T, dtype=torch.float64, device="cuda"),
+                    torch.empty(self.d, dtype=torch.float64, device="cuda"),
+                    torch.empty_like(W), torch.empty(self.T, dtype=torch.float64, device="cuda"),
+                    torch.empty(1, dtype=torch.float64, device="cuda"))
+        out, tau, ge, gW, gv, gs = outs
+        check(lib().mtgp_nll_grad(self._h, _ptr(eta), _ptr(W), W.shape[1], _ptr(v), _ptr(s2), _ptr(out), _ptr(tau),
+                                  _ptr(ge), _ptr(gW), _ptr(gv), _ptr(gs), _stream(stream)), "mtgp_nll_grad")
+        return outs
+
+    def posterior(self, eta, W, v, sigma2, xq, task, variance=True, stream=None):
+        eta, W, v, s2 = self._theta(eta, W, v, sigma2)
+        xq = _dev(xq).reshape(-1, self.d)
+        task = _dev(task, torch.int32).reshape(-1)
+        nq = xq.shape[0]
+        mean = torch.empty(nq, dtype=torch.float64, device="cuda")
+        var = torch.empty(nq, dtype=torch.float64, device="cuda") if variance else None
+        check(lib().mtgp_posterior(self._h, _ptr(eta), _ptr(W), W.shape[1], _ptr(v), _ptr(s2), nq, _ptr(xq),
+                                   _ptr(task), _ptr(mean), _ptr(var), _stream(stream)), "mtgp_posterior")
+        return mean, var
+
+    def sync(self, stream=None) -> None:
+        check(lib().mtgp_sync(self._h, _stream(stream)), "mtgp_sync")
+
+    def workspace_bytes(self) -> int:
+        return int(lib().mtgp_workspace_bytes(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            check(lib().mtgp_destroy(self._h), "mtgp_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class NLLFunction(torch.autograd.Function):
+    """NLL as a differentiable function of (eta, W, v, sigma2) through the hand-written adjoint."""
+
+    @staticmethod
+    def forward(ctx, model: MTGP, eta, W, v, sigma2):
+        out, tau, ge, gW, gv, gs = model.nll_grad(eta, W, v, sigma2)
+        ctx.save_for_backward(ge, gW.reshape(W.shape), gv, gs.reshape(sigma2.shape))
+        return out[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        ge, gW, gv, gs = ctx.saved_tensors
+        return None, g * ge, g * gW, g * gv, g * gs
+
+
+def nll(model: MTGP, eta, W, v, sigma2):
+    return NLLFunction.apply(model, eta, W, v, sigma2)

@@ -1,0 +1,224 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on identical seeded inputs.
+
+Tolerances: NLL within 1e-8 relative in FP64 mode and 1e-5 in FP32-transform mode.  Gradients:
+within 1e-7 (FP64) / 1e-4 (FP32) of the gradient's max-norm scale.  Posterior: |delta mean| and
+|delta var| within 1e-8 (FP64) / 1e-5 (FP32) of the largest prior variance R_tt Q(x, x).
+FP32-transform mode is exercised on digital nets, the designs it is specified for: the SI lattice
+spectrum decays like f^-4 and falls below FP32 transform noise (precision modes).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import dense, design, spectral  # noqa: E402
+from paper_2603_16014_gb300 import inputs  # noqa: E402
+
+TOL_NLL = {"fp64": 1e-8, "fp32": 1e-5}
+TOL_GRAD = {"fp64": 1e-7, "fp32": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2603_16014_gb300 import build
+    build.build()
+
+
+def _model(p, precision):
+    from paper_2603_16014_gb300.mtgp import MTGP
+    return MTGP.from_problem(p, precision)
+
+
+def _points_oracle(p):
+    return dense.all_points(p.kind, p.gen, p.shift, p.m)
+
+
+SMALL = [
+    ("lattice", 2, (5, 5)), ("dnet", 3, (6, 6, 6)), ("lattice", 2, (6, 4, 3)), ("dnet", 2, (7, 5, 5, 3)),
+    ("lattice", 3, (3, 6, 4)), ("dnet", 2, (4, 0)), ("lattice", 2, (0, 0)), ("lattice", 1, (7,)),
+    ("dnet", 4, (6,)), ("dnet", 2, (3,) * 8), ("lattice", 2, (2, 2, 2, 2, 2)), ("dnet", 3, (5, 5, 3, 3)),
+]
+
+
+@pytest.mark.parametrize("kind,d,m", SMALL)
+def test_points_bit_exact(kind, d, m):
+    p = inputs.make_problem(kind, d, m, seed=41)
+    model = _model(p, "fp64")
+    got = model.points().cpu().numpy().view(np.uint32)
+    ref = np.concatenate(_points_oracle(p))
+    assert np.array_equal(got, ref)
+
+
+CASES = [(k, d, m, "fp64") for (k, d, m) in SMALL] + [(k, d, m, "fp32") for (k, d, m) in SMALL if k == "dnet"]
+
+
+@pytest.mark.parametrize("kind,d,m,precision", CASES)
+def test_nll_and_grad_vs_dense_oracle(kind, d, m, precision):
+    p = inputs.make_problem(kind, d, m, seed=43, eta=0.6, v=0.1, sigma2=1e-4, s=min(2, len(m)))
+    X = _points_oracle(p)
+    y = inputs.synth_y(p, X)
+    ref, g_eta, g_W, g_v, g_s2 = dense.nll_grad(kind, X, y, p.eta, p.W, p.v, p.sigma2)
+    model = _model(p, precision)
+    model.set_y(torch.from_numpy(y))
+    out, tau, ge, gW, gv, gs = model.nll_grad(p.eta, p.W, p.v, p.sigma2)
+    model.sync()
+    out = out.cpu().numpy()
+    tol = TOL_NLL[precision]
+    assert abs(out[0] - ref["nll"]) <= tol * abs(ref["nll"]), (out[0], ref["nll"])
+    assert abs(out[1] + out[2] - ref["L"]) <= tol * max(abs(ref["quad"]) + abs(ref["logdet"]), 1.0)
+    assert np.allclose(tau.cpu().numpy(), ref["tau"], rtol=0, atol=10 * tol * (1 + np.abs(ref["tau"]).max()))
+    gref = np.concatenate([0.5 * g_eta, 0.5 * g_W.ravel(), 0.5 * g_v, [0.5 * g_s2]])
+    got = np.concatenate([ge.cpu().numpy(), gW.cpu().numpy().ravel(), gv.cpu().numpy(), gs.cpu().numpy()])
+    scale = 1.0 + np.abs(gref).max()
+    err = np.abs(got - gref).max()
+    assert err <= TOL_GRAD[precision] * scale, (err, scale, got, gref)
+    # NLL-only entry point agrees with the NLL of the gradient call
+    out2, tau2 = model.nll(p.eta, p.W, p.v, p.sigma2)
+    model.sync()
+    assert abs(out2.cpu().numpy()[0] - out[0]) <= 1e-12 * abs(out[0])
+
+
+@pytest.mark.parametrize("kind,d,m,precision", [("lattice", 2, (6, 6), "fp64"), ("dnet", 3, (5, 5, 5), "fp64"),
+                                                ("lattice", 2, (6, 4, 3), "fp64"), ("dnet", 2, (6, 3), "fp64"),
+                                                ("dnet", 3, (5, 5, 5), "fp32"), ("dnet", 2, (6, 3), "fp32")])
+def test_posterior_vs_dense_oracle(kind, d, m, precision):
+    p = inputs.make_problem(kind, d, m, seed=47, eta=0.6, v=0.1, sigma2=1e-4)
+    X = _points_oracle(p)
+    y = inputs.synth_y(p, X)
+    Xq, xq, tq = inputs.query_points(37, d, seed=5, tasks=len(m))
+    mean_ref, var_ref, prior = dense.posterior(kind, X, y, p.eta, p.W, p.v, p.sigma2, Xq, tq)
+    model = _model(p, precision)
+    model.set_y(torch.from_numpy(y))
+    equal = len(set(m)) == 1
+    mean, var = model.posterior(p.eta, p.W, p.v, p.sigma2, torch.from_numpy(xq), torch.from_numpy(tq), variance=equal)
+    model.sync()
+    tol = TOL_NLL[precision]
+    assert np.allclose(mean.cpu().numpy(), mean_ref, rtol=0, atol=tol * prior.max())
+    if equal:
+        assert np.allclose(var.cpu().numpy(), var_ref, rtol=0, atol=tol * prior.max())
+
+
+def test_errors_surface_through_status():
+    p = inputs.make_problem("dnet", 2, (5, 5), seed=3, sigma2=1e-4)
+    from paper_2603_16014_gb300._lib import MTGPError
+    model = _model(p, "fp64")
+    with pytest.raises(MTGPError):                 # NLL before set_y
+        model.nll(p.eta, p.W, p.v, p.sigma2)
+    y = np.zeros(p.N)
+    y[3] = np.nan
+    model.set_y(torch.from_numpy(y))
+    with pytest.raises(MTGPError) as ei:
+        model.sync()
+    assert ei.value.code == 3                       # MTGP_ERR_NUMERIC
+    model.set_y(torch.zeros(p.N, dtype=torch.float64))
+    model.sync()
+    # an indefinite task covariance (v < 0 and W = 0) makes a pivot negative
+    with pytest.raises(MTGPError):
+        model.nll(p.eta, np.zeros_like(p.W), -np.ones(p.T), 1e-6)
+        model.sync()
+    model.sync()
+    # unequal sizes: variance not supported in this build, mean is
+    q = inputs.make_problem("dnet", 2, (5, 3), seed=3)
+    mq = _model(q, "fp64")
+    mq.set_y(torch.zeros(q.N, dtype=torch.float64))
+    with pytest.raises(MTGPError) as ei:
+        mq.posterior(q.eta, q.W, q.v, q.sigma2, torch.zeros(4, 2, dtype=torch.float64), torch.zeros(4, dtype=torch.int32))
+    assert ei.value.code == 5
+
+
+# ----------------------------------------------------------------------------- full sizes
+
+def test_full_lattice_d2_T2_n1024_vs_dense():
+    p = inputs.lattice_small()
+    X = _points_oracle(p)
+    y = inputs.synth_y(p, X)
+    ref, g_eta, g_W, g_v, g_s2 = dense.nll_grad(p.kind, X, y, p.eta, p.W, p.v, p.sigma2)
+    model = _model(p, "fp64")
+    model.set_y(torch.from_numpy(y))
+    out, tau, ge, gW, gv, gs = model.nll_grad(p.eta, p.W, p.v, p.sigma2)
+    model.sync()
+    assert abs(out[0].item() - ref["nll"]) <= 1e-8 * abs(ref["nll"])
+    gref = np.concatenate([0.5 * g_eta, 0.5 * g_W.ravel(), 0.5 * g_v, [0.5 * g_s2]])
+    got = np.concatenate([ge.cpu().numpy(), gW.cpu().numpy().ravel(), gv.cpu().numpy(), gs.cpu().numpy()])
+    assert np.abs(got - gref).max() <= 1e-7 * (1 + np.abs(gref).max())
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_full_dnet_d8_T4_n65536_vs_spectral_oracle(precision):
+    p = inputs.dnet_equal()
+    X = _points_oracle(p)
+    y = inputs.synth_y(p, X)
+    ref, g_eta, g_W, g_v, g_s2 = spectral.nll_grad_equal(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2)
+    model = _model(p, precision)
+    model.set_y(torch.from_numpy(y))
+    out, tau, ge, gW, gv, gs = model.nll_grad(p.eta, p.W, p.v, p.sigma2)
+    model.sync()
+    assert abs(out[0].item() - ref["nll"]) <= TOL_NLL[precision] * abs(ref["nll"])
+    assert np.allclose(tau.cpu().numpy(), ref["tau"], atol=1e-12)
+    gref = np.concatenate([0.5 * g_eta, 0.5 * g_W.ravel(), 0.5 * g_v, [0.5 * g_s2]])
+    got = np.concatenate([ge.cpu().numpy(), gW.cpu().numpy().ravel(), gv.cpu().numpy(), gs.cpu().numpy()])
+    assert np.abs(got - gref).max() <= TOL_GRAD[precision] * (1 + np.abs(gref).max()), (got, gref)
+    if precision == "fp64":
+        # central differences (sigma2 = 1e-8 moves the NLL below FP64 resolution: checked above only)
+        _check_fd(model, p, ge, gW, gv, gs, idx_eta=[0, 5], idx_W=[(1, 0), (3, 1)], idx_v=[2], nll=out[0].item(),
+                  with_sigma2=False)
+
+
+def _check_fd(model, p, ge, gW, gv, gs, idx_eta, idx_W, idx_v, nll, with_sigma2=True, h=1e-6, rtol=1e-5):
+    """Central differences with step h (relative, in log space, for eta, v, sigma2; absolute for W).
+    Allowed error = rtol (|g| + 1) + roundoff of the difference quotient, 16 eps |NLL| / h."""
+    eps = np.finfo(np.float64).eps
+    rnd = 16 * eps * abs(nll) / h
+
+    def f(eta, W, v, s2):
+        out, _ = model.nll(eta, W, v, s2)
+        return out[0].item()
+
+    def ok(fd, g):
+        return abs(fd - g) <= rtol * (abs(g) + 1) + rnd
+    for j in idx_eta:
+        e1, e2 = p.eta.copy(), p.eta.copy()
+        e1[j] *= np.exp(h)
+        e2[j] *= np.exp(-h)
+        fd = (f(e1, p.W, p.v, p.sigma2) - f(e2, p.W, p.v, p.sigma2)) / (2 * h) / p.eta[j]
+        assert ok(fd, ge[j].item()), (j, fd, ge[j].item(), rnd)
+    for (t, k) in idx_W:
+        W1, W2 = p.W.copy(), p.W.copy()
+        W1[t, k] += h
+        W2[t, k] -= h
+        fd = (f(p.eta, W1, p.v, p.sigma2) - f(p.eta, W2, p.v, p.sigma2)) / (2 * h)
+        assert ok(fd, gW[t, k].item()), (t, k, fd, gW[t, k].item(), rnd)
+    for t in idx_v:
+        v1, v2 = p.v.copy(), p.v.copy()
+        v1[t] *= np.exp(h)
+        v2[t] *= np.exp(-h)
+        fd = (f(p.eta, p.W, v1, p.sigma2) - f(p.eta, p.W, v2, p.sigma2)) / (2 * h) / p.v[t]
+        assert ok(fd, gv[t].item()), (t, fd, gv[t].item(), rnd)
+    if with_sigma2:
+        fd = (f(p.eta, p.W, p.v, p.sigma2 * np.exp(h)) - f(p.eta, p.W, p.v, p.sigma2 * np.exp(-h))) / (2 * h) / p.sigma2
+        assert abs(fd - gs[0].item()) <= rtol * (abs(gs[0].item()) + 1) + rnd / p.sigma2, (fd, gs[0].item())
+
+
+def test_full_lattice_d16_T5_nested_vs_class_oracle():
+    p = inputs.lattice_nested()
+    X = _points_oracle(p)
+    y = inputs.synth_y(p, X)
+    model = _model(p, "fp64")
+    model.set_y(torch.from_numpy(y))
+    out, tau, ge, gW, gv, gs = model.nll_grad(p.eta, p.W, p.v, p.sigma2)
+    model.sync()
+    ref = spectral.nll_by_class(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2)
+    assert abs(out[0].item() - ref["nll"]) <= 1e-8 * abs(ref["nll"]), (out[0].item(), ref["nll"])
+    assert np.allclose(tau.cpu().numpy(), ref["tau"], atol=1e-8 * (1 + np.abs(ref["tau"]).max()))
+    nll = out[0].item()
+    allW = [(t, k) for t in range(5) for k in range(2)]
+    # the finite-difference step of the workload definition (1e-6) ...
+    _check_fd(model, p, ge, gW, gv, gs, idx_eta=list(range(16)), idx_W=allW, idx_v=list(range(5)), nll=nll,
+              with_sigma2=False)
+    # ... and a tighter check at a step where truncation (h^2) and roundoff (1/h) are both small
+    _check_fd(model, p, ge, gW, gv, gs, idx_eta=list(range(16)), idx_W=allW, idx_v=list(range(5)), nll=nll,
+              with_sigma2=True, h=1e-4, rtol=1e-6)

@@ -174,3 +174,16 @@ def test_posterior_by_class_matches_dense(kind, m):
     mean_s, var_s = spectral.posterior_by_class(kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2, Xq, tq)
     assert np.allclose(mean_s, mean_d, atol=1e-9)
     assert np.allclose(var_s, var_d, atol=1e-9)
+
+
+@pytest.mark.parametrize("kind,m,d", [("lattice", (5, 5), 2), ("dnet", (4, 4, 4), 3), ("dnet", (6,), 2),
+                                      ("lattice", (3, 3, 3, 3), 1)])
+def test_equal_spectral_gradient_matches_dense(kind, m, d):
+    p = inputs.make_problem(kind, d, m, seed=31, eta=0.7, v=0.2, sigma2=1e-3, s=min(2, len(m)))
+    X = dense.all_points(kind, p.gen, p.shift, p.m)
+    y = inputs.synth_y(p, X)
+    ref = dense.nll_grad(kind, X, y, p.eta, p.W, p.v, p.sigma2)
+    got = spectral.nll_grad_equal(kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2)
+    assert abs(got[0]["L"] - ref[0]["L"]) < 1e-9 * abs(ref[0]["L"])
+    for a, b in zip(got[1:], ref[1:]):
+        assert np.allclose(a, b, rtol=1e-8, atol=1e-8 * (1 + np.abs(np.asarray(ref[1])).max()))
