@@ -1,0 +1,373 @@
+"""Benchmark: exact fast-MTGP NLL + gradient evaluations per second on GB300.
+
+Workload (default): digital net, d=8, T=4 tasks, n=2^16 points per task (N=262144), order-2
+digitally-shift-invariant kernel, W 4x2, v=0.05, sigma2=1e-8, FP32 kernel-column transforms and
+FP64 per-frequency solves.  One step = one NLL + gradient evaluation through the C ABI (kernel
+columns, transforms, per-frequency FP64 solves, adjoint transforms, eta-gradient pass).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs independent replicas (one fit per rank, no collective in the data path) under torchrun.
+The inputs (4 MB) are far below L2 (129 MB), so L2 is flushed (256 MB write) between timed steps.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "NLL+grad evals/s (T=4, N=4·2^16) vs plain; % HBM peak; fit time w/ proposal"
+UNIT = "evals/s"
+WORKLOAD = "dnet_d8_T4_n2^16_nll_grad"
+FP64_PEAK_TFLOPS = 1.25       # GB300 dense FP64, nominal
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu", action="store_true",
+                    help="only warm-up + K steps of the workload, no extras (for ncu captures)")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+# ----------------------------------------------------------------------------- FP64 work model
+
+def solve_flops_per_freq(T: int, cplx: bool, grad: bool) -> int:
+    """FP64 flops of one frequency's solve (factor, log-det product, forward solve and, with the
+    gradient, backward solve, unit-lower inverse, G = Lambda^-1 - alpha alpha^H and contractions),
+    counted from the recurrences: real add/mul = 1, complex add = 2, complex mul = 6,
+    real*complex = 2, |z|^2 = 3 (1 for reals), reciprocal = 1."""
+    A, M, S, N2 = (2, 6, 2, 3) if cplx else (1, 1, 1, 1)
+    f = 0
+    for k in range(T):
+        f += 2 + k * (N2 + 2) + 1                        # D_k and 1/D_k
+        for _ in range(k + 1, T):
+            f += S + k * (M + S + A) + S                 # L[i][k]
+    f += T                                               # pivot product
+    for k in range(T):
+        f += k * (M + A) + N2 + 2                        # forward solve + quad
+    if not grad:
+        return f
+    for k in range(T):
+        f += S + (T - 1 - k) * (M + A)                   # alpha
+    for j in range(T):
+        for i in range(j + 1, T):
+            f += (i - j - 1) * (M + A)                   # L^-1
+    for t in range(T):
+        for u in range(t, T):
+            if u == t:
+                f += 1 + (T - 1 - u) * (N2 + 2) + (M + A) + 1 + 2 + 3
+            else:
+                f += S + (T - 1 - u) * (M + S + A) + (M + A) + (M + 1) + (S + 1)
+    return f
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self, index: int):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- workload
+
+def make_workload(seed: int = 0):
+    import numpy as np
+    import torch
+
+    from paper_2603_16014_gb300 import inputs
+    from paper_2603_16014_gb300.mtgp import MTGP
+
+    p = inputs.dnet_equal(seed=seed)
+    model = MTGP.from_problem(p, "fp32")
+    X = model.points().cpu().numpy().view(np.uint32)
+    offs = np.concatenate([[0], np.cumsum(p.n)])
+    y = inputs.synth_y(p, [X[offs[t]:offs[t + 1]] for t in range(p.T)])
+    model.set_y(torch.from_numpy(y))
+    model.sync()
+    return p, model, y
+
+
+def cpu_baseline(seconds: float = 10.0):
+    """The oracle (spectral FP64, numpy) on full NLL + gradient evaluations of the same workload."""
+    import numpy as np
+
+    from oracle import dense, spectral
+    from paper_2603_16014_gb300 import inputs
+
+    p = inputs.dnet_equal()
+    X = dense.all_points(p.kind, p.gen, p.shift, p.m)
+    y = inputs.synth_y(p, X)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        spectral.nll_grad_equal(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and reps >= 2:
+            break
+    return {"value": reps / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{reps} full NLL+gradient evaluations of {WORKLOAD} (FP64 numpy spectral oracle), {el:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- ours
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    p, model, y = make_workload(seed=rank)
+    th = [torch.as_tensor(a, dtype=torch.float64).cuda().contiguous() for a in (p.eta, p.W, p.v, [p.sigma2])]
+    outs = model.nll_grad(*th)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 3)):
+        model.nll_grad(*th, outs=outs)
+        flush.fill_(1.0)
+    model.sync()
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = ClockSampler()
+    if rank == 0:
+        clocks.start(torch.cuda.current_device())
+        time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(K):
+        ev[i][0].record(stream)
+        model.nll_grad(*th, outs=outs)
+        ev[i][1].record(stream)
+        flush.fill_(float(i))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total = torch.tensor([sum(step_ms)], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(total, op=dist.ReduceOp.MAX)
+    clk = clocks.stop() if rank == 0 else None
+    model.sync()
+    ms_per_step = total.item() / K
+    value = world * K / (total.item() / 1e3)
+
+    # ---- end to end through the public API: theta from pinned host memory, results back to host
+    h_theta = [torch.as_tensor(a, dtype=torch.float64).reshape(-1).pin_memory() for a in (p.eta, p.W, p.v, [p.sigma2])]
+    h_out = [torch.empty(o.numel(), dtype=torch.float64).pin_memory() for o in outs]
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize()
+    for i in range(K):
+        e2e_ev[i][0].record(stream)
+        for d_t, h_t in zip(th, h_theta):
+            d_t.view(-1).copy_(h_t, non_blocking=True)
+        model.nll_grad(*th, outs=outs)
+        for h_o, d_o in zip(h_out, outs):
+            h_o.copy_(d_o.view(-1), non_blocking=True)
+        e2e_ev[i][1].record(stream)
+        stream.synchronize()
+        flush.fill_(float(i))
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev)
+    e2e_total = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(e2e_total, op=dist.ReduceOp.MAX)
+    h2d = sum(h.numel() * 8 for h in h_theta)
+    d2h = sum(h.numel() * 8 for h in h_out)
+
+    # ---- per-kernel times (CUDA events on the launching stream) for the roofline
+    model.profile(True)
+    P = min(K, 20)
+    for i in range(P):
+        model.nll_grad(*th, outs=outs)
+        flush.fill_(float(i))
+    prof = model.profile_read()
+    model.profile(False)
+    model.sync()
+    launches_per_step = sum(c for (_, c) in prof.values()) // P + 1     # + theta check kernel
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_cnt) = dom[0], dom[1]
+    dom_avg_s = dom_ms / dom_cnt / 1e3
+    n, T = p.n[0], p.T
+    C = 1 + T * (T - 1) // 2
+    peaks = measured_peaks()
+    if dom_name == "fused_b":
+        flops = n * solve_flops_per_freq(T, False, True)
+        achieved = flops / dom_avg_s / 1e12
+        roof = {"bound": "alu", "kernel": "k_fused_b (transform stages a..m-1 + FP64 per-frequency solve + adjoint stages)",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "flops_per_launch": flops, "avg_launch_us": dom_avg_s * 1e6,
+                "peak_source": "GB300 dense FP64 nominal (1.25 TFLOP/s); FMA probe measured 1.20"}
+    else:
+        bytes_ = n * (8 * T + 4 * C * 4)
+        achieved = bytes_ / dom_avg_s / 1e9
+        roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "avg_launch_us": dom_avg_s * 1e6}
+    roof["kernels_us_per_step"] = {k: v[0] / v[1] * 1e3 for k, v in prof.items()}
+    # the whole step against the HBM roofline of its algorithmic bytes (two-pass transform model)
+    step_bytes = n * (8 * T + 2 * C * 4 + 2 * C * 4)
+    roof["step_hbm_view"] = {"algorithmic_bytes": step_bytes, "achieved_gbs": step_bytes / (ms_per_step / 1e3) / 1e9,
+                             "peak_gbs": peaks["hbm_gbs"], "frac": step_bytes / (ms_per_step / 1e3) / 1e9 / peaks["hbm_gbs"]}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 transforms, f64 solves", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "kind": "digital net", "d": p.d, "T": T, "n_per_task": n, "N": p.N,
+                   "precision": "FP32 transforms / FP64 per-frequency solves", "l2": "flushed (256 MB write) between steps",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "e2e": {"value": world * K / (e2e_total.item() / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * K,
+        "roofline": roof,
+        "clocks": clk,
+        "nll": outs[0][0].item(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_ncu_case(args):
+    """W warm-up then K steps, nothing else: 1 + 3 kernels per step (theta check, fused A, B, C)."""
+    import torch
+
+    p, model, y = make_workload()
+    th = [torch.as_tensor(a, dtype=torch.float64).cuda().contiguous() for a in (p.eta, p.W, p.v, [p.sigma2])]
+    outs = model.nll_grad(*th)
+    for _ in range(args.warmup + args.steps):
+        model.nll_grad(*th, outs=outs)
+    model.sync()
+    torch.cuda.synchronize()
+    print(json.dumps({"nll": outs[0][0].item(), "steps": args.steps, "warmup": args.warmup}))
+
+
+# ----------------------------------------------------------------------------- reference (oracle)
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import dense, spectral
+    from paper_2603_16014_gb300 import inputs
+
+    p = inputs.dnet_equal()
+    X = dense.all_points(p.kind, p.gen, p.shift, p.m)
+    y = inputs.synth_y(p, X)
+    for _ in range(args.warmup):
+        spectral.nll_grad_equal(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        out = spectral.nll_grad_equal(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2)
+    el = time.perf_counter() - t0
+    value = args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "kind": "digital net", "d": p.d, "T": p.T, "n_per_task": p.n[0], "N": p.N,
+                   "precision": "FP64 (CPU oracle)", "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"{args.steps} full NLL+gradient evaluations of {WORKLOAD}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "nll": out[0]["nll"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if local_rank == 0:
+        from paper_2603_16014_gb300 import build
+        build.build()
+    if args.ncu:
+        run_ncu_case(args)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

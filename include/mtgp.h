@@ -135,6 +135,18 @@ int mtgp_sync(mtgp_t* h, cudaStream_t stream);
 /* mtgp_last_error_string -- description of the calling thread's last host-side error. */
 const char* mtgp_last_error_string(void);
 
+/*
+ * mtgp_profile -- enable (1) or disable (0) kernel timing on the handle.  When enabled, every kernel
+ * the handle launches is bracketed by CUDA events on the call's stream (adds two event records per
+ * launch; off by default).
+ * mtgp_profile_read -- synchronise on the recorded events, aggregate by kernel name and clear the log.
+ *   names     host, max_entries x 32 chars (NUL-terminated kernel names)
+ *   total_ms  host, max_entries doubles: summed duration per name;  counts: launches per name
+ *   n_out     number of distinct names (may exceed max_entries; only the first max_entries are written)
+ */
+int mtgp_profile(mtgp_t* h, int enable);
+int mtgp_profile_read(mtgp_t* h, int max_entries, char* names, double* total_ms, int* counts, int* n_out);
+
 /* mtgp_workspace_bytes -- device bytes the handle holds (for capacity planning). */
 long long mtgp_workspace_bytes(const mtgp_t* h);
 

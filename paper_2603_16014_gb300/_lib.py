@@ -34,6 +34,8 @@ _SIGS = {
     "mtgp_sync": (_i, [_p, _p]),
     "mtgp_last_error_string": (ctypes.c_char_p, []),
     "mtgp_workspace_bytes": (ctypes.c_longlong, [_p]),
+    "mtgp_profile": (_i, [_p, _i]),
+    "mtgp_profile_read": (_i, [_p, _i, _p, _p, _p, _p]),
 }
 
 _LIB = None

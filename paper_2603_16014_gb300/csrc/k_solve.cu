@@ -15,55 +15,14 @@
 //
 // Gradient (tau held at its optimum): dL = sum over pattern G_{ji} dLambda_{ij},
 //   G = Lambda^-1 - alpha alpha^H, alpha = Lambda^-1 rhat.
-#include <type_traits>
-
-#include "mtgp_internal.cuh"
+#include "freq_solve.cuh"
 
 namespace {
 
-template <bool CPLX>
-using Vt = typename std::conditional<CPLX, cx<double>, double>::type;
-
-__device__ __forceinline__ double vmul(double a, double b) { return a * b; }
-__device__ __forceinline__ cx<double> vmul(cx<double> a, cx<double> b) { return a * b; }
-__device__ __forceinline__ double vscale(double a, double s) { return a * s; }
-__device__ __forceinline__ cx<double> vscale(cx<double> a, double s) { return mk(a.re * s, a.im * s); }
-__device__ __forceinline__ double vadd(double a, double b) { return a + b; }
-__device__ __forceinline__ cx<double> vadd(cx<double> a, cx<double> b) { return a + b; }
-__device__ __forceinline__ double vsub(double a, double b) { return a - b; }
-__device__ __forceinline__ cx<double> vsub(cx<double> a, cx<double> b) { return a - b; }
-
 template <typename S, bool CPLX>
-__device__ __forceinline__ Vt<CPLX> load_spec(const void* p, long long i) {
-    if constexpr (CPLX) {
-        cx<S> v = reinterpret_cast<const cx<S>*>(p)[i];
-        return mk((double)v.re, (double)v.im);
-    } else {
-        return (double)reinterpret_cast<const S*>(p)[i];
-    }
-}
+__device__ __forceinline__ Vt<CPLX> load_spec(const void* p, long long i) { return load_elem<S, CPLX>(p, i); }
 template <typename S, bool CPLX>
-__device__ __forceinline__ void store_spec(void* p, long long i, Vt<CPLX> v) {
-    if constexpr (CPLX) {
-        reinterpret_cast<cx<S>*>(p)[i] = mk((S)v.re, (S)v.im);
-    } else {
-        reinterpret_cast<S*>(p)[i] = (S)v;
-    }
-}
-template <bool CPLX>
-__device__ __forceinline__ Vt<CPLX> ld(const double* p, long long i) {
-    if constexpr (CPLX) return mk(p[2 * i], p[2 * i + 1]);
-    else return p[i];
-}
-template <bool CPLX>
-__device__ __forceinline__ void st(double* p, long long i, Vt<CPLX> v) {
-    if constexpr (CPLX) {
-        p[2 * i] = v.re;
-        p[2 * i + 1] = v.im;
-    } else {
-        p[i] = v;
-    }
-}
+__device__ __forceinline__ void store_spec(void* p, long long i, Vt<CPLX> v) { store_elem<S, CPLX>(p, i, v); }
 
 struct SolveParams {
     int T, s, nT;
@@ -107,120 +66,31 @@ k_solve_equal(const void* spec, void* wgt, const double* yhat, SolveParams p, Th
     double acc[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+    LogAcc lacc;
+    lacc.init();
     int bad = 0;
     for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < n; f += (long long)gridDim.x * blockDim.x) {
-        V mu[T][T];  // mu[t][u] for t <= u
-        V lam[T][T];
+        V mu[T][T], w[T][T], al[T], rh[T];
 #pragma unroll
         for (int t = 0; t < T; ++t) {
 #pragma unroll
-            for (int u = t; u < T; ++u) {
-                int c = p.colidx[t][u];
-                mu[t][u] = load_spec<S, CPLX>(spec, p.coloff[c] + f);
-            }
+            for (int u = t; u < T; ++u) mu[t][u] = load_spec<S, CPLX>(spec, p.coloff[p.colidx[t][u]] + f);
+            rh[t] = (f == 0) ? czero<V>() : ld<CPLX>(yhat, p.yoff[t] + f);
         }
-        double mu0 = creal(mu[0][0]);
-        double ind0 = 1.0;
-        if (p.clamp && mu0 < 0.0) {
-            mu0 = 0.0;
-            ind0 = 0.0;
+        solve_freq<T, CPLX>(mu, rh, sR, sig, p.clamp != 0, p.grad != 0, lacc, acc, w, al, p.store_alpha != 0, bad);
+        if (p.store_alpha) {
+#pragma unroll
+            for (int k = 0; k < T; ++k) st<CPLX>(alpha_out, p.yoff[k] + f, al[k]);
         }
+        if (p.grad) {
 #pragma unroll
-        for (int i = 0; i < T; ++i) {
-            lam[i][i] = cfromreal<V>(sR[i * T + i] * mu0 + sig);
+            for (int t = 0; t < T; ++t)
 #pragma unroll
-            for (int j = 0; j < i; ++j) lam[i][j] = vscale(cconj(mu[j][i]), sR[j * T + i]);
-        }
-        // L D L^H
-        double D[T];
-        V L[T][T];
-#pragma unroll
-        for (int k = 0; k < T; ++k) {
-            double dk = creal(lam[k][k]);
-#pragma unroll
-            for (int j = 0; j < k; ++j) dk -= cabs2(L[k][j]) * D[j];
-            if (!(dk > 0.0) || !isfinite(dk)) {
-                bad = 1;
-                dk = 1.0;
-            }
-            D[k] = dk;
-            double inv = 1.0 / dk;
-#pragma unroll
-            for (int i = k + 1; i < T; ++i) {
-                V a = lam[i][k];
-#pragma unroll
-                for (int j = 0; j < k; ++j) a = vsub(a, vscale(vmul(L[i][j], cconj(L[k][j])), D[j]));
-                L[i][k] = vscale(a, inv);
-            }
-        }
-        double prodD = 1.0;
-#pragma unroll
-        for (int k = 0; k < T; ++k) prodD *= D[k];
-        acc[0] += log(prodD);
-        // forward solve with rhat (rhat(0) = 0: tau = sample means)
-        V u[T];
-#pragma unroll
-        for (int k = 0; k < T; ++k) {
-            V r = (f == 0) ? czero<V>() : ld<CPLX>(yhat, p.yoff[k] + f);
-#pragma unroll
-            for (int j = 0; j < k; ++j) r = vsub(r, vmul(L[k][j], u[j]));
-            u[k] = r;
-            acc[1] += cabs2(r) / D[k];
-        }
-        if (p.grad || p.store_alpha) {
-            V al[T];
-#pragma unroll
-            for (int k = T - 1; k >= 0; --k) {
-                V a = vscale(u[k], 1.0 / D[k]);
-#pragma unroll
-                for (int i = k + 1; i < T; ++i) a = vsub(a, vmul(cconj(L[i][k]), al[i]));
-                al[k] = a;
-            }
-            if (p.store_alpha) {
-#pragma unroll
-                for (int k = 0; k < T; ++k) st<CPLX>(alpha_out, p.yoff[k] + f, al[k]);
-            }
-            if (p.grad) {
-                // Linv = L^-1 (unit lower), Z = Linv^H D^-1 Linv (lower part), G = Z - alpha alpha^H
-                V Li[T][T];
-#pragma unroll
-                for (int j = 0; j < T; ++j) {
-                    Li[j][j] = cfromreal<V>(1.0);
-#pragma unroll
-                    for (int i = j + 1; i < T; ++i) {
-                        V a = czero<V>();
-#pragma unroll
-                        for (int k = j; k < i; ++k) a = vsub(a, vmul(L[i][k], Li[k][j]));
-                        Li[i][j] = a;
-                    }
-                }
-                double wdiag = 0.0;
-                int q = 3;
-#pragma unroll
-                for (int t = 0; t < T; ++t) {
-#pragma unroll
-                    for (int uu = t; uu < T; ++uu) {
-                        // G[uu][t] (uu >= t)
-                        V z = czero<V>();
-#pragma unroll
-                        for (int k = uu; k < T; ++k) z = vadd(z, vscale(vmul(cconj(Li[k][uu]), Li[k][t]), 1.0 / D[k]));
-                        V g = vsub(z, vmul(al[uu], cconj(al[t])));
-                        if (uu == t) {
-                            double gd = creal(g);
-                            acc[2] += gd;
-                            acc[q] += gd * mu0;
-                            wdiag += sR[t * T + t] * gd;
-                        } else {
-                            acc[q] += creal(vmul(g, mu[t][uu]));
-                            store_spec<S, CPLX>(wgt, p.coloff[p.colidx[t][uu]] + f, vscale(g, 2.0 * sR[t * T + uu]));
-                        }
-                        ++q;
-                    }
-                }
-                store_spec<S, CPLX>(wgt, p.coloff[0] + f, cfromreal<V>(wdiag * ind0));
-            }
+                for (int u = t; u < T; ++u)
+                    if (u != t || t == 0) store_spec<S, CPLX>(wgt, p.coloff[p.colidx[t][u]] + f, w[t][u]);
         }
     }
+    acc[0] = lacc.log_value();
     if (bad) set_status(status, ST_NOT_PD);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -236,7 +106,6 @@ k_solve_equal(const void* spec, void* wgt, const double* yhat, SolveParams p, Th
         partials[(long long)blockIdx.x * NQ + q] = v;
     }
 }
-
 
 // --------------------------------------------------------------------------- tree solver
 

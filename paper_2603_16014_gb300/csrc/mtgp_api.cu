@@ -11,6 +11,44 @@
 
 void posterior_release(const Handle* h);
 
+struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+struct Prof {
+    bool on = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    ProfRec cur{};
+};
+
+static cudaEvent_t prof_event(Prof* p) {
+    if (!p->pool.empty()) {
+        cudaEvent_t e = p->pool.back();
+        p->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void mtgp_prof_begin(const Handle* h, const char* name, cudaStream_t st) {
+    Prof* p = h->prof;
+    if (!p || !p->on) return;
+    p->cur.name = name;
+    p->cur.a = prof_event(p);
+    p->cur.b = prof_event(p);
+    cudaEventRecord(p->cur.a, st);
+}
+
+void mtgp_prof_end(const Handle* h, cudaStream_t st) {
+    Prof* p = h->prof;
+    if (!p || !p->on) return;
+    cudaEventRecord(p->cur.b, st);
+    p->recs.push_back(p->cur);
+}
+
 struct mtgp_s {
     Handle h;
 };
@@ -71,9 +109,18 @@ cudaError_t dalloc(Handle* h, T** p, size_t count) {
 
 void free_all(Handle* h) {
     void* ptrs[] = {h->gen, h->shift, h->cols_dev, h->offs_dev, h->yoffs_dev, h->twid, h->twid32, h->yhat, h->spec,
-                    h->wgt, h->S, h->Z, h->r, h->alpha, h->tau, h->partials, h->status, h->out_tmp};
+                    h->wgt, h->S, h->Z, h->r, h->alpha, h->tau, h->partials, h->status, h->out_tmp, h->counters};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (h->prof) {
+        for (auto& r : h->prof->recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (auto e : h->prof->pool) cudaEventDestroy(e);
+        delete h->prof;
+        h->prof = nullptr;
+    }
 }
 
 int validate_theta(const Handle* h, const double* eta, const double* W, int s, const double* v, const double* sigma2) {
@@ -84,18 +131,30 @@ int validate_theta(const Handle* h, const double* eta, const double* W, int s, c
 
 // NLL (and gradient) at theta; leaves alpha = Lambda^-1 rhat in h->alpha and tau in h->tau.
 int run_nll(Handle* h, ThetaPtrs th, bool grad, double* out, double* tau, double* g_eta, double* g_W, double* g_v,
-            double* g_s2, cudaStream_t st) {
+            double* g_s2, cudaStream_t st, bool store_alpha = false) {
     k_check_theta<<<1, 64, 0, st>>>(th, h->d, h->T, h->status);
+    if (h->equal && fused_supported(h)) {
+        launch_fused(h, th, grad, store_alpha, out, tau, g_eta, g_W, g_v, g_s2, st);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        return MTGP_OK;
+    }
+    mtgp_prof_begin(h, "colgen", st);
     launch_colgen(h, th.eta, h->spec, st);
+    mtgp_prof_end(h, st);
     for (int g = 0; g < h->ngroups; ++g)
         launch_transform(h, h->spec, h->fp32, h->cplx, h->group_m[g], h->offs_dev + h->group_first[g],
                          h->group_count[g], false, st);
     int nsolve;
     if (h->equal) {
+        mtgp_prof_begin(h, "solve_equal", st);
         launch_solve_equal(h, th, grad, h->partials, st);
+        mtgp_prof_end(h, st);
         nsolve = solve_equal_blocks(h);
     } else {
+        mtgp_prof_begin(h, "solve_tree", st);
         launch_solve_tree(h, th, grad, h->partials, st);
+        mtgp_prof_end(h, st);
         nsolve = solve_tree_blocks(h);
     }
     const int NQ = 3 + h->T * (h->T + 1) / 2;
@@ -106,9 +165,13 @@ int run_nll(Handle* h, ThetaPtrs th, bool grad, double* out, double* tau, double
             launch_transform(h, h->wgt, h->fp32, h->cplx, h->group_m[g], h->offs_dev + h->group_first[g],
                              h->group_count[g], true, st);
         neta = eta_grad_blocks(h);
+        mtgp_prof_begin(h, "eta_grad", st);
         launch_eta_grad(h, th.eta, h->wgt, eta_part, neta, st);
+        mtgp_prof_end(h, st);
     }
+    mtgp_prof_begin(h, "finalize", st);
     launch_finalize(h, th, grad, h->partials, nsolve, eta_part, neta, out, tau, g_eta, g_W, g_v, g_s2, st);
+    mtgp_prof_end(h, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return MTGP_OK;
@@ -252,11 +315,15 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
         const int NQ = 3 + T * (T + 1) / 2;
         long long nsolve = h->equal ? solve_equal_blocks(h) : solve_tree_blocks(h);
         h->partials_len = nsolve * NQ + (long long)eta_grad_blocks(h) * d;
+        long long fl = fused_partials_len(h);
+        if (fl > h->partials_len) h->partials_len = fl;
         AL(h->partials, (size_t)h->partials_len);
     }
     AL(h->status, (size_t)1);
     AL(h->out_tmp, (size_t)4);
+    AL(h->counters, (size_t)4);
 #undef AL
+    h->prof = new Prof();
     // upload descriptors
     std::vector<uint32_t> shift_sorted((size_t)T * d);
     for (int t = 0; t < T; ++t)
@@ -270,6 +337,7 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
                cudaMemcpy(h->offs_dev, offs.data(), offs.size() * sizeof(long long), cudaMemcpyHostToDevice) == cudaSuccess &&
                cudaMemcpy(h->yoffs_dev, yoffs.data(), yoffs.size() * sizeof(long long), cudaMemcpyHostToDevice) == cudaSuccess &&
                cudaMemset(h->status, 0, sizeof(int)) == cudaSuccess &&
+               cudaMemset(h->counters, 0, 4 * sizeof(unsigned)) == cudaSuccess &&
                cudaMemset(h->tau, 0, MTGP_TMAX * sizeof(double)) == cudaSuccess;
     if (!okc) {
         free_all(h);
@@ -352,11 +420,51 @@ int mtgp_posterior(mtgp_t* hs, const double* eta, const double* W, int s, const 
     if (nq == 0) return MTGP_OK;
     ThetaPtrs th{eta, W, s, v, sigma2};
     // the solve leaves alpha = Lambda^-1 rhat and tau in the workspace
-    rc = run_nll(h, th, false, h->out_tmp, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    rc = run_nll(h, th, false, h->out_tmp, nullptr, nullptr, nullptr, nullptr, nullptr, st, true);
     if (rc) return rc;
     rc = posterior_run(h, th, nq, xq, task, mean, var, st);
     if (rc) return rc == MTGP_ERR_CUDA ? fail(rc, "posterior scratch allocation failed") : fail(rc, "posterior");
     CK(cudaGetLastError());
+    return MTGP_OK;
+}
+
+int mtgp_profile(mtgp_t* hs, int enable) {
+    if (!hs) return fail(MTGP_ERR_INVALID_ARG, "NULL handle");
+    hs->h.prof->on = enable != 0;
+    return MTGP_OK;
+}
+
+int mtgp_profile_read(mtgp_t* hs, int max_entries, char* names, double* total_ms, int* counts, int* n_out) {
+    if (!hs || !n_out || (max_entries > 0 && (!names || !total_ms || !counts)))
+        return fail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    Prof* p = hs->h.prof;
+    std::vector<std::string> nm;
+    std::vector<double> tot;
+    std::vector<int> cnt;
+    for (auto& r : p->recs) {
+        CK(cudaEventSynchronize(r.b));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        size_t i = 0;
+        while (i < nm.size() && nm[i] != r.name) ++i;
+        if (i == nm.size()) {
+            nm.push_back(r.name);
+            tot.push_back(0.0);
+            cnt.push_back(0);
+        }
+        tot[i] += ms;
+        cnt[i] += 1;
+        p->pool.push_back(r.a);
+        p->pool.push_back(r.b);
+    }
+    p->recs.clear();
+    int n = (int)nm.size();
+    *n_out = n;
+    for (int i = 0; i < n && i < max_entries; ++i) {
+        std::snprintf(names + 32 * i, 32, "%s", nm[i].c_str());
+        total_ms[i] = tot[i];
+        counts[i] = cnt[i];
+    }
     return MTGP_OK;
 }
 

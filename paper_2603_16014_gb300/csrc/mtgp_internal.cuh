@@ -161,6 +161,16 @@ void launch_finalize(const Handle* h, ThetaPtrs th, bool grad, const double* par
                      const double* eta_partials, int neta, double* out, double* tau, double* g_eta,
                      double* g_W, double* g_v, double* g_s2, cudaStream_t st);
 
+// k_fused.cu (equal sizes)
+bool fused_supported(const Handle* h);
+long long fused_partials_len(const Handle* h);
+void launch_fused(const Handle* h, ThetaPtrs th, bool grad, bool store_alpha, double* out, double* tau,
+                  double* g_eta, double* g_W, double* g_v, double* g_s2, cudaStream_t st);
+
+// kernel timing (mtgp_api.cu): no-ops unless profiling is enabled on the handle
+void mtgp_prof_begin(const Handle* h, const char* name, cudaStream_t st);
+void mtgp_prof_end(const Handle* h, cudaStream_t st);
+
 // k_posterior.cu
 int posterior_run(Handle* h, ThetaPtrs th, int nq, const double* xq, const int* task, double* mean,
                   double* var, cudaStream_t st);
@@ -212,6 +222,8 @@ struct Handle {
     long long partials_len;
     int* status;
     double* out_tmp;     // NLL outputs of calls that only need the solve (posterior)
+    unsigned* counters;  // last-block election counters of the fused kernels (reset by the last block)
+    struct Prof* prof;   // kernel timing log (host side)
     long long ws_bytes;
     bool y_set;
 };

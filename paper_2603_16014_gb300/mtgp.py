@@ -117,6 +117,24 @@ class MTGP:
     def sync(self, stream=None) -> None:
         check(lib().mtgp_sync(self._h, _stream(stream)), "mtgp_sync")
 
+    def profile(self, enable: bool) -> None:
+        """Bracket every kernel the handle launches with CUDA events (off by default)."""
+        check(lib().mtgp_profile(self._h, 1 if enable else 0), "mtgp_profile")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total ms, launches)} since the last read; synchronises on the events."""
+        cap = 64
+        names = ctypes.create_string_buffer(32 * cap)
+        ms = (ctypes.c_double * cap)()
+        cnt = (ctypes.c_int * cap)()
+        n = ctypes.c_int()
+        check(lib().mtgp_profile_read(self._h, cap, names, ms, cnt, ctypes.byref(n)), "mtgp_profile_read")
+        out = {}
+        for i in range(min(n.value, cap)):
+            nm = names.raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
+            out[nm] = (ms[i], cnt[i])
+        return out
+
     def workspace_bytes(self) -> int:
         return int(lib().mtgp_workspace_bytes(self._h))
 
