@@ -147,6 +147,33 @@ const char* mtgp_last_error_string(void);
 int mtgp_profile(mtgp_t* h, int enable);
 int mtgp_profile_read(mtgp_t* h, int max_entries, char* names, double* total_ms, int* counts, int* n_out);
 
+/*
+ * mtgp_nll_equal_static -- the NLL of mtgp_nll for one fit with equal task sizes, computed without
+ * allocating any device memory.  The paper has no counterpart: this is a deployment variant for
+ * callers that cannot call cudaMalloc (code where allocation is forbidden or unsafe: inside regions
+ * that must not synchronise the device, allocator callbacks, plugin hosts that own the device heap,
+ * processes that pre-reserved all free memory).  Every intermediate lives in one file-scope device
+ * array of MTGP_STATIC_SCRATCH_BYTES (8 MiB), which each GPU that loads the library holds until
+ * the process exits.
+ *   kind, d, T, gen, gen_cols, shift, precision   as mtgp_create, with every task of size 2^m
+ *                                                 (4 <= m); host arrays.
+ *   y       device, T * 2^m observations (tasks in order, each in radical-inverse order).
+ *   eta, W, s, v, sigma2, out, tau                as mtgp_nll (device pointers; tau may be NULL).
+ *   status  device int or NULL: set to 0 by the call, then to the kernel status bits
+ *           (1 = non-positive pivot, 2 = non-finite value) if any.
+ * Returns MTGP_ERR_INVALID_ARG, with a message in mtgp_last_error_string, for arguments out of
+ * range and for problems whose intermediates exceed the scratch array (checked before any device
+ * work); nothing is allocated on any path.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All calls share the one
+ * array and the call clears what must start at zero: calls whose work overlaps on the GPU (two
+ * streams, two host threads) race and must be serialised by the caller.
+ */
+int mtgp_nll_equal_static(int kind, int d, int T, int m, const uint32_t* gen, int gen_cols,
+                          const uint32_t* shift, int precision, const double* y, const double* eta,
+                          const double* W, int s, const double* v, const double* sigma2, double* out,
+                          double* tau, int* status, cudaStream_t stream);
+
 /* mtgp_workspace_bytes -- device bytes the handle holds (for capacity planning). */
 long long mtgp_workspace_bytes(const mtgp_t* h);
 

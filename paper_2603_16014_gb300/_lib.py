@@ -36,6 +36,7 @@ _SIGS = {
     "mtgp_workspace_bytes": (ctypes.c_longlong, [_p]),
     "mtgp_profile": (_i, [_p, _i]),
     "mtgp_profile_read": (_i, [_p, _i, _p, _p, _p, _p]),
+    "mtgp_nll_equal_static": (_i, [_i, _i, _i, _i, _p, _i, _p, _i, _p, _p, _p, _i, _p, _p, _p, _p, _p, _p]),
 }
 
 _LIB = None

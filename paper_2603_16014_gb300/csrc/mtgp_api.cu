@@ -179,6 +179,8 @@ int run_nll(Handle* h, ThetaPtrs th, bool grad, double* out, double* tau, double
 
 }  // namespace
 
+void mtgp_set_error(const char* msg) { g_err = msg; }
+
 extern "C" {
 
 const char* mtgp_last_error_string(void) { return g_err.c_str(); }

@@ -167,6 +167,9 @@ long long fused_partials_len(const Handle* h);
 void launch_fused(const Handle* h, ThetaPtrs th, bool grad, bool store_alpha, double* out, double* tau,
                   double* g_eta, double* g_W, double* g_v, double* g_s2, cudaStream_t st);
 
+// records the message returned by mtgp_last_error_string for the calling thread (mtgp_api.cu)
+void mtgp_set_error(const char* msg);
+
 // kernel timing (mtgp_api.cu): no-ops unless profiling is enabled on the handle
 void mtgp_prof_begin(const Handle* h, const char* name, cudaStream_t st);
 void mtgp_prof_end(const Handle* h, cudaStream_t st);

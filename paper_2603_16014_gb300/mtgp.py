@@ -150,6 +150,27 @@ class MTGP:
             pass
 
 
+def nll_equal_static(kind: str, d: int, T: int, m: int, gen, shift, y, eta, W, v, sigma2, precision="fp64",
+                     stream=None):
+    """NLL of an equal-size fit through mtgp_nll_equal_static, which allocates no device memory
+    (for callers that cannot call cudaMalloc); returns (out [NLL, quad, logdet], tau, status)."""
+    k = LATTICE if kind == "lattice" else DNET
+    gen = np.ascontiguousarray(np.asarray(gen, dtype=np.uint32))
+    shift = np.ascontiguousarray(np.asarray(shift, dtype=np.uint32).reshape(T, d))
+    gen_cols = int(gen.shape[1]) if (k == DNET and gen.ndim == 2) else 0
+    y = _dev(y)
+    eta, W, v, s2 = _dev(eta).reshape(-1), _dev(W).reshape(T, -1), _dev(v).reshape(-1), _dev(sigma2).reshape(1)
+    out = torch.empty(3, dtype=torch.float64, device="cuda")
+    tau = torch.empty(T, dtype=torch.float64, device="cuda")
+    status = torch.empty(1, dtype=torch.int32, device="cuda")
+    check(lib().mtgp_nll_equal_static(k, d, T, m, gen.ctypes.data_as(ctypes.c_void_p), gen_cols,
+                                      shift.ctypes.data_as(ctypes.c_void_p),
+                                      FP32_TRANSFORM if precision == "fp32" else FP64, _ptr(y), _ptr(eta), _ptr(W),
+                                      W.shape[1], _ptr(v), _ptr(s2), _ptr(out), _ptr(tau), _ptr(status),
+                                      _stream(stream)), "mtgp_nll_equal_static")
+    return out, tau, status
+
+
 class NLLFunction(torch.autograd.Function):
     """NLL as a differentiable function of (eta, W, v, sigma2) through the hand-written adjoint."""
 
