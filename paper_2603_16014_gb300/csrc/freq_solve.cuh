@@ -86,19 +86,17 @@ __device__ __forceinline__ void st(double* p, long long i, Vt<CPLX> v) {
     }
 }
 
-// 1 / x in FP64: hardware reciprocal approximation (rcp.approx.ftz.f64) refined by two Newton steps
-// r <- r (2 - x r) (each step doubles the correct bits); exact division outside binary exponents
+// 1 / x in FP64: hardware reciprocal approximation (rcp.approx.ftz.f64, about 20 correct bits)
+// refined by one third-order step (error cubed); exact division outside binary exponents
 // [-1000, 1000], tested on the bit pattern so the common path issues no FP64 compare.
 __device__ __forceinline__ double fast_rcp(double x) {
     const unsigned ex = (unsigned)(__double_as_longlong(x) >> 52) & 0x7ffu;
     if (ex < 23u || ex > 2023u) return 1.0 / x;
     double r;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-    double e = fma(-x, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-x, r, 1.0);
-    r = fma(r, e, r);
-    return r;
+    // with e = 1 - x r:  1/x = r (1 + e + e^2 + ...); r (1 + e + e^2) leaves a relative error e^3
+    const double e = fma(-x, r, 1.0);
+    return fma(r, fma(e, e, e), r);
 }
 
 // x > 0 and finite, tested on the bit pattern (sign clear, not zero, exponent not all ones)
@@ -126,6 +124,15 @@ struct LogAcc {
         expo += e;
     }
     __device__ __forceinline__ double log_value() const { return log(mant) + (double)expo * 0.6931471805599453; }
+    // product over the 32 lanes of a warp (all lanes call); the total is valid in lane 0
+    __device__ __forceinline__ void warp_product() {
+        for (int o = 16; o > 0; o >>= 1) {
+            double m2 = __shfl_down_sync(0xffffffffu, mant, o);
+            long long e2 = __shfl_down_sync(0xffffffffu, expo, o);
+            mul(m2);
+            expo += e2;
+        }
+    }
 };
 
 // Solve one frequency.  mu[t][u] (t <= u) are the first-column transforms M(f); rh[t] = rhat_t(f).

@@ -345,7 +345,9 @@ k_fused_b(void* spec, void* wgt, const double* __restrict__ yhat, double* alpha_
                 }
         }
     }
-    acc[0] = lacc.log_value();
+    // one logarithm per warp: multiply the lanes' mantissa/exponent products first
+    lacc.warp_product();
+    acc[0] = ((threadIdx.x & 31) == 0) ? lacc.log_value() : 0.0;
     if (bad) set_status(status, ST_NOT_PD);
     __syncthreads();
     if (p.store_alpha && !p.grad) {
