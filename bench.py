@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu", action="store_true",
                     help="only warm-up + K steps of the workload, no extras (for ncu captures)")
+    ap.add_argument("--workload", default="nllgrad", choices=["nllgrad", "batch512"],
+                    help="nllgrad: the headline NLL+gradient evaluation; batch512: 512 heterogeneous fits, "
+                         "Adam steps in one CUDA graph vs a plain per-fit optimiser")
+    ap.add_argument("--fits", type=int, default=512)
     return ap.parse_args()
 
 
@@ -320,6 +324,107 @@ def run_ncu_case(args):
     print(json.dumps({"nll": outs[0][0].item(), "steps": args.steps, "warmup": args.warmup}))
 
 
+# ----------------------------------------------------------------------------- batched fits
+
+def batch_problems(nfits: int, seed: int = 0):
+    """Fits of mixed shape: n = 2^U{8..16} per task (equal across tasks), T ~ U{2..8}, d ~ U{2..12},
+    first half lattices, second half digital nets; parameters and responses as the d=8 digital-net
+    workload (W T x 2, correlated Walsh/cosine modes)."""
+    import numpy as np
+
+    from paper_2603_16014_gb300 import inputs
+
+    rng = np.random.default_rng([seed, 4242])
+    probs = []
+    for f in range(nfits):
+        kind = "lattice" if f < nfits // 2 else "dnet"
+        m = int(rng.integers(8, 17))
+        T = int(rng.integers(2, 9))
+        d = int(rng.integers(2, 13))
+        eta = float(np.exp(rng.uniform(np.log(0.1), np.log(2.0))))
+        v = float(np.exp(rng.uniform(np.log(0.01), np.log(1.0))))
+        s2 = float(np.exp(rng.uniform(np.log(1e-8), np.log(1e-4))))
+        probs.append(inputs.make_problem(kind, d, (m,) * T, seed=int(rng.integers(1 << 30)), s=2, eta=eta, v=v,
+                                         sigma2=s2, recipe="walshcos32", mmax=16))
+    return probs
+
+
+def default_theta(p):
+    """The plain optimiser's fixed starting point: eta = 1, W = 0.1, v = 1, sigma2 = 1e-4."""
+    import numpy as np
+    return (np.ones(p.d), np.full(p.W.shape, 0.1), np.ones(p.T), 1e-4)
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+
+    from paper_2603_16014_gb300 import inputs
+    from paper_2603_16014_gb300.mtgp import MTGP, Batch, nll as nll_fn
+
+    torch.cuda.set_device(0)
+    probs = batch_problems(args.fits)
+    ys = []
+    for p in probs:
+        m = MTGP.from_problem(p, "fp32")
+        X = m.points().cpu().numpy().view(np.uint32)
+        ys.append(inputs.synth_y(p, [X[i * p.n[0]:(i + 1) * p.n[0]] for i in range(p.T)]))
+        m.close()
+    b = Batch(probs, s=2, precision="fp32")
+    b.set_y(torch.from_numpy(np.concatenate(ys)))
+    theta0 = b.pack([default_theta(p) for p in probs])
+    b.set_theta(torch.from_numpy(theta0))
+    t0 = time.perf_counter()
+    b.autotune(reps=2)
+    tune_s = time.perf_counter() - t0
+    steps, lr = args.steps, 0.05
+    stream = torch.cuda.Stream()
+    trace = torch.zeros(steps * len(probs), dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        b.set_theta(torch.from_numpy(theta0))
+        b.adam(steps, lr, graph=True, trace=trace)      # capture + first replay (warm-up)
+        stream.synchronize()
+        b.set_theta(torch.from_numpy(theta0))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.adam(steps, lr, graph=True, trace=trace)
+        e1.record(stream)
+        stream.synchronize()
+    graph_ms = e0.elapsed_time(e1)
+    final_batch = trace.view(steps, -1)[-1].cpu().numpy()
+    # plain per-fit optimiser: torch Adam on log parameters through the autograd NLL, one fit at a time
+    k_plain = max(2, min(5, steps))
+    t0 = time.perf_counter()
+    for p, y in zip(probs, ys):
+        m = MTGP.from_problem(p, "fp32")
+        m.set_y(torch.from_numpy(y))
+        eta, W, v, s2 = [torch.as_tensor(np.asarray(x, dtype=np.float64)).cuda() for x in default_theta(p)]
+        le, lv, ls = eta.log().requires_grad_(), v.log().requires_grad_(), s2.reshape(1).log().requires_grad_()
+        W = W.clone().requires_grad_()
+        opt = torch.optim.Adam([le, W, lv, ls], lr=lr)
+        for _ in range(k_plain):
+            opt.zero_grad()
+            loss = nll_fn(m, le.exp(), W, lv.exp(), ls.exp())
+            loss.backward()
+            opt.step()
+        torch.cuda.synchronize()
+        m.close()
+    plain_s = (time.perf_counter() - t0) * steps / k_plain
+    line = {
+        "metric": "batched fits: Adam fit-steps/s (512 mixed fits, one CUDA graph) vs plain per-fit optimiser",
+        "value": len(probs) * steps / (graph_ms / 1e3), "unit": "fit-steps/s", "n_gpus": 1, "steps": steps,
+        "fits": len(probs), "ms_per_step": graph_ms / steps, "higher_is_better": True,
+        "plain_fit_steps_per_s": len(probs) * steps / plain_s,
+        "speedup_vs_plain": plain_s / (graph_ms / 1e3), "autotune_s": tune_s,
+        "config": {"workload": "batch512_mixed", "n": "2^U{8..16}", "T": "U{2..8}", "d": "U{2..12}",
+                   "kinds": "half lattice, half digital net", "precision": "FP32 transforms / FP64 solves",
+                   "plain": f"torch Adam through the autograd NLL, fit by fit, {k_plain} steps per fit scaled to {steps}"},
+        "final_nll_mean": float(np.mean(final_batch)),
+    }
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
 # ----------------------------------------------------------------------------- reference (oracle)
 
 def run_reference(args, rank, world):
@@ -365,6 +470,9 @@ def main():
         build.build()
     if args.ncu:
         run_ncu_case(args)
+        return
+    if args.workload == "batch512":
+        run_batch(args)
         return
     run_ours(args, rank, world, local_rank)
 

@@ -174,6 +174,46 @@ int mtgp_nll_equal_static(int kind, int d, int T, int m, const uint32_t* gen, in
                           const double* W, int s, const double* v, const double* sigma2, double* out,
                           double* tau, int* status, cudaStream_t stream);
 
+/*
+ * Batched fits: many independent fits with equal task sizes (each fit: kind, d, T tasks of 2^m
+ * points) evaluated and optimised together.  No counterpart in the paper beyond its optimisation
+ * loop (Sec. 4.1 fits each model by a first-order optimiser on the MLE loss (3.3)); here every
+ * optimiser step of all fits is one batched NLL + gradient evaluation plus one Adam update.
+ *
+ * Parameters of fit f are packed as [eta (d), W (T x s, row-major), v (T), sigma2 (1)], fits
+ * concatenated (offsets from mtgp_batch_layout).  Adam acts on log eta, W, log v, log sigma2 with
+ * beta1 = 0.9, beta2 = 0.999, eps = 1e-8; gradients returned by mtgp_batch_nll_grad are with respect
+ * to the packed (natural) parameters.
+ *
+ * mtgp_batch_create -- host arrays of length nfits: kind, d, T, m, gen_cols; gen and shift are the
+ *   fits' generator / shift arrays (as mtgp_create) concatenated; s is W's column count for every
+ *   fit (1 <= s <= T).  precision as mtgp_create.  MTGP_ERR_UNSUPPORTED if a fit's size is outside
+ *   the fused kernels (m >= 4, per-CTA tiles <= 96 KB).
+ * mtgp_batch_layout -- host arrays of nfits + 1 offsets into the packed parameters and observations.
+ * mtgp_batch_set_y -- device, all fits' observations concatenated (each fit as mtgp_set_y).
+ * mtgp_batch_set_theta / mtgp_batch_get_theta -- device packed parameters (natural scale); set
+ *   also resets the Adam moments and step count.
+ * mtgp_batch_nll_grad -- device outputs: nll (nfits, NLL of each fit), grad (packed), either NULL.
+ * mtgp_batch_adam -- `steps` Adam steps at learning rate lr; trace (device, steps x nfits, or NULL)
+ *   receives each step's NLL before its update.  use_graph = 1 captures the steps in one CUDA graph
+ *   on the first call (stream must not be the legacy default stream) and replays it afterwards.
+ * mtgp_batch_autotune -- times the candidate transform splits of each distinct (kind, T, m,
+ *   dimension bucket) on one representative fit (reps timed runs each), keeps the fastest for all
+ *   fits of that key and rebuilds the launch tables; chosen (host, nfits, or NULL) receives the
+ *   splits.  Needs observations and parameters set; synchronises the device.
+ */
+typedef struct mtgp_batch_s mtgp_batch_t;
+int mtgp_batch_create(mtgp_batch_t** out, int nfits, const int* kind, const int* d, const int* T, const int* m,
+                      const uint32_t* gen, const int* gen_cols, const uint32_t* shift, int s, int precision);
+int mtgp_batch_destroy(mtgp_batch_t* b);
+int mtgp_batch_layout(const mtgp_batch_t* b, long long* param_offsets, long long* y_offsets);
+int mtgp_batch_set_y(mtgp_batch_t* b, const double* y, cudaStream_t stream);
+int mtgp_batch_set_theta(mtgp_batch_t* b, const double* theta, cudaStream_t stream);
+int mtgp_batch_get_theta(mtgp_batch_t* b, double* theta, cudaStream_t stream);
+int mtgp_batch_nll_grad(mtgp_batch_t* b, double* nll, double* grad, cudaStream_t stream);
+int mtgp_batch_adam(mtgp_batch_t* b, int steps, double lr, int use_graph, double* trace, cudaStream_t stream);
+int mtgp_batch_autotune(mtgp_batch_t* b, int reps, int* chosen, cudaStream_t stream);
+
 /* mtgp_workspace_bytes -- device bytes the handle holds (for capacity planning). */
 long long mtgp_workspace_bytes(const mtgp_t* h);
 

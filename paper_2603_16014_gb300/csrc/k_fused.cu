@@ -12,6 +12,8 @@
 // results do not depend on block scheduling.  Columns: c = 0 is the diagonal block's column (shared
 // by all tasks for equal sizes), then one per task pair t < u.
 #include <cstring>
+#include <mutex>
+#include <unordered_map>
 
 #include "freq_solve.cuh"
 
@@ -137,13 +139,13 @@ __device__ void reduce_columns(const double* part, int nrows, int ncols, double*
 }
 
 // last-block election: true in exactly one block, after all blocks have written their partials
-__device__ bool last_block(unsigned* counter) {
+__device__ bool last_block(unsigned* counter, unsigned nblocks) {
     __shared__ bool am_last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned prev = atomicAdd(counter, 1u);
-        am_last = (prev == gridDim.x - 1);
+        am_last = (prev == nblocks - 1);
     }
     __syncthreads();
     if (am_last) __threadfence();
@@ -157,6 +159,26 @@ struct OutPtrs {
     double* g_W;
     double* g_v;
     double* g_s2;
+};
+
+// Everything one fit needs on the device: its parameters, theta / output pointers and buffers.
+// Single-fit kernels take it by value; batched kernels read it from a device array.
+struct FitDesc {
+    FusedParams p;
+    ThetaPtrs th;
+    OutPtrs o;
+    const uint32_t* gen;
+    const uint32_t* shift;
+    const void* tw;          // twiddles of the transform precision (lattices)
+    void* spec;              // C x n spectra
+    void* wgt;               // C x n adjoint weights
+    const double* yhat;      // T x n observations, transformed
+    double* alpha;           // T x n Lambda^-1 rhat (posterior)
+    const double* tau;       // T optimal means (sorted)
+    double* partials;        // kernel B partials (nb x NQ), then kernel C partials (na x d)
+    unsigned* counters;      // [0] B (NLL only), [1] C
+    int* status;
+    int na, nb;              // kernel A / C blocks, kernel B blocks
 };
 
 __device__ __forceinline__ int gq(int t, int u, int T) { return t * T - t * (t - 1) / 2 + (u - t); }
@@ -217,10 +239,14 @@ __device__ __forceinline__ void load_design_smem(const FusedParams& p, const uin
 }
 
 template <typename S, bool CPLX, int DMAX>
-__global__ void __launch_bounds__(512)
-k_fused_a(void* spec, FusedParams p, const uint32_t* __restrict__ gen, const uint32_t* __restrict__ shift,
-          const double* __restrict__ eta, const cx<S>* __restrict__ tw) {
+__device__ __forceinline__ void fused_a_body(const FitDesc& f, int blk) {
     using E = typename El<S, CPLX>::T;
+    const FusedParams& p = f.p;
+    void* spec = f.spec;
+    const uint32_t* gen = f.gen;
+    const uint32_t* shift = f.shift;
+    const double* eta = f.th.eta;
+    const cx<S>* tw = reinterpret_cast<const cx<S>*>(f.tw);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     E* buf = reinterpret_cast<E*>(smem_raw);
     __shared__ S s_eta[MTGP_MAX_DIM];
@@ -228,7 +254,7 @@ k_fused_a(void* spec, FusedParams p, const uint32_t* __restrict__ gen, const uin
     __shared__ uint32_t s_sh[MTGP_TMAX * MTGP_MAX_DIM];
     __shared__ uint32_t s_gen[MTGP_MAX_DIM * 32];
     const int HA = 1 << p.a;
-    const long long base = (long long)blockIdx.x << p.a;
+    const long long base = (long long)blk << p.a;
     const int d = p.d;
     if (threadIdx.x < d) s_eta[threadIdx.x] = (S)eta[threadIdx.x];
     load_design_smem(p, gen, shift, eta, base, s_gen, s_sh, s_zhi);
@@ -265,11 +291,19 @@ k_fused_a(void* spec, FusedParams p, const uint32_t* __restrict__ gen, const uin
 constexpr int kBThreads = 256;
 
 template <int T, bool CPLX, typename S>
-__global__ void __launch_bounds__(kBThreads, 2)
-k_fused_b(void* spec, void* wgt, const double* __restrict__ yhat, double* alpha_out, const double* tau_sorted,
-          FusedParams p, ThetaPtrs th, const cx<S>* __restrict__ tw, double* partials, unsigned* counter, OutPtrs o,
-          int* status) {
+__device__ __forceinline__ void fused_b_body(const FitDesc& f, int blk) {
     using E = typename El<S, CPLX>::T;
+    const FusedParams& p = f.p;
+    const ThetaPtrs& th = f.th;
+    void* spec = f.spec;
+    void* wgt = f.wgt;
+    const double* yhat = f.yhat;
+    double* alpha_out = f.alpha;
+    const double* tau_sorted = f.tau;
+    const cx<S>* tw = reinterpret_cast<const cx<S>*>(f.tw);
+    double* partials = f.partials;
+    unsigned* counter = f.counters;
+    int* status = f.status;
     using V = Vt<CPLX>;
     constexpr int NQ = 3 + T * (T + 1) / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -285,7 +319,7 @@ k_fused_b(void* spec, void* wgt, const double* __restrict__ yhat, double* alpha_
     const int L = 1 << p.lgL;
     const int tile = HB * L;
     const int lgT = lgH + p.lgL;
-    const long long lo0 = (long long)blockIdx.x << p.lgL;
+    const long long lo0 = (long long)blk << p.lgL;
     // observations of this thread's first frequency, requested before the transform stages so the
     // (L2-flushed) loads overlap them
     V rh0[T];
@@ -382,14 +416,14 @@ k_fused_b(void* spec, void* wgt, const double* __restrict__ yhat, double* alpha_
             double v = 0.0;
             for (int b = lane; b < (int)blockDim.x; b += 32) v += s_acc[q * blockDim.x + b];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) partials[(long long)blockIdx.x * NQ + q] = v;
+            if (lane == 0) partials[(long long)blk * NQ + q] = v;
         }
     }
     if (p.grad) return;  // kernel C finishes
-    if (!last_block(counter)) return;
-    reduce_columns(partials, gridDim.x, NQ, s_tot);
+    if (!last_block(counter, f.nb)) return;
+    reduce_columns(partials, f.nb, NQ, s_tot);
     if (threadIdx.x == 0) {
-        write_outputs(s_tot, nullptr, p, th, tau_sorted, o);
+        write_outputs(s_tot, nullptr, p, th, tau_sorted, f.o);
         *counter = 0u;
     }
 }
@@ -397,11 +431,20 @@ k_fused_b(void* spec, void* wgt, const double* __restrict__ yhat, double* alpha_
 // ---------------------------------------------------------------------------------- kernel C
 
 template <typename S, bool CPLX, int DMAX>
-__global__ void __launch_bounds__(512)
-k_fused_c(const void* wgt, FusedParams p, const uint32_t* __restrict__ gen, const uint32_t* __restrict__ shift,
-          const double* __restrict__ eta, const cx<S>* __restrict__ tw, const double* partials_b, int nb,
-          double* partials_c, unsigned* counter, ThetaPtrs th, const double* tau_sorted, OutPtrs o) {
+__device__ __forceinline__ void fused_c_body(const FitDesc& f, int blk) {
     using E = typename El<S, CPLX>::T;
+    const FusedParams& p = f.p;
+    const ThetaPtrs& th = f.th;
+    const void* wgt = f.wgt;
+    const uint32_t* gen = f.gen;
+    const uint32_t* shift = f.shift;
+    const double* eta = f.th.eta;
+    const cx<S>* tw = reinterpret_cast<const cx<S>*>(f.tw);
+    const int nb = f.nb;
+    const double* partials_b = f.partials;
+    double* partials_c = f.partials + (long long)f.nb * (3 + p.T * (p.T + 1) / 2);
+    unsigned* counter = f.counters + 1;
+    const double* tau_sorted = f.tau;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     E* buf = reinterpret_cast<E*>(smem_raw);
     __shared__ S s_eta[MTGP_MAX_DIM];
@@ -412,7 +455,7 @@ k_fused_c(const void* wgt, FusedParams p, const uint32_t* __restrict__ gen, cons
     __shared__ double s_tot[3 + MTGP_MAX_COLS];
     __shared__ double s_etot[MTGP_MAX_DIM];
     const int HA = 1 << p.a;
-    const long long base = (long long)blockIdx.x << p.a;
+    const long long base = (long long)blk << p.a;
     const int d = p.d;
     if (threadIdx.x < d) s_eta[threadIdx.x] = (S)eta[threadIdx.x];
     load_design_smem(p, gen, shift, eta, base, s_gen, s_sh, s_zhi);
@@ -458,15 +501,54 @@ k_fused_c(const void* wgt, FusedParams p, const uint32_t* __restrict__ gen, cons
     __shared__ S s_scr_s[32];
     for (int j = 0; j < d; ++j) {
         S v = block_sum_s<S>(j < DMAX ? part[j] : (S)0, s_scr_s);
-        if (threadIdx.x == 0) partials_c[(long long)blockIdx.x * d + j] = (double)v;
+        if (threadIdx.x == 0) partials_c[(long long)blk * d + j] = (double)v;
     }
-    if (!last_block(counter)) return;
+    if (!last_block(counter, f.na)) return;
     const int NQ = 3 + p.T * (p.T + 1) / 2;
     reduce_columns(partials_b, nb, NQ, s_tot);
-    reduce_columns(partials_c, gridDim.x, d, s_etot);
+    reduce_columns(partials_c, f.na, d, s_etot);
     if (threadIdx.x == 0) {
-        write_outputs(s_tot, s_etot, p, th, tau_sorted, o);
+        write_outputs(s_tot, s_etot, p, th, tau_sorted, f.o);
         *counter = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------------- kernels
+
+template <typename S, bool CPLX, int DMAX>
+__global__ void __launch_bounds__(512) k_fused_a(FitDesc f) { fused_a_body<S, CPLX, DMAX>(f, blockIdx.x); }
+
+template <int T, bool CPLX, typename S>
+__global__ void __launch_bounds__(kBThreads, 2) k_fused_b(FitDesc f) { fused_b_body<T, CPLX, S>(f, blockIdx.x); }
+
+template <typename S, bool CPLX, int DMAX>
+__global__ void __launch_bounds__(512) k_fused_c(FitDesc f) { fused_c_body<S, CPLX, DMAX>(f, blockIdx.x); }
+
+// Batched fits: a persistent grid walks a table of (fit, block) items, largest fits first.
+template <typename S, bool CPLX, int DMAX>
+__global__ void __launch_bounds__(512) k_batch_a(const FitDesc* fits, const int2* items, int nitems) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 w = items[it];
+        fused_a_body<S, CPLX, DMAX>(fits[w.x], w.y);
+        __syncthreads();
+    }
+}
+
+template <int T, bool CPLX, typename S>
+__global__ void __launch_bounds__(kBThreads, 2) k_batch_b(const FitDesc* fits, const int2* items, int nitems) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 w = items[it];
+        fused_b_body<T, CPLX, S>(fits[w.x], w.y);
+        __syncthreads();
+    }
+}
+
+template <typename S, bool CPLX, int DMAX>
+__global__ void __launch_bounds__(512) k_batch_c(const FitDesc* fits, const int2* items, int nitems) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 w = items[it];
+        fused_c_body<S, CPLX, DMAX>(fits[w.x], w.y);
+        __syncthreads();
     }
 }
 
@@ -476,24 +558,54 @@ k_fused_c(const void* wgt, FusedParams p, const uint32_t* __restrict__ gen, cons
 
 namespace {
 
-size_t elem_size(const Handle* h) { return (h->fp32 ? 4 : 8) * (h->cplx ? 2 : 1); }
+size_t elem_size_of(bool fp32, bool cplx) { return (fp32 ? 4 : 8) * (cplx ? 2 : 1); }
+size_t elem_size(const Handle* h) { return elem_size_of(h->fp32, h->cplx); }
 
-// split n = 2^m into a low part 2^a (kernels A, C) and a high part 2^(m-a) (kernel B)
-bool plan(const Handle* h, int* a_out, int* lgL_out) {
-    const int m = h->m[0];
-    if (!h->equal || m < 4) return false;
-    const size_t es = elem_size(h);
+// Raise a kernel's dynamic shared-memory limit to `bytes` (the default limit counts static shared
+// memory too, so any dynamic size may need it); remembered per kernel so each value is set once.
+std::mutex g_smem_mu;
+std::unordered_map<const void*, size_t> g_smem_set;
+
+template <typename F>
+void set_smem(F* fn, size_t bytes) {
+    if (bytes == 0) return;
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    size_t& cur = g_smem_set[reinterpret_cast<const void*>(fn)];
+    if (bytes > cur) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        cur = bytes;
+    }
+}
+
+}  // namespace
+
+// split n = 2^m into a low part 2^a (kernels A, C) and a high part 2^(m-a) (kernel B); a_pref >= 0
+// asks for a specific split (the autotuner), -1 for the default (B tiles of 2^8 frequencies)
+bool fused_plan(int m, int ncols, bool fp32, bool cplx, int a_pref, int* a_out, int* lgL_out) {
+    if (m < 4) return false;
+    const size_t es = elem_size_of(fp32, cplx);
     const size_t cap = 96 * 1024;
-    const int C = h->ncols;
-    // kernel B tiles hold 2^(m-a) frequencies (one per thread at 2^8); kernels A and C hold 2^a values
-    int a = m - 8;
-    if (a < m / 2) a = m / 2;
-    while (a > 1 && (size_t)C * ((size_t)1 << a) * es > cap) --a;
+    int a;
+    if (a_pref >= 0) {
+        a = a_pref;
+    } else {
+        a = m - 8;
+        if (a < m / 2) a = m / 2;
+        while (a > 1 && (size_t)ncols * ((size_t)1 << a) * es > cap) --a;
+    }
     if (a < 1 || a > m - 1) return false;
-    if ((size_t)C * ((size_t)1 << (m - a)) * es > cap) return false;
+    if ((size_t)ncols * ((size_t)1 << a) * es > cap) return false;
+    if ((size_t)ncols * ((size_t)1 << (m - a)) * es > cap) return false;
     *a_out = a;
     *lgL_out = 0;
     return true;
+}
+
+namespace {
+
+bool plan(const Handle* h, int* a_out, int* lgL_out) {
+    if (!h->equal) return false;
+    return fused_plan(h->m[0], h->ncols, h->fp32, h->cplx, -1, a_out, lgL_out);
 }
 
 FusedParams make_params(const Handle* h, ThetaPtrs th, bool grad, bool store_alpha, int a, int lgL) {
@@ -526,86 +638,188 @@ FusedParams make_params(const Handle* h, ThetaPtrs th, bool grad, bool store_alp
     return p;
 }
 
-template <typename F>
-void set_smem(F* fn, size_t bytes) {
-    if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+FitDesc make_desc(const Handle* h, ThetaPtrs th, OutPtrs o, bool grad, bool store_alpha, int a, int lgL) {
+    FitDesc f;
+    std::memset(&f, 0, sizeof(f));
+    f.p = make_params(h, th, grad, store_alpha, a, lgL);
+    f.th = th;
+    f.o = o;
+    f.gen = h->gen;
+    f.shift = h->shift;
+    f.tw = h->fp32 ? h->twid32 : h->twid;
+    f.spec = h->spec;
+    f.wgt = h->wgt;
+    f.yhat = h->yhat;
+    f.alpha = h->alpha;
+    f.tau = h->tau;
+    f.partials = h->partials;
+    f.counters = h->counters;
+    f.status = h->status;
+    f.na = 1 << (f.p.m - a);
+    f.nb = 1 << (a - lgL);
+    return f;
+}
+
+// ---- shared dispatch: one phase of one class, single fit (fits == nullptr) or a batch item table
+
+size_t smem_ac(int C, int a, size_t es) { return es * C * ((size_t)1 << a); }
+size_t smem_b(int T, int C, int lgH, size_t es) {
+    size_t s = es * C * ((size_t)1 << lgH);
+    const size_t red = (size_t)(3 + T * (T + 1) / 2) * kBThreads * sizeof(double);
+    return s > red ? s : red;
+}
+int threads_ac(int a) { return (1 << a) < 512 ? ((1 << a) < 64 ? 64 : (1 << a)) : 512; }
+
+template <typename S, bool CPLX, int DMAX>
+void phase_ac(bool is_c, const FitDesc* single, const FitDesc* fits, const int2* items, int nitems, int grid,
+              int threads, size_t smem, cudaStream_t st) {
+    if (!is_c) {
+        if (single) {
+            set_smem(k_fused_a<S, CPLX, DMAX>, smem);
+            k_fused_a<S, CPLX, DMAX><<<grid, threads, smem, st>>>(*single);
+        } else {
+            set_smem(k_batch_a<S, CPLX, DMAX>, smem);
+            k_batch_a<S, CPLX, DMAX><<<grid, threads, smem, st>>>(fits, items, nitems);
+        }
+    } else {
+        if (single) {
+            set_smem(k_fused_c<S, CPLX, DMAX>, smem);
+            k_fused_c<S, CPLX, DMAX><<<grid, threads, smem, st>>>(*single);
+        } else {
+            set_smem(k_batch_c<S, CPLX, DMAX>, smem);
+            k_batch_c<S, CPLX, DMAX><<<grid, threads, smem, st>>>(fits, items, nitems);
+        }
+    }
+}
+
+template <typename S, bool CPLX>
+void phase_ac_d(int dmax, bool is_c, const FitDesc* single, const FitDesc* fits, const int2* items, int nitems,
+                int grid, int threads, size_t smem, cudaStream_t st) {
+    if (dmax <= 4) phase_ac<S, CPLX, 4>(is_c, single, fits, items, nitems, grid, threads, smem, st);
+    else if (dmax <= 8) phase_ac<S, CPLX, 8>(is_c, single, fits, items, nitems, grid, threads, smem, st);
+    else if (dmax <= 16) phase_ac<S, CPLX, 16>(is_c, single, fits, items, nitems, grid, threads, smem, st);
+    else phase_ac<S, CPLX, 32>(is_c, single, fits, items, nitems, grid, threads, smem, st);
 }
 
 template <int T, bool CPLX, typename S>
-void launch_b(const Handle* h, FusedParams p, ThetaPtrs th, OutPtrs o, cudaStream_t st) {
-    size_t smem = elem_size(h) * p.C * ((size_t)1 << (p.m - p.a + p.lgL));
-    const size_t red = (size_t)(3 + T * (T + 1) / 2) * kBThreads * sizeof(double);
-    if (red > smem) smem = red;
-    set_smem(k_fused_b<T, CPLX, S>, smem);
-    const int grid = 1 << (p.a - p.lgL);
-    const void* twp = h->fp32 ? h->twid32 : h->twid;
-    mtgp_prof_begin(h, "fused_b", st);
-    k_fused_b<T, CPLX, S><<<grid, kBThreads, smem, st>>>(h->spec, h->wgt, h->yhat, h->alpha, h->tau, p, th,
-                                                   reinterpret_cast<const cx<S>*>(twp), h->partials, h->counters, o,
-                                                   h->status);
-    mtgp_prof_end(h, st);
-}
-
-template <bool CPLX, typename S>
-void dispatch_b(const Handle* h, FusedParams p, ThetaPtrs th, OutPtrs o, cudaStream_t st) {
-    switch (h->T) {
-        case 1: launch_b<1, CPLX, S>(h, p, th, o, st); break;
-        case 2: launch_b<2, CPLX, S>(h, p, th, o, st); break;
-        case 3: launch_b<3, CPLX, S>(h, p, th, o, st); break;
-        case 4: launch_b<4, CPLX, S>(h, p, th, o, st); break;
-        case 5: launch_b<5, CPLX, S>(h, p, th, o, st); break;
-        case 6: launch_b<6, CPLX, S>(h, p, th, o, st); break;
-        case 7: launch_b<7, CPLX, S>(h, p, th, o, st); break;
-        default: launch_b<8, CPLX, S>(h, p, th, o, st); break;
+void phase_b_t(const FitDesc* single, const FitDesc* fits, const int2* items, int nitems, int grid, size_t smem,
+               cudaStream_t st) {
+    if (single) {
+        set_smem(k_fused_b<T, CPLX, S>, smem);
+        k_fused_b<T, CPLX, S><<<grid, kBThreads, smem, st>>>(*single);
+    } else {
+        set_smem(k_batch_b<T, CPLX, S>, smem);
+        k_batch_b<T, CPLX, S><<<grid, kBThreads, smem, st>>>(fits, items, nitems);
     }
 }
 
 template <bool CPLX, typename S>
-void run_fused(const Handle* h, FusedParams p, ThetaPtrs th, OutPtrs o, cudaStream_t st) {
-    using E = typename El<S, CPLX>::T;
-    const void* twp = h->fp32 ? h->twid32 : h->twid;
-    const cx<S>* tw = reinterpret_cast<const cx<S>*>(twp);
-    const size_t smem_a = sizeof(E) * p.C * ((size_t)1 << p.a);
-    const int grid_a = 1 << (p.m - p.a);
-    const int thr_a = (1 << p.a) < 512 ? ((1 << p.a) < 64 ? 64 : (1 << p.a)) : 512;
-    mtgp_prof_begin(h, "fused_a", st);
-    if (h->d <= 4) {
-        set_smem(k_fused_a<S, CPLX, 4>, smem_a);
-        k_fused_a<S, CPLX, 4><<<grid_a, thr_a, smem_a, st>>>(h->spec, p, h->gen, h->shift, th.eta, tw);
-    } else if (h->d <= 8) {
-        set_smem(k_fused_a<S, CPLX, 8>, smem_a);
-        k_fused_a<S, CPLX, 8><<<grid_a, thr_a, smem_a, st>>>(h->spec, p, h->gen, h->shift, th.eta, tw);
-    } else if (h->d <= 16) {
-        set_smem(k_fused_a<S, CPLX, 16>, smem_a);
-        k_fused_a<S, CPLX, 16><<<grid_a, thr_a, smem_a, st>>>(h->spec, p, h->gen, h->shift, th.eta, tw);
-    } else {
-        set_smem(k_fused_a<S, CPLX, 32>, smem_a);
-        k_fused_a<S, CPLX, 32><<<grid_a, thr_a, smem_a, st>>>(h->spec, p, h->gen, h->shift, th.eta, tw);
+void phase_b(int T, const FitDesc* single, const FitDesc* fits, const int2* items, int nitems, int grid, size_t smem,
+             cudaStream_t st) {
+    switch (T) {
+        case 1: phase_b_t<1, CPLX, S>(single, fits, items, nitems, grid, smem, st); break;
+        case 2: phase_b_t<2, CPLX, S>(single, fits, items, nitems, grid, smem, st); break;
+        case 3: phase_b_t<3, CPLX, S>(single, fits, items, nitems, grid, smem, st); break;
+        case 4: phase_b_t<4, CPLX, S>(single, fits, items, nitems, grid, smem, st); break;
+        case 5: phase_b_t<5, CPLX, S>(single, fits, items, nitems, grid, smem, st); break;
+        case 6: phase_b_t<6, CPLX, S>(single, fits, items, nitems, grid, smem, st); break;
+        case 7: phase_b_t<7, CPLX, S>(single, fits, items, nitems, grid, smem, st); break;
+        default: phase_b_t<8, CPLX, S>(single, fits, items, nitems, grid, smem, st); break;
     }
-    mtgp_prof_end(h, st);
-    dispatch_b<CPLX, S>(h, p, th, o, st);
-    if (!p.grad) return;
-    const int nb = 1 << (p.a - p.lgL);
-    const int NQ = 3 + h->T * (h->T + 1) / 2;
-    double* part_c = h->partials + (long long)nb * NQ;
-    mtgp_prof_begin(h, "fused_c", st);
-    if (h->d <= 4) {
-        set_smem(k_fused_c<S, CPLX, 4>, smem_a);
-        k_fused_c<S, CPLX, 4><<<grid_a, thr_a, smem_a, st>>>(h->wgt, p, h->gen, h->shift, th.eta, tw, h->partials, nb, part_c, h->counters + 1, th, h->tau, o);
-    } else if (h->d <= 8) {
-        set_smem(k_fused_c<S, CPLX, 8>, smem_a);
-        k_fused_c<S, CPLX, 8><<<grid_a, thr_a, smem_a, st>>>(h->wgt, p, h->gen, h->shift, th.eta, tw, h->partials, nb, part_c, h->counters + 1, th, h->tau, o);
-    } else if (h->d <= 16) {
-        set_smem(k_fused_c<S, CPLX, 16>, smem_a);
-        k_fused_c<S, CPLX, 16><<<grid_a, thr_a, smem_a, st>>>(h->wgt, p, h->gen, h->shift, th.eta, tw, h->partials, nb, part_c, h->counters + 1, th, h->tau, o);
-    } else {
-        set_smem(k_fused_c<S, CPLX, 32>, smem_a);
-        k_fused_c<S, CPLX, 32><<<grid_a, thr_a, smem_a, st>>>(h->wgt, p, h->gen, h->shift, th.eta, tw, h->partials, nb, part_c, h->counters + 1, th, h->tau, o);
-    }
-    mtgp_prof_end(h, st);
 }
 
 }  // namespace
+
+// one phase (0 = A, 1 = B, 2 = C) for one class; single != nullptr launches one fit with a grid of
+// its own blocks, otherwise a persistent grid over `nitems` batch items
+void fused_phase(int phase, bool fp32, bool cplx, int T, int dmax, const void* single_v, const void* fits_v,
+                 const int2* items, int nitems, int grid, int threads_acq, size_t smem, cudaStream_t st) {
+    const FitDesc* single = static_cast<const FitDesc*>(single_v);
+    const FitDesc* fits = static_cast<const FitDesc*>(fits_v);
+    if (phase == 1) {
+        if (fp32) {
+            if (cplx) phase_b<true, float>(T, single, fits, items, nitems, grid, smem, st);
+            else phase_b<false, float>(T, single, fits, items, nitems, grid, smem, st);
+        } else {
+            if (cplx) phase_b<true, double>(T, single, fits, items, nitems, grid, smem, st);
+            else phase_b<false, double>(T, single, fits, items, nitems, grid, smem, st);
+        }
+        return;
+    }
+    const bool is_c = phase == 2;
+    if (fp32) {
+        if (cplx) phase_ac_d<float, true>(dmax, is_c, single, fits, items, nitems, grid, threads_acq, smem, st);
+        else phase_ac_d<float, false>(dmax, is_c, single, fits, items, nitems, grid, threads_acq, smem, st);
+    } else {
+        if (cplx) phase_ac_d<double, true>(dmax, is_c, single, fits, items, nitems, grid, threads_acq, smem, st);
+        else phase_ac_d<double, false>(dmax, is_c, single, fits, items, nitems, grid, threads_acq, smem, st);
+    }
+}
+
+size_t fused_desc_size() { return sizeof(FitDesc); }
+
+void fused_make_desc(const Handle* h, ThetaPtrs th, double* out, double* tau, double* g_eta, double* g_W, double* g_v,
+                     double* g_s2, bool grad, int a, double* partials, unsigned* counters, void* desc) {
+    OutPtrs o{out, tau, g_eta, g_W, g_v, g_s2};
+    FitDesc f = make_desc(h, th, o, grad, false, a, 0);
+    f.partials = partials;
+    f.counters = counters;
+    std::memcpy(desc, &f, sizeof(FitDesc));
+}
+
+int fused_threads(int phase, int a) { return phase == 1 ? kBThreads : threads_ac(a); }
+
+namespace {
+template <typename F>
+int occ(F* fn, int threads, size_t smem) {
+    set_smem(fn, smem);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess || nb < 1) nb = 1;
+    cudaGetLastError();  // a failed query must not surface as a later launch error
+    return nb;
+}
+template <typename S, bool CPLX>
+int occ_ac(bool is_c, int dmax, int threads, size_t smem) {
+    if (!is_c) {
+        if (dmax <= 4) return occ(k_batch_a<S, CPLX, 4>, threads, smem);
+        if (dmax <= 8) return occ(k_batch_a<S, CPLX, 8>, threads, smem);
+        if (dmax <= 16) return occ(k_batch_a<S, CPLX, 16>, threads, smem);
+        return occ(k_batch_a<S, CPLX, 32>, threads, smem);
+    }
+    if (dmax <= 4) return occ(k_batch_c<S, CPLX, 4>, threads, smem);
+    if (dmax <= 8) return occ(k_batch_c<S, CPLX, 8>, threads, smem);
+    if (dmax <= 16) return occ(k_batch_c<S, CPLX, 16>, threads, smem);
+    return occ(k_batch_c<S, CPLX, 32>, threads, smem);
+}
+template <bool CPLX, typename S>
+int occ_b(int T, size_t smem) {
+    switch (T) {
+        case 1: return occ(k_batch_b<1, CPLX, S>, kBThreads, smem);
+        case 2: return occ(k_batch_b<2, CPLX, S>, kBThreads, smem);
+        case 3: return occ(k_batch_b<3, CPLX, S>, kBThreads, smem);
+        case 4: return occ(k_batch_b<4, CPLX, S>, kBThreads, smem);
+        case 5: return occ(k_batch_b<5, CPLX, S>, kBThreads, smem);
+        case 6: return occ(k_batch_b<6, CPLX, S>, kBThreads, smem);
+        case 7: return occ(k_batch_b<7, CPLX, S>, kBThreads, smem);
+        default: return occ(k_batch_b<8, CPLX, S>, kBThreads, smem);
+    }
+}
+}  // namespace
+
+int fused_resident_blocks(int phase, bool fp32, bool cplx, int T, int dmax, int threads, size_t smem) {
+    if (phase == 1) {
+        if (fp32) return cplx ? occ_b<true, float>(T, smem) : occ_b<false, float>(T, smem);
+        return cplx ? occ_b<true, double>(T, smem) : occ_b<false, double>(T, smem);
+    }
+    const bool is_c = phase == 2;
+    if (fp32) return cplx ? occ_ac<float, true>(is_c, dmax, threads, smem) : occ_ac<float, false>(is_c, dmax, threads, smem);
+    return cplx ? occ_ac<double, true>(is_c, dmax, threads, smem) : occ_ac<double, false>(is_c, dmax, threads, smem);
+}
+size_t fused_smem(int phase, int T, int C, int m, int a, bool fp32, bool cplx) {
+    const size_t es = elem_size_of(fp32, cplx);
+    return phase == 1 ? smem_b(T, C, m - a, es) : smem_ac(C, a, es);
+}
+int fused_threads_ac(int a) { return threads_ac(a); }
 
 bool fused_supported(const Handle* h) {
     int a, lgL;
@@ -623,13 +837,20 @@ void launch_fused(const Handle* h, ThetaPtrs th, bool grad, bool store_alpha, do
                   double* g_W, double* g_v, double* g_s2, cudaStream_t st) {
     int a = 0, lgL = 0;
     plan(h, &a, &lgL);
-    FusedParams p = make_params(h, th, grad, store_alpha, a, lgL);
     OutPtrs o{out, tau, g_eta, g_W, g_v, g_s2};
-    if (h->fp32) {
-        if (h->cplx) run_fused<true, float>(h, p, th, o, st);
-        else run_fused<false, float>(h, p, th, o, st);
-    } else {
-        if (h->cplx) run_fused<true, double>(h, p, th, o, st);
-        else run_fused<false, double>(h, p, th, o, st);
-    }
+    const FitDesc f = make_desc(h, th, o, grad, store_alpha, a, lgL);
+    const int C = h->ncols;
+    mtgp_prof_begin(h, "fused_a", st);
+    fused_phase(0, h->fp32, h->cplx, h->T, h->d, &f, nullptr, nullptr, 0, f.na, threads_ac(a),
+                fused_smem(0, h->T, C, f.p.m, a, h->fp32, h->cplx), st);
+    mtgp_prof_end(h, st);
+    mtgp_prof_begin(h, "fused_b", st);
+    fused_phase(1, h->fp32, h->cplx, h->T, h->d, &f, nullptr, nullptr, 0, f.nb, kBThreads,
+                fused_smem(1, h->T, C, f.p.m, a, h->fp32, h->cplx), st);
+    mtgp_prof_end(h, st);
+    if (!grad) return;
+    mtgp_prof_begin(h, "fused_c", st);
+    fused_phase(2, h->fp32, h->cplx, h->T, h->d, &f, nullptr, nullptr, 0, f.na, threads_ac(a),
+                fused_smem(2, h->T, C, f.p.m, a, h->fp32, h->cplx), st);
+    mtgp_prof_end(h, st);
 }

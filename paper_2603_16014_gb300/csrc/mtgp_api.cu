@@ -49,10 +49,6 @@ void mtgp_prof_end(const Handle* h, cudaStream_t st) {
     p->recs.push_back(p->cur);
 }
 
-struct mtgp_s {
-    Handle h;
-};
-
 namespace {
 
 thread_local std::string g_err;

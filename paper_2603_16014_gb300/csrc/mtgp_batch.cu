@@ -1,0 +1,502 @@
+// Batched fits: many independent equal-size fits advanced together.
+//
+// Each fit keeps its own workspace (an ordinary handle).  One NLL + gradient evaluation of the whole
+// batch is three phases (kernels A, B, C of k_fused.cu); within a phase the fits are grouped into
+// classes that share a kernel specialisation -- (design kind, T) for the per-frequency FP64 solve,
+// (design kind, dimension bucket) for the generation / adjoint kernels -- and each class runs as one
+// persistent launch over a table of (fit, block) items ordered largest fit first.  Classes of one
+// phase run concurrently on side streams.  An optimiser step adds one Adam update on the packed
+// parameters (log eta, W, log v, log sigma2); a run of steps can be captured in one CUDA graph.
+// The split of each fit's transform between kernels A/C and B can be chosen by timing (autotune).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "mtgp_internal.cuh"
+
+namespace {
+
+constexpr int kSide = 16;
+
+struct Cls {
+    int phase;
+    bool cplx;
+    int key;          // T (phase B) or dimension bucket (phases A, C)
+    int2* items;      // device
+    int nitems;
+    int grid, threads;
+    size_t smem;
+};
+
+int dbucket(int d) { return d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : 32; }
+
+__global__ void k_batch_theta_in(const double* nat, double* lg, double* nv, const int* pinfo, long long np, double* m1,
+                                 double* m2) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
+        double x = nat[p];
+        lg[p] = pinfo[2 * p + 1] ? log(x) : x;
+        nv[p] = x;
+        m1[p] = 0.0;
+        m2[p] = 0.0;
+    }
+}
+
+// Adam on the packed parameters; positive parameters live in log space (chain rule d/dlog x = x d/dx).
+// The objective's value at the parameters this step used is recorded in trace (if given).
+__global__ void k_batch_adam(double* lg, double* nv, const double* g, double* m1, double* m2, const int* pinfo,
+                             long long np, const int* tstep, int step, double lr, const double* out, double* trace,
+                             int nfits) {
+    const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
+    const int t = *tstep + step + 1;
+    const double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < np; p += (long long)gridDim.x * blockDim.x) {
+        const bool islog = pinfo[2 * p + 1] != 0;
+        double gg = g[p];
+        if (islog) gg *= nv[p];
+        const double a = b1 * m1[p] + (1.0 - b1) * gg;
+        const double b = b2 * m2[p] + (1.0 - b2) * gg * gg;
+        m1[p] = a;
+        m2[p] = b;
+        const double x = lg[p] - lr * (a / c1) / (sqrt(b / c2) + eps);
+        lg[p] = x;
+        nv[p] = islog ? exp(x) : x;
+        if (trace && p < nfits) trace[(long long)step * nfits + p] = out[3 * p];
+    }
+}
+
+__global__ void k_batch_tick(int* tstep, int k) { *tstep += k; }
+
+}  // namespace
+
+struct mtgp_batch_s {
+    int nfits = 0, s = 1;
+    bool fp32 = true;
+    std::vector<mtgp_t*> fits;
+    std::vector<int> a;
+    std::vector<long long> poff, yoff, partoff;
+    long long np = 0;
+    double *th_log = nullptr, *th_nat = nullptr, *g_nat = nullptr, *m1 = nullptr, *m2 = nullptr;
+    double *out = nullptr, *tau = nullptr, *partials = nullptr;
+    unsigned* counters = nullptr;
+    int* pinfo = nullptr;
+    int* tstep = nullptr;
+    unsigned char* descs = nullptr;
+    std::vector<unsigned char> descs_host;
+    std::vector<Cls> cls[3];
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t evfork = nullptr, evjoin[kSide] = {};
+    cudaGraphExec_t gexec = nullptr;
+    int gsteps = 0;
+    double glr = 0.0;
+    double* gtrace = nullptr;
+    int nsm = 1;
+};
+
+namespace {
+
+int bfail(int code, const char* msg) {
+    mtgp_set_error(msg);
+    return code;
+}
+
+int launch_status(const char* where) {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return MTGP_OK;
+    char msg[256];
+    std::snprintf(msg, sizeof(msg), "%s: %s", where, cudaGetErrorString(e));
+    return bfail(MTGP_ERR_CUDA, msg);
+}
+
+void free_classes(mtgp_batch_s* b) {
+    for (int ph = 0; ph < 3; ++ph) {
+        for (auto& c : b->cls[ph]) cudaFree(c.items);
+        b->cls[ph].clear();
+    }
+}
+
+// (re)build descriptors, partial-sum buffers and class item tables for the current splits
+int build_plan(mtgp_batch_s* b) {
+    cudaDeviceSynchronize();  // earlier launches may still read the old tables
+    free_classes(b);
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    const size_t dsz = fused_desc_size();
+    b->partoff.assign(b->nfits + 1, 0);
+    for (int f = 0; f < b->nfits; ++f) {
+        const Handle& h = b->fits[f]->h;
+        const int NQ = 3 + h.T * (h.T + 1) / 2;
+        const int m = h.m[0], a = b->a[f];
+        b->partoff[f + 1] = b->partoff[f] + ((long long)1 << a) * NQ + ((long long)1 << (m - a)) * h.d;
+    }
+    cudaFree(b->partials);
+    b->partials = nullptr;
+    if (cudaMalloc(&b->partials, sizeof(double) * (size_t)std::max<long long>(b->partoff[b->nfits], 1)) != cudaSuccess)
+        return bfail(MTGP_ERR_CUDA, "batch partials allocation failed");
+    b->descs_host.assign(dsz * b->nfits, 0);
+    for (int f = 0; f < b->nfits; ++f) {
+        const Handle& h = b->fits[f]->h;
+        const long long o = b->poff[f];
+        const int d = h.d, T = h.T, s = b->s;
+        ThetaPtrs th{b->th_nat + o, b->th_nat + o + d, s, b->th_nat + o + d + (long long)T * s,
+                     b->th_nat + o + d + (long long)T * s + T};
+        fused_make_desc(&h, th, b->out + 3 * f, b->tau + (long long)MTGP_TMAX * f, b->g_nat + o, b->g_nat + o + d,
+                        b->g_nat + o + d + (long long)T * s, b->g_nat + o + d + (long long)T * s + T, true, b->a[f],
+                        b->partials + b->partoff[f], b->counters + 2 * f, b->descs_host.data() + dsz * f);
+    }
+    if (!b->descs) {
+        if (cudaMalloc(&b->descs, dsz * b->nfits) != cudaSuccess) return bfail(MTGP_ERR_CUDA, "batch descriptor allocation failed");
+    }
+    if (cudaMemcpy(b->descs, b->descs_host.data(), dsz * b->nfits, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bfail(MTGP_ERR_CUDA, "batch descriptor upload failed");
+    // classes, fits largest first
+    std::vector<int> order(b->nfits);
+    for (int f = 0; f < b->nfits; ++f) order[f] = f;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const Handle &hx = b->fits[x]->h, &hy = b->fits[y]->h;
+        return hx.n[0] * hx.T * hx.T > hy.n[0] * hy.T * hy.T;
+    });
+    for (int ph = 0; ph < 3; ++ph) {
+        std::map<std::pair<int, int>, std::vector<int2>> items;
+        std::map<std::pair<int, int>, std::pair<size_t, int>> res;  // smem, threads
+        for (int f : order) {
+            const Handle& h = b->fits[f]->h;
+            const int m = h.m[0], a = b->a[f];
+            const int key = ph == 1 ? h.T : dbucket(h.d);
+            auto k = std::make_pair(h.cplx ? 1 : 0, key);
+            const int nblk = ph == 1 ? (1 << a) : (1 << (m - a));
+            for (int j = 0; j < nblk; ++j) items[k].push_back(make_int2(f, j));
+            const size_t sm = fused_smem(ph, h.T, h.ncols, m, a, h.fp32, h.cplx);
+            const int th = fused_threads(ph, a);
+            auto& r = res[k];
+            r.first = std::max(r.first, sm);
+            r.second = std::max(r.second, th);
+        }
+        for (auto& kv : items) {
+            Cls c;
+            c.phase = ph;
+            c.cplx = kv.first.first != 0;
+            c.key = kv.first.second;
+            c.nitems = (int)kv.second.size();
+            c.smem = res[kv.first].first;
+            c.threads = res[kv.first].second;
+            const int T = ph == 1 ? c.key : 1;
+            const int per_sm = fused_resident_blocks(ph, b->fp32, c.cplx, T, c.key, c.threads, c.smem);
+            c.grid = std::min(c.nitems, per_sm * b->nsm);
+            if (cudaMalloc(&c.items, sizeof(int2) * c.nitems) != cudaSuccess)
+                return bfail(MTGP_ERR_CUDA, "batch item table allocation failed");
+            cudaMemcpy(c.items, kv.second.data(), sizeof(int2) * c.nitems, cudaMemcpyHostToDevice);
+            b->cls[ph].push_back(c);
+        }
+    }
+    return MTGP_OK;
+}
+
+// with MTGP_BATCH_CHECK set in the environment every class launch is checked (outside graph capture)
+void check_launch(const Cls& c, int T) {
+    static const bool on = std::getenv("MTGP_BATCH_CHECK") != nullptr;
+    if (!on) return;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        std::fprintf(stderr, "batch launch failed: %s phase=%d cplx=%d key=%d T=%d grid=%d threads=%d smem=%zu items=%d\n",
+                     cudaGetErrorString(e), c.phase, (int)c.cplx, c.key, T, c.grid, c.threads, c.smem, c.nitems);
+}
+
+// the three phases of one batched NLL + gradient evaluation on stream st (classes forked to side streams)
+void launch_eval(mtgp_batch_s* b, cudaStream_t st) {
+    for (int ph = 0; ph < 3; ++ph) {
+        const auto& cl = b->cls[ph];
+        if (cl.size() == 1) {
+            const Cls& c = cl[0];
+            const int T = ph == 1 ? c.key : 1;
+            fused_phase(ph, b->fp32, c.cplx, T, c.key, nullptr, b->descs, c.items, c.nitems, c.grid, c.threads, c.smem, st);
+            check_launch(c, T);
+            continue;
+        }
+        cudaEventRecord(b->evfork, st);
+        for (size_t i = 0; i < cl.size(); ++i) {
+            const Cls& c = cl[i];
+            cudaStream_t ss = b->side[i % kSide];
+            cudaStreamWaitEvent(ss, b->evfork, 0);
+            const int T = ph == 1 ? c.key : 1;
+            fused_phase(ph, b->fp32, c.cplx, T, c.key, nullptr, b->descs, c.items, c.nitems, c.grid, c.threads, c.smem, ss);
+            check_launch(c, T);
+        }
+        const int used = (int)std::min<size_t>(cl.size(), kSide);
+        for (int i = 0; i < used; ++i) {
+            cudaEventRecord(b->evjoin[i], b->side[i]);
+            cudaStreamWaitEvent(st, b->evjoin[i], 0);
+        }
+    }
+}
+
+void launch_steps(mtgp_batch_s* b, int steps, double lr, double* trace, cudaStream_t st) {
+    const int thr = 256;
+    const int blocks = (int)std::min<long long>((b->np + thr - 1) / thr, 4096);
+    for (int k = 0; k < steps; ++k) {
+        launch_eval(b, st);
+        k_batch_adam<<<blocks, thr, 0, st>>>(b->th_log, b->th_nat, b->g_nat, b->m1, b->m2, b->pinfo, b->np, b->tstep, k,
+                                             lr, b->out, trace, b->nfits);
+    }
+    k_batch_tick<<<1, 1, 0, st>>>(b->tstep, steps);
+}
+
+}  // namespace
+
+extern "C" {
+
+int mtgp_batch_create(mtgp_batch_t** out, int nfits, const int* kind, const int* d, const int* T, const int* m,
+                      const uint32_t* gen, const int* gen_cols, const uint32_t* shift, int s, int precision) {
+    if (!out) return bfail(MTGP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nfits < 1 || !kind || !d || !T || !m || !gen || !gen_cols || !shift)
+        return bfail(MTGP_ERR_INVALID_ARG, "nfits < 1 or NULL host array");
+    if (s < 1) return bfail(MTGP_ERR_INVALID_ARG, "s must be >= 1");
+    for (int f = 0; f < nfits; ++f)
+        if (T[f] < s) return bfail(MTGP_ERR_INVALID_ARG, "every fit needs T >= s");
+    auto* b = new mtgp_batch_s();
+    b->nfits = nfits;
+    b->s = s;
+    b->fp32 = precision == MTGP_FP32_TRANSFORM;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+    long long goff = 0, soff = 0, poff = 0, yoff = 0;
+    b->poff.push_back(0);
+    b->yoff.push_back(0);
+    std::vector<int> pinfo;
+    for (int f = 0; f < nfits; ++f) {
+        std::vector<int> mm(T[f], m[f]);
+        mtgp_t* hf = nullptr;
+        int rc = mtgp_create(&hf, kind[f], d[f], T[f], mm.data(), gen + goff, gen_cols[f], shift + soff, precision);
+        if (rc) {
+            mtgp_batch_destroy(b);
+            return rc;
+        }
+        b->fits.push_back(hf);
+        int a = 0, lgL = 0;
+        if (!fused_plan(m[f], hf->h.ncols, b->fp32, hf->h.cplx, -1, &a, &lgL)) {
+            mtgp_batch_destroy(b);
+            return bfail(MTGP_ERR_UNSUPPORTED, "a fit's size is not handled by the fused kernels (m >= 4, tiles <= 96 KB)");
+        }
+        b->a.push_back(a);
+        goff += kind[f] == MTGP_LATTICE ? d[f] : (long long)d[f] * gen_cols[f];
+        soff += (long long)T[f] * d[f];
+        const long long npf = d[f] + (long long)T[f] * s + T[f] + 1;
+        for (long long q = 0; q < npf; ++q) {
+            const bool is_w = q >= d[f] && q < d[f] + (long long)T[f] * s;
+            pinfo.push_back(f);
+            pinfo.push_back(is_w ? 0 : 1);
+        }
+        poff += npf;
+        yoff += (long long)T[f] << m[f];
+        b->poff.push_back(poff);
+        b->yoff.push_back(yoff);
+    }
+    b->np = poff;
+    bool ok = cudaMalloc(&b->th_log, sizeof(double) * poff) == cudaSuccess &&
+              cudaMalloc(&b->th_nat, sizeof(double) * poff) == cudaSuccess &&
+              cudaMalloc(&b->g_nat, sizeof(double) * poff) == cudaSuccess &&
+              cudaMalloc(&b->m1, sizeof(double) * poff) == cudaSuccess &&
+              cudaMalloc(&b->m2, sizeof(double) * poff) == cudaSuccess &&
+              cudaMalloc(&b->out, sizeof(double) * 3 * nfits) == cudaSuccess &&
+              cudaMalloc(&b->tau, sizeof(double) * MTGP_TMAX * nfits) == cudaSuccess &&
+              cudaMalloc(&b->counters, sizeof(unsigned) * 2 * nfits) == cudaSuccess &&
+              cudaMalloc(&b->pinfo, sizeof(int) * pinfo.size()) == cudaSuccess &&
+              cudaMalloc(&b->tstep, sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        mtgp_batch_destroy(b);
+        return bfail(MTGP_ERR_CUDA, "batch allocation failed");
+    }
+    cudaMemcpy(b->pinfo, pinfo.data(), sizeof(int) * pinfo.size(), cudaMemcpyHostToDevice);
+    cudaMemset(b->counters, 0, sizeof(unsigned) * 2 * nfits);
+    cudaMemset(b->tstep, 0, sizeof(int));
+    cudaMemset(b->th_nat, 0, sizeof(double) * poff);
+    for (int i = 0; i < kSide; ++i) {
+        cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&b->evjoin[i], cudaEventDisableTiming);
+    }
+    cudaEventCreateWithFlags(&b->evfork, cudaEventDisableTiming);
+    int rc = build_plan(b);
+    if (rc) {
+        mtgp_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return MTGP_OK;
+}
+
+int mtgp_batch_destroy(mtgp_batch_t* b) {
+    if (!b) return MTGP_OK;
+    cudaDeviceSynchronize();
+    free_classes(b);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (auto* f : b->fits) mtgp_destroy(f);
+    void* ptrs[] = {b->th_log, b->th_nat, b->g_nat, b->m1, b->m2, b->out, b->tau, b->partials, b->counters, b->pinfo,
+                    b->tstep, b->descs};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int i = 0; i < kSide; ++i) {
+        if (b->side[i]) cudaStreamDestroy(b->side[i]);
+        if (b->evjoin[i]) cudaEventDestroy(b->evjoin[i]);
+    }
+    if (b->evfork) cudaEventDestroy(b->evfork);
+    delete b;
+    return MTGP_OK;
+}
+
+int mtgp_batch_layout(const mtgp_batch_t* b, long long* param_offsets, long long* y_offsets) {
+    if (!b || !param_offsets || !y_offsets) return bfail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    for (int f = 0; f <= b->nfits; ++f) {
+        param_offsets[f] = b->poff[f];
+        y_offsets[f] = b->yoff[f];
+    }
+    return MTGP_OK;
+}
+
+int mtgp_batch_set_y(mtgp_batch_t* b, const double* y, cudaStream_t st) {
+    if (!b || !y) return bfail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    for (int f = 0; f < b->nfits; ++f) {
+        int rc = mtgp_set_y(b->fits[f], y + b->yoff[f], st);
+        if (rc) return rc;
+    }
+    return MTGP_OK;
+}
+
+int mtgp_batch_set_theta(mtgp_batch_t* b, const double* theta, cudaStream_t st) {
+    if (!b || !theta) return bfail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    const int blocks = (int)std::min<long long>((b->np + 255) / 256, 4096);
+    k_batch_theta_in<<<blocks, 256, 0, st>>>(theta, b->th_log, b->th_nat, b->pinfo, b->np, b->m1, b->m2);
+    cudaMemsetAsync(b->tstep, 0, sizeof(int), st);
+    return launch_status("mtgp_batch_set_theta");
+}
+
+int mtgp_batch_get_theta(mtgp_batch_t* b, double* theta, cudaStream_t st) {
+    if (!b || !theta) return bfail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    cudaMemcpyAsync(theta, b->th_nat, sizeof(double) * b->np, cudaMemcpyDeviceToDevice, st);
+    return MTGP_OK;
+}
+
+int mtgp_batch_nll_grad(mtgp_batch_t* b, double* nll, double* grad, cudaStream_t st) {
+    if (!b) return bfail(MTGP_ERR_INVALID_ARG, "NULL handle");
+    for (auto* f : b->fits)
+        if (!f->h.y_set) return bfail(MTGP_ERR_STATE, "mtgp_batch_set_y must be called first");
+    launch_eval(b, st);
+    if (nll) {
+        // out holds [NLL, quad, logdet] per fit
+        cudaMemcpy2DAsync(nll, sizeof(double), b->out, 3 * sizeof(double), sizeof(double), b->nfits,
+                          cudaMemcpyDeviceToDevice, st);
+    }
+    if (grad) cudaMemcpyAsync(grad, b->g_nat, sizeof(double) * b->np, cudaMemcpyDeviceToDevice, st);
+    return launch_status("mtgp_batch_nll_grad");
+}
+
+int mtgp_batch_adam(mtgp_batch_t* b, int steps, double lr, int use_graph, double* trace, cudaStream_t st) {
+    if (!b || steps < 1) return bfail(MTGP_ERR_INVALID_ARG, "NULL handle or steps < 1");
+    for (auto* f : b->fits)
+        if (!f->h.y_set) return bfail(MTGP_ERR_STATE, "mtgp_batch_set_y must be called first");
+    if (!use_graph) {
+        launch_steps(b, steps, lr, trace, st);
+        return launch_status("mtgp_batch_adam");
+    }
+    if (!b->gexec || b->gsteps != steps || b->glr != lr || b->gtrace != trace) {
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+        cudaGraph_t g;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return bfail(MTGP_ERR_CUDA, "cudaStreamBeginCapture failed (stream must be a non-default stream)");
+        launch_steps(b, steps, lr, trace, st);
+        if (cudaStreamEndCapture(st, &g) != cudaSuccess) return bfail(MTGP_ERR_CUDA, "graph capture failed");
+        cudaError_t e = cudaGraphInstantiate(&b->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return bfail(MTGP_ERR_CUDA, "graph instantiation failed");
+        b->gsteps = steps;
+        b->glr = lr;
+        b->gtrace = trace;
+    }
+    return cudaGraphLaunch(b->gexec, st) == cudaSuccess ? MTGP_OK : bfail(MTGP_ERR_CUDA, "graph launch failed");
+}
+
+int mtgp_batch_autotune(mtgp_batch_t* b, int reps, int* chosen, cudaStream_t st) {
+    if (!b) return bfail(MTGP_ERR_INVALID_ARG, "NULL handle");
+    for (auto* f : b->fits)
+        if (!f->h.y_set) return bfail(MTGP_ERR_STATE, "mtgp_batch_set_y must be called first");
+    if (reps < 1) reps = 3;
+    const size_t dsz = fused_desc_size();
+    std::vector<unsigned char> desc(dsz);
+    std::map<std::tuple<int, int, int, int>, int> best;  // (kind, T, m, dbucket) -> split
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double* part = nullptr;
+    unsigned* cnt = nullptr;
+    long long partcap = 0;
+    for (int f = 0; f < b->nfits; ++f) {
+        const Handle& h = b->fits[f]->h;
+        const int m = h.m[0];
+        auto key = std::make_tuple(h.kind, h.T, m, dbucket(h.d));
+        if (best.count(key)) continue;
+        const long long o = b->poff[f];
+        ThetaPtrs th{b->th_nat + o, b->th_nat + o + h.d, b->s, b->th_nat + o + h.d + (long long)h.T * b->s,
+                     b->th_nat + o + h.d + (long long)h.T * b->s + h.T};
+        float best_ms = 1e30f;
+        int best_a = b->a[f];
+        for (int a = 2; a <= m - 2; ++a) {
+            int aa, lgL;
+            if (!fused_plan(m, h.ncols, h.fp32, h.cplx, a, &aa, &lgL)) continue;
+            const int NQ = 3 + h.T * (h.T + 1) / 2;
+            const long long need = ((long long)1 << a) * NQ + ((long long)1 << (m - a)) * h.d;
+            if (need > partcap) {
+                cudaFree(part);
+                partcap = need;
+                if (cudaMalloc(&part, sizeof(double) * partcap) != cudaSuccess) return bfail(MTGP_ERR_CUDA, "autotune scratch");
+            }
+            if (!cnt) {
+                if (cudaMalloc(&cnt, 2 * sizeof(unsigned)) != cudaSuccess) return bfail(MTGP_ERR_CUDA, "autotune scratch");
+                cudaMemset(cnt, 0, 2 * sizeof(unsigned));
+            }
+            fused_make_desc(&h, th, b->out + 3 * f, nullptr, b->g_nat + o, b->g_nat + o + h.d,
+                            b->g_nat + o + h.d + (long long)h.T * b->s, b->g_nat + o + h.d + (long long)h.T * b->s + h.T,
+                            true, a, part, cnt, desc.data());
+            float tot = 0.f;
+            for (int r = 0; r <= reps; ++r) {
+                cudaEventRecord(e0, st);
+                for (int ph = 0; ph < 3; ++ph) {
+                    const int grid = ph == 1 ? (1 << a) : (1 << (m - a));
+                    fused_phase(ph, h.fp32, h.cplx, h.T, h.d, desc.data(), nullptr, nullptr, 0, grid,
+                                fused_threads(ph, a), fused_smem(ph, h.T, h.ncols, m, a, h.fp32, h.cplx), st);
+                }
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (r > 0) tot += ms;  // first run warms up
+            }
+            if (tot < best_ms) {
+                best_ms = tot;
+                best_a = a;
+            }
+        }
+        best[key] = best_a;
+    }
+    cudaFree(part);
+    cudaFree(cnt);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int f = 0; f < b->nfits; ++f) {
+        const Handle& h = b->fits[f]->h;
+        b->a[f] = best[std::make_tuple(h.kind, h.T, h.m[0], dbucket(h.d))];
+        if (chosen) chosen[f] = b->a[f];
+    }
+    return build_plan(b);
+}
+
+}  // extern "C"

@@ -166,6 +166,20 @@ bool fused_supported(const Handle* h);
 long long fused_partials_len(const Handle* h);
 void launch_fused(const Handle* h, ThetaPtrs th, bool grad, bool store_alpha, double* out, double* tau,
                   double* g_eta, double* g_W, double* g_v, double* g_s2, cudaStream_t st);
+// split of n = 2^m between kernels A/C (2^a) and B (2^(m-a)); a_pref < 0 picks the default
+bool fused_plan(int m, int ncols, bool fp32, bool cplx, int a_pref, int* a_out, int* lgL_out);
+// device descriptor of one fit (fused_desc_size() bytes, written to desc) with split a and the given
+// partial-sum buffer (2^a NQ + 2^(m-a) d doubles) and counters (2 unsigned)
+size_t fused_desc_size();
+void fused_make_desc(const Handle* h, ThetaPtrs th, double* out, double* tau, double* g_eta, double* g_W,
+                     double* g_v, double* g_s2, bool grad, int a, double* partials, unsigned* counters, void* desc);
+// one phase (0 = A, 1 = B, 2 = C) of one class: `single` (host descriptor) launches one fit with a grid of
+// its blocks, otherwise a persistent grid walks `nitems` (fit, block) items over the device descriptors
+void fused_phase(int phase, bool fp32, bool cplx, int T, int dmax, const void* single, const void* fits,
+                 const int2* items, int nitems, int grid, int threads, size_t smem, cudaStream_t st);
+size_t fused_smem(int phase, int T, int C, int m, int a, bool fp32, bool cplx);
+int fused_threads(int phase, int a);
+int fused_resident_blocks(int phase, bool fp32, bool cplx, int T, int dmax, int threads, size_t smem);
 
 // records the message returned by mtgp_last_error_string for the calling thread (mtgp_api.cu)
 void mtgp_set_error(const char* msg);
@@ -232,3 +246,7 @@ struct Handle {
 };
 
 __device__ __forceinline__ void set_status(int* st, int bit) { atomicOr(st, bit); }
+
+struct mtgp_s {
+    Handle h;
+};

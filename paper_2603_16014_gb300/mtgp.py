@@ -171,6 +171,102 @@ def nll_equal_static(kind: str, d: int, T: int, m: int, gen, shift, y, eta, W, v
     return out, tau, status
 
 
+def _carr(ctype, vals):
+    return (ctype * len(vals))(*vals)
+
+
+class Batch:
+    """Many independent equal-size fits evaluated / optimised together (C ABI mtgp_batch_*).
+
+    ``problems``: objects with kind, d, m (equal sizes), gen, shift (e.g. inputs.Problem).
+    Parameters are packed per fit as [eta, W (T x s), v, sigma2].
+    """
+
+    def __init__(self, problems, s: int = 2, precision: str = "fp32"):
+        self.problems = list(problems)
+        n = len(self.problems)
+        kind = [LATTICE if p.kind == "lattice" else DNET for p in self.problems]
+        d = [int(p.d) for p in self.problems]
+        T = [len(p.m) for p in self.problems]
+        m = [int(p.m[0]) for p in self.problems]
+        gens, gcols, shifts = [], [], []
+        for p, k in zip(self.problems, kind):
+            g = np.asarray(p.gen, dtype=np.uint32)
+            gens.append(g.ravel())
+            gcols.append(int(g.shape[1]) if (k == DNET and g.ndim == 2) else 0)
+            shifts.append(np.asarray(p.shift, dtype=np.uint32).ravel())
+        gen = np.ascontiguousarray(np.concatenate(gens))
+        shift = np.ascontiguousarray(np.concatenate(shifts))
+        h = ctypes.c_void_p()
+        check(lib().mtgp_batch_create(ctypes.byref(h), n, _carr(ctypes.c_int, kind), _carr(ctypes.c_int, d),
+                                      _carr(ctypes.c_int, T), _carr(ctypes.c_int, m),
+                                      gen.ctypes.data_as(ctypes.c_void_p), _carr(ctypes.c_int, gcols),
+                                      shift.ctypes.data_as(ctypes.c_void_p), s,
+                                      FP32_TRANSFORM if precision == "fp32" else FP64), "mtgp_batch_create")
+        self._h = h
+        self.n, self.s = n, s
+        po = (ctypes.c_longlong * (n + 1))()
+        yo = (ctypes.c_longlong * (n + 1))()
+        check(lib().mtgp_batch_layout(self._h, po, yo), "mtgp_batch_layout")
+        self.param_offsets = list(po)
+        self.y_offsets = list(yo)
+        self.nparams = self.param_offsets[-1]
+
+    def pack(self, thetas) -> np.ndarray:
+        """[(eta, W, v, sigma2), ...] -> packed natural parameters."""
+        return np.concatenate([np.concatenate([np.ravel(e), np.ravel(W), np.ravel(v), np.ravel([s2])])
+                               for (e, W, v, s2) in thetas]).astype(np.float64)
+
+    def unpack(self, packed):
+        out = []
+        packed = np.asarray(packed)
+        for f, p in enumerate(self.problems):
+            o, d, T = self.param_offsets[f], p.d, len(p.m)
+            x = packed[o:self.param_offsets[f + 1]]
+            out.append((x[:d], x[d:d + T * self.s].reshape(T, self.s), x[d + T * self.s:d + T * self.s + T],
+                        float(x[-1])))
+        return out
+
+    def set_y(self, y, stream=None):
+        self._y = _dev(y)
+        check(lib().mtgp_batch_set_y(self._h, _ptr(self._y), _stream(stream)), "mtgp_batch_set_y")
+
+    def set_theta(self, packed, stream=None):
+        self._t = _dev(packed)
+        check(lib().mtgp_batch_set_theta(self._h, _ptr(self._t), _stream(stream)), "mtgp_batch_set_theta")
+
+    def get_theta(self, stream=None) -> torch.Tensor:
+        t = torch.empty(self.nparams, dtype=torch.float64, device="cuda")
+        check(lib().mtgp_batch_get_theta(self._h, _ptr(t), _stream(stream)), "mtgp_batch_get_theta")
+        return t
+
+    def nll_grad(self, stream=None):
+        nll = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        g = torch.empty(self.nparams, dtype=torch.float64, device="cuda")
+        check(lib().mtgp_batch_nll_grad(self._h, _ptr(nll), _ptr(g), _stream(stream)), "mtgp_batch_nll_grad")
+        return nll, g
+
+    def adam(self, steps: int, lr: float, graph: bool = True, trace=None, stream=None):
+        check(lib().mtgp_batch_adam(self._h, steps, lr, 1 if graph else 0, _ptr(trace), _stream(stream)),
+              "mtgp_batch_adam")
+
+    def autotune(self, reps: int = 3, stream=None):
+        chosen = (ctypes.c_int * self.n)()
+        check(lib().mtgp_batch_autotune(self._h, reps, chosen, _stream(stream)), "mtgp_batch_autotune")
+        return list(chosen)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            check(lib().mtgp_batch_destroy(self._h), "mtgp_batch_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class NLLFunction(torch.autograd.Function):
     """NLL as a differentiable function of (eta, W, v, sigma2) through the hand-written adjoint."""
 
