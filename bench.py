@@ -43,10 +43,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu", action="store_true",
                     help="only warm-up + K steps of the workload, no extras (for ncu captures)")
-    ap.add_argument("--workload", default="nllgrad", choices=["nllgrad", "batch512"],
+    ap.add_argument("--workload", default="nllgrad", choices=["nllgrad", "batch512", "proposal"],
                     help="nllgrad: the headline NLL+gradient evaluation; batch512: 512 heterogeneous fits, "
                          "Adam steps in one CUDA graph vs a plain per-fit optimiser")
     ap.add_argument("--fits", type=int, default=512)
+    ap.add_argument("--train-fits", type=int, default=2048, help="proposal: training fits")
+    ap.add_argument("--label-steps", type=int, default=1000, help="proposal: Adam steps that label a training fit")
+    ap.add_argument("--train-steps", type=int, default=3000, help="proposal: MLP Adam steps")
+    ap.add_argument("--eval-fits", type=int, default=256, help="proposal: held-out fits")
+    ap.add_argument("--eval-steps", type=int, default=2000, help="proposal: Adam steps per held-out run")
+    ap.add_argument("--eval-precision", default="fp64", choices=["fp64", "fp32"])
     return ap.parse_args()
 
 
@@ -425,6 +431,180 @@ def run_batch(args):
     b.close()
 
 
+# ----------------------------------------------------------------------------- learned proposal
+
+def _synth_worker(job):
+    from paper_2603_16014_gb300 import inputs
+    p, X = job
+    return inputs.synth_y(p, X)
+
+
+def _synth_all(pool, probs):
+    """Responses of every fit: design points from the library on the GPU, synthesis on host cores."""
+    import numpy as np
+
+    from paper_2603_16014_gb300.mtgp import MTGP
+    jobs = []
+    for p in probs:
+        m = MTGP.from_problem(p, "fp64")
+        X = m.points().cpu().numpy().view(np.uint32)
+        jobs.append((p, [X[i * p.n[0]:(i + 1) * p.n[0]] for i in range(p.T)]))
+        m.close()
+    return pool.map(_synth_worker, jobs, chunksize=4)
+
+
+def heldout_problems(nfits: int, seed: int = 7):
+    """Held-out fits: T = 4, n = 2^16 per task, d = 8, half lattices and half digital nets; true
+    parameters drawn as for the mixed batch."""
+    import numpy as np
+
+    from paper_2603_16014_gb300 import inputs
+    rng = np.random.default_rng([seed, 5151])
+    probs = []
+    for f in range(nfits):
+        kind = "lattice" if f < nfits // 2 else "dnet"
+        eta = float(np.exp(rng.uniform(np.log(0.1), np.log(2.0))))
+        v = float(np.exp(rng.uniform(np.log(0.01), np.log(1.0))))
+        s2 = float(np.exp(rng.uniform(np.log(1e-8), np.log(1e-4))))
+        probs.append(inputs.make_problem(kind, 8, (16,) * 4, seed=int(rng.integers(1 << 30)), s=2, eta=eta, v=v,
+                                         sigma2=s2, recipe="walshcos32", mmax=16))
+    return probs
+
+
+def steps_to_target(trace, target):
+    """First step index whose NLL is within 1e-6 (relative) of target, per fit (-1 if never)."""
+    import numpy as np
+    ok = trace <= (target + 1e-6 * np.abs(target))[None, :]
+    first = np.argmax(ok, axis=0)
+    return np.where(ok.any(axis=0), first, -1)
+
+
+def run_proposal(args):
+    """Train the proposal network on fits labelled by the batched optimiser, then count the Adam
+    steps held-out fits need to reach the plain fit's NLL from the default start and from the
+    proposal."""
+    import multiprocessing as mp
+
+    import numpy as np
+    pool = mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1))  # before any CUDA call
+    import torch
+
+    from paper_2603_16014_gb300.mtgp import Batch
+    from paper_2603_16014_gb300.proposal import MLP, propose, train
+
+    torch.cuda.set_device(0)
+    lr = 0.05
+    stream = torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    feats, tgts, masks = [], [], []
+    n_ok = 0
+    t_lab = 0.0
+    t0 = time.perf_counter()
+    for c in range(0, args.train_fits, 512):
+        probs = batch_problems(min(512, args.train_fits - c), seed=1000 + c)
+        ys = _synth_all(pool, probs)
+        b = Batch(probs, s=2, precision="fp32")
+        b.set_y(torch.from_numpy(np.concatenate(ys)))
+        with torch.cuda.stream(stream):
+            b.set_theta(torch.from_numpy(b.pack([default_theta(p) for p in probs])))
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            b.adam(args.label_steps, lr, graph=True)
+            e1.record(stream)
+            f = b.features()
+            t, mk = b.targets()
+            stream.synchronize()
+        t_lab += e0.elapsed_time(e1) / 1e3
+        feats.append(f)
+        tgts.append(t)
+        masks.append(mk)
+        n_ok += int((mk.sum(1) > 0).sum().item())
+        b.close()
+    gen_s = time.perf_counter() - t0 - t_lab
+    X, Y, M = torch.cat(feats), torch.cat(tgts), torch.cat(masks)
+    net = MLP(max_batch=1024)
+    net.set_params(net.init_params(0))
+    with torch.cuda.stream(stream):
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        losses = train(net, X, Y, M, steps=args.train_steps, batch=256, lr=1e-3, seed=1, lr_final=3e-5)
+        e1.record(stream)
+        stream.synchronize()
+    t_train = e0.elapsed_time(e1) / 1e3
+    losses = losses.cpu().numpy()
+
+    probs = heldout_problems(args.eval_fits)
+    ys = _synth_all(pool, probs)
+    pool.close()
+    b = Batch(probs, s=2, precision=args.eval_precision)
+    b.set_y(torch.from_numpy(np.concatenate(ys)))
+    S = args.eval_steps
+    theta0 = torch.from_numpy(b.pack([default_theta(p) for p in probs]))
+    traces = {}
+    with torch.cuda.stream(stream):
+        # time of one batched optimiser step (graph replay after a warm-up replay) and of the proposal
+        kt = 20
+        b.set_theta(theta0)
+        b.adam(kt, lr, graph=True)
+        e0, e1, e2 = ev(), ev(), ev()
+        e0.record(stream)
+        propose(b, net, stream)
+        e1.record(stream)
+        b.adam(kt, lr, graph=True)
+        e2.record(stream)
+        stream.synchronize()
+        prop_ms, step_ms = e0.elapsed_time(e1), e1.elapsed_time(e2) / kt
+        # the optimiser traces (same kernels launched eagerly; identical results to the graph)
+        for name in ("plain", "proposal"):
+            tr = torch.zeros(S * len(probs), dtype=torch.float64, device="cuda")
+            if name == "plain":
+                b.set_theta(theta0)
+            else:
+                propose(b, net, stream)
+            b.adam(S, lr, graph=False, trace=tr)
+            stream.synchronize()
+            traces[name] = tr.view(S, -1).cpu().numpy()
+    b.close()
+    plain, prop = traces["plain"], traces["proposal"]
+    with np.errstate(invalid="ignore"):
+        target = np.nanmin(np.where(np.isfinite(plain), plain, np.nan), axis=0)
+    valid = np.isfinite(target)
+    k_plain = steps_to_target(plain[:, valid], target[valid]) + 1
+    k_prop = steps_to_target(prop[:, valid], target[valid])
+    reached = k_prop >= 0
+    k_prop = np.where(reached, k_prop + 1, S)           # unreached runs count as S (censored)
+    med_plain = float(np.median(k_plain))
+    med_prop = float(np.median(k_prop))
+
+    def gap(k):
+        """median relative NLL excess over the target after k steps"""
+        k = min(k, S - 1)
+        with np.errstate(invalid="ignore"):
+            return {"plain": float(np.nanmedian((plain[k, valid] - target[valid]) / np.abs(target[valid]))),
+                    "proposal": float(np.nanmedian((prop[k, valid] - target[valid]) / np.abs(target[valid])))}
+    line = {
+        "metric": "learned proposal: median Adam steps for held-out fits to reach the plain fit's NLL (1e-6 rel)",
+        "value": med_prop, "unit": "steps", "higher_is_better": False, "n_gpus": 1,
+        "plain_median_steps": med_plain, "reached_fraction": float(reached.mean()),
+        "valid_fits": int(valid.sum()),
+        "proposal_first_nll_better_fraction": float(np.mean(prop[0, valid] < plain[0, valid])),
+        "relative_nll_excess": {str(k): gap(k) for k in (0, 50, 200, 1000)},
+        "wall_ms_to_target": {"plain": med_plain * step_ms, "proposal": prop_ms + med_prop * step_ms},
+        "ms_per_batched_step": step_ms, "proposal_overhead_ms": prop_ms,
+        "plain_converged_fraction": float(np.mean(np.abs(plain[-1, valid] - plain[-2, valid])
+                                                  <= 1e-10 * np.abs(plain[-1, valid]))),
+        "train": {"fits": args.train_fits, "finite_labels": n_ok, "label_steps": args.label_steps, "label_s": t_lab,
+                  "host_input_s": gen_s, "mlp_steps": args.train_steps, "mlp_train_s": t_train,
+                  "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-50:].mean())},
+        "config": {"workload": "proposal_heldout", "eval_fits": len(probs), "T": 4, "n": 65536, "d": 8,
+                   "kinds": "half lattice, half digital net", "eval_precision": args.eval_precision,
+                   "eval_steps": S, "lr": lr, "mlp": "258-256-256-256-37 BF16 weights / FP32 accumulate",
+                   "train_set": "mixed fits n = 2^U{8..16}, T ~ U{2..8}, d ~ U{2..12}, labelled by batched Adam"},
+        "data": "synthetic",
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- reference (oracle)
 
 def run_reference(args, rank, world):
@@ -473,6 +653,9 @@ def main():
         return
     if args.workload == "batch512":
         run_batch(args)
+        return
+    if args.workload == "proposal":
+        run_proposal(args)
         return
     run_ours(args, rank, world, local_rank)
 

@@ -214,6 +214,66 @@ int mtgp_batch_nll_grad(mtgp_batch_t* b, double* nll, double* grad, cudaStream_t
 int mtgp_batch_adam(mtgp_batch_t* b, int steps, double lr, int use_graph, double* trace, cudaStream_t stream);
 int mtgp_batch_autotune(mtgp_batch_t* b, int reps, int* chosen, cudaStream_t stream);
 
+/*
+ * Learned proposal of starting hyper-parameters.  The paper has no counterpart: it starts every fit's
+ * optimiser (Sec. 4.1) from a fixed point.  A small MLP maps a fixed-size spectral summary of a fit
+ * to its parameters; starting the optimiser there saves steps when the prediction is close.
+ *
+ * mtgp_batch_features -- feat (device, nfits x 258 FP32, row per fit): for each caller task t < 8 and
+ *   bin k < 32, log(mean |yhat_t(f)|^2 + 1e-30) over the frequencies f = 1..n-1 with
+ *   bin(f) = floor(4 q(f) / m), q(f) = 8 floor(log2 f) + (the three bits of f after its leading one,
+ *   zero-filled), yhat_t = V^dagger y_t of Sec. 3.3 (computed by mtgp_batch_set_y, which must come
+ *   first); an empty bin repeats the previous bin; tasks t >= T are 0; then m and d.
+ * mtgp_batch_targets -- target, mask (device, nfits x 37 FP32): from the current parameters
+ *   [log eta_j (j < 12), W (8 x 2, row-major), log v_t (t < 8), log sigma2], mask 1 where the entry
+ *   exists (j < d, t < T).  W is canonicalised first: multiplied on the right by the orthogonal 2 x 2
+ *   matrix that gives W[0][1] = 0, W[0][0] >= 0, W[1][1] >= 0 (R = W W^T + diag(v) is unchanged).
+ *   A fit with a non-finite entry (e.g. an optimiser run that diverged) gets target 0 and mask 0.
+ * mtgp_batch_set_theta_proposal -- pred (device, nfits x 37 FP32, layout as the targets) becomes the
+ *   parameters: log entries are clamped to [-40, 20] and exponentiated, W is taken as is.  Resets the
+ *   Adam moments and step count like mtgp_batch_set_theta.
+ * All three need s = 2 and d <= 12 for every fit (else MTGP_ERR_UNSUPPORTED); the first call builds a
+ * small per-fit table on the device (synchronous allocation).
+ */
+int mtgp_batch_features(mtgp_batch_t* b, float* feat, cudaStream_t stream);
+int mtgp_batch_targets(mtgp_batch_t* b, float* target, float* mask, cudaStream_t stream);
+int mtgp_batch_set_theta_proposal(mtgp_batch_t* b, const float* pred, cudaStream_t stream);
+
+/*
+ * Multilayer perceptron with BF16 weights and FP32 accumulation (the proposal network): L layers,
+ * h_{l+1} = act(h_l W_l^T + b_l) with ReLU on hidden layers and the identity on the last; the input
+ * is standardised x' = (x - mu) / sd per column first.  Masters are FP32; the GEMMs read BF16 copies
+ * of the weights, of x' and of the hidden activations, and accumulate in FP32 on the tensor cores.
+ *
+ * mtgp_mlp_create -- widths (host, nlayers + 1 entries, each 1..4096), max_batch rows per call.
+ *   Weights start at zero with mu = 0, sd = 1: set them with mtgp_mlp_set_params.
+ * mtgp_mlp_set_params / mtgp_mlp_get_params -- params (host FP32): per layer W_l (out x in, row-major)
+ *   then b_l (out); mu, sd (host, widths[0] each, NULL to keep mu = 0 / sd = 1 on set, or to skip on
+ *   get).  set also clears the optimiser state.  Both synchronise the device.
+ * mtgp_mlp_fit_scaling -- mu and sd from the columns of x (device, rows x widths[0]); sd is floored
+ *   at 1e-3.
+ * mtgp_mlp_forward -- y (device, B x widths[L]) from x (device, B x widths[0]); 1 <= B <= max_batch.
+ * mtgp_mlp_gradients -- masked squared loss sum(mask (out - target)^2) / max(sum(mask), 1) over the
+ *   batch and its gradient.  rows (device, B int, or NULL for 0..B-1) selects the rows of x, target
+ *   and mask (each with widths[0] or widths[L] columns) that form the batch; every entry must index
+ *   a row of those arrays (not checked).  loss (device, 1 float)
+ *   and grads (device, packed like params) may be NULL.
+ * mtgp_mlp_train_step -- one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr on
+ *   the same loss; loss as above.
+ * The handle's buffers are reused by every call: calls on one handle must be ordered on one stream.
+ */
+typedef struct mtgp_mlp_s mtgp_mlp_t;
+int mtgp_mlp_create(mtgp_mlp_t** out, int nlayers, const int* widths, int max_batch);
+int mtgp_mlp_destroy(mtgp_mlp_t* m);
+int mtgp_mlp_set_params(mtgp_mlp_t* m, const float* params, const float* mu, const float* sd);
+int mtgp_mlp_get_params(mtgp_mlp_t* m, float* params, float* mu, float* sd);
+int mtgp_mlp_fit_scaling(mtgp_mlp_t* m, int rows, const float* x, cudaStream_t stream);
+int mtgp_mlp_forward(mtgp_mlp_t* m, int B, const float* x, float* y, cudaStream_t stream);
+int mtgp_mlp_gradients(mtgp_mlp_t* m, int B, const float* x, const float* target, const float* mask,
+                       const int* rows, float* grads, float* loss, cudaStream_t stream);
+int mtgp_mlp_train_step(mtgp_mlp_t* m, int B, const float* x, const float* target, const float* mask,
+                        const int* rows, float lr, float* loss, cudaStream_t stream);
+
 /* mtgp_workspace_bytes -- device bytes the handle holds (for capacity planning). */
 long long mtgp_workspace_bytes(const mtgp_t* h);
 

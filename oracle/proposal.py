@@ -17,7 +17,8 @@ not the paper's):
   * targets (37 values): 12 x log eta_j, 8 x 2 entries of W, 8 x log v_t, log sigma2, with a mask that
     is 0 for j >= d and for tasks t >= T.  R = W W^T + diag(v) does not change when W is multiplied on
     the right by an orthogonal 2 x 2 matrix, so W is first brought to the canonical form with
-    W[0, 1] = 0, W[0, 0] >= 0, W[1, 1] >= 0 (a rotation, then the sign of column 1).
+    W[0, 1] = 0, W[0, 0] >= 0, W[1, 1] >= 0 (a rotation, then the sign of column 1).  A fit whose
+    parameters give a non-finite entry (a diverged optimiser run) is left out: target 0, mask 0.
 """
 from __future__ import annotations
 
@@ -83,15 +84,18 @@ def targets(eta, W, v, sigma2):
     d, T = len(eta), len(v)
     t = np.zeros(NOUT)
     mk = np.zeros(NOUT)
-    t[:d] = np.log(eta)
-    mk[:d] = 1
-    Wc = canonical_w(W)
-    t[DMAXP:DMAXP + 2 * T] = Wc.ravel()
-    mk[DMAXP:DMAXP + 2 * T] = 1
-    t[DMAXP + 2 * NT:DMAXP + 2 * NT + T] = np.log(v)
-    mk[DMAXP + 2 * NT:DMAXP + 2 * NT + T] = 1
-    t[-1] = np.log(sigma2)
-    mk[-1] = 1
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t[:d] = np.log(eta)
+        mk[:d] = 1
+        Wc = canonical_w(W)
+        t[DMAXP:DMAXP + 2 * T] = Wc.ravel()
+        mk[DMAXP:DMAXP + 2 * T] = 1
+        t[DMAXP + 2 * NT:DMAXP + 2 * NT + T] = np.log(v)
+        mk[DMAXP + 2 * NT:DMAXP + 2 * NT + T] = 1
+        t[-1] = np.log(sigma2)
+        mk[-1] = 1
+    if not np.all(np.isfinite(t)):
+        return np.zeros(NOUT), np.zeros(NOUT)
     return t, mk
 
 

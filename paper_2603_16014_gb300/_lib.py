@@ -46,6 +46,17 @@ _SIGS = {
     "mtgp_batch_nll_grad": (_i, [_p, _p, _p, _p]),
     "mtgp_batch_adam": (_i, [_p, _i, ctypes.c_double, _i, _p, _p]),
     "mtgp_batch_autotune": (_i, [_p, _i, _p, _p]),
+    "mtgp_batch_features": (_i, [_p, _p, _p]),
+    "mtgp_batch_targets": (_i, [_p, _p, _p, _p]),
+    "mtgp_batch_set_theta_proposal": (_i, [_p, _p, _p]),
+    "mtgp_mlp_create": (_i, [ctypes.POINTER(_p), _i, _p, _i]),
+    "mtgp_mlp_destroy": (_i, [_p]),
+    "mtgp_mlp_set_params": (_i, [_p, _p, _p, _p]),
+    "mtgp_mlp_get_params": (_i, [_p, _p, _p, _p]),
+    "mtgp_mlp_fit_scaling": (_i, [_p, _i, _p, _p]),
+    "mtgp_mlp_forward": (_i, [_p, _i, _p, _p, _p]),
+    "mtgp_mlp_gradients": (_i, [_p, _i, _p, _p, _p, _p, _p, _p, _p]),
+    "mtgp_mlp_train_step": (_i, [_p, _i, _p, _p, _p, _p, ctypes.c_float, _p, _p]),
 }
 
 _LIB = None

@@ -95,6 +95,7 @@ struct mtgp_batch_s {
     double glr = 0.0;
     double* gtrace = nullptr;
     int nsm = 1;
+    void* fdesc = nullptr;  // proposal descriptors (device), built on first use
 };
 
 namespace {
@@ -195,6 +196,195 @@ int build_plan(mtgp_batch_s* b) {
             b->cls[ph].push_back(c);
         }
     }
+    return MTGP_OK;
+}
+
+// ---- learned proposal: per-fit spectral features, training targets and the map back to parameters ----
+
+constexpr int kFeat = 8 * 32 + 2, kOut = 37, kDmaxProp = 12;
+
+struct FeatDesc {
+    const double* yhat;
+    long long yoff[MTGP_TMAX];  // element offset of caller task t's transformed observations
+    long long poff;             // offset of the fit's packed parameters
+    int T, m, d, cplx;
+};
+
+// bin(f) = floor(4 q / m), q = 8 floor(log2 f) + the three bits after f's leading one (zero-filled)
+__device__ __forceinline__ int freq_bin(unsigned long long f, int m) {
+    const int L = 63 - __clzll((long long)f);
+    const int frac3 = L >= 3 ? (int)((f >> (L - 3)) & 7ull) : (int)((f << (3 - L)) & 7ull);
+    return (4 * (8 * L + frac3)) / m;
+}
+
+// one block per fit: per task, log of the mean |yhat(f)|^2 over each of 32 log-spaced frequency bins
+// (f = 1..n-1; empty bins repeat the previous value), then log2 n and d.  A warp takes 32 consecutive
+// frequencies; their bins form contiguous runs, summed by a segmented warp scan in a fixed order, and
+// the run's last lane adds the run to the warp's own bin row, so the sums are deterministic.
+__global__ void __launch_bounds__(256) k_batch_features(const FeatDesc* __restrict__ fds, float* __restrict__ feat) {
+    __shared__ double s_sum[8][32], s_cnt[8][32];
+    const FeatDesc& fd = fds[blockIdx.x];
+    float* out = feat + (long long)blockIdx.x * kFeat;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long n = 1ll << fd.m;
+    for (int t = 0; t < MTGP_TMAX; ++t) {
+        if (t >= fd.T) {
+            if (threadIdx.x < 32) out[t * 32 + threadIdx.x] = 0.f;
+            continue;
+        }
+        s_sum[warp][lane] = 0.0;
+        s_cnt[warp][lane] = 0.0;
+        __syncthreads();
+        const double* y = fd.yhat + (fd.cplx ? 2 : 1) * fd.yoff[t];
+        for (long long base = (long long)warp * 32; base < n; base += 256) {
+            const long long f = base + lane;
+            int bin = 32;  // past the last frequency: no bin
+            double e = 0.0, c = 0.0;
+            if (f < n) {
+                bin = f == 0 ? 0 : freq_bin((unsigned long long)f, fd.m);
+                if (f > 0) {
+                    if (fd.cplx) {
+                        const double re = y[2 * f], im = y[2 * f + 1];
+                        e = re * re + im * im;
+                    } else {
+                        e = y[f] * y[f];
+                    }
+                    c = 1.0;
+                }
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double ue = __shfl_up_sync(0xffffffffu, e, o);
+                const double uc = __shfl_up_sync(0xffffffffu, c, o);
+                const int ub = __shfl_up_sync(0xffffffffu, bin, o);
+                if (lane >= o && ub == bin) {
+                    e += ue;
+                    c += uc;
+                }
+            }
+            const int nb = __shfl_down_sync(0xffffffffu, bin, 1);
+            if ((lane == 31 || nb != bin) && bin < 32) {
+                s_sum[warp][bin] += e;
+                s_cnt[warp][bin] += c;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float prev = 0.f;
+            for (int k = 0; k < 32; ++k) {
+                double sm = 0.0, cn = 0.0;
+                for (int w = 0; w < 8; ++w) {
+                    sm += s_sum[w][k];
+                    cn += s_cnt[w][k];
+                }
+                if (k == 0 || cn > 0.0) prev = (float)log(sm / (cn > 1.0 ? cn : 1.0) + 1e-30);
+                out[t * 32 + k] = prev;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[256] = (float)fd.m;
+        out[257] = (float)fd.d;
+    }
+}
+
+// one thread per fit: [log eta (12), canonical W (8 x 2), log v (8), log sigma2] and its mask; a fit
+// whose parameters give a non-finite entry gets target 0 and mask 0 throughout
+__global__ void k_batch_targets(const FeatDesc* __restrict__ fds, const double* __restrict__ nat, int nfits,
+                                float* __restrict__ tgt, float* __restrict__ mask) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfits) return;
+    const FeatDesc& fd = fds[f];
+    const double* p = nat + fd.poff;
+    float t[kOut], mk[kOut];
+    const int d = fd.d, T = fd.T;
+    for (int j = 0; j < kDmaxProp; ++j) {
+        t[j] = j < d ? (float)log(p[j]) : 0.f;
+        mk[j] = j < d ? 1.f : 0.f;
+    }
+    // W Q with Q the rotation taking row 0 to (r, 0), then column 1 negated if W[1][1] < 0
+    const double* W = p + d;
+    const double a = W[0], b = W[1], r = sqrt(a * a + b * b);
+    const double c = r > 0.0 ? a / r : 1.0, sn = r > 0.0 ? b / r : 0.0;
+    const double w11 = T > 1 ? -W[2] * sn + W[3] * c : 0.0;
+    const double sg = w11 < 0.0 ? -1.0 : 1.0;
+    for (int u = 0; u < MTGP_TMAX; ++u) {
+        float w0 = 0.f, w1 = 0.f, m = 0.f;
+        if (u < T) {
+            w0 = (float)(W[2 * u] * c + W[2 * u + 1] * sn);
+            w1 = u == 0 ? 0.f : (float)(sg * (-W[2 * u] * sn + W[2 * u + 1] * c));
+            m = 1.f;
+        }
+        t[kDmaxProp + 2 * u] = w0;
+        t[kDmaxProp + 2 * u + 1] = w1;
+        mk[kDmaxProp + 2 * u] = m;
+        mk[kDmaxProp + 2 * u + 1] = m;
+        t[kDmaxProp + 16 + u] = u < T ? (float)log(p[d + 2 * T + u]) : 0.f;
+        mk[kDmaxProp + 16 + u] = m;
+    }
+    t[kOut - 1] = (float)log(p[d + 3 * T]);
+    mk[kOut - 1] = 1.f;
+    bool ok = true;
+    for (int k = 0; k < kOut; ++k) ok = ok && isfinite(t[k]);
+    float* to = tgt + (long long)f * kOut;
+    float* mo = mask + (long long)f * kOut;
+    for (int k = 0; k < kOut; ++k) {
+        to[k] = ok ? t[k] : 0.f;
+        mo[k] = ok ? mk[k] : 0.f;
+    }
+}
+
+// one thread per fit: parameters from a prediction (exp of the log entries clamped to [-40, 20]);
+// Adam moments of the fit cleared
+__global__ void k_batch_propose(const FeatDesc* __restrict__ fds, const float* __restrict__ pred, int nfits,
+                                double* __restrict__ lg, double* __restrict__ nv, double* __restrict__ m1,
+                                double* __restrict__ m2) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfits) return;
+    const FeatDesc& fd = fds[f];
+    const float* q = pred + (long long)f * kOut;
+    const int d = fd.d, T = fd.T;
+    const long long o = fd.poff;
+    auto put_log = [&](long long k, float z) {
+        double x = (double)z;
+        x = x < -40.0 ? -40.0 : (x > 20.0 ? 20.0 : x);
+        lg[o + k] = x;
+        nv[o + k] = exp(x);
+    };
+    for (int j = 0; j < d; ++j) put_log(j, q[j]);
+    for (int k = 0; k < 2 * T; ++k) {
+        lg[o + d + k] = (double)q[kDmaxProp + k];
+        nv[o + d + k] = (double)q[kDmaxProp + k];
+    }
+    for (int u = 0; u < T; ++u) put_log(d + 2 * T + u, q[kDmaxProp + 16 + u]);
+    put_log(d + 3 * T, q[kOut - 1]);
+    for (long long k = 0; k < d + 3 * T + 1; ++k) {
+        m1[o + k] = 0.0;
+        m2[o + k] = 0.0;
+    }
+}
+
+int ensure_fdesc(mtgp_batch_s* b) {
+    if (b->fdesc) return MTGP_OK;
+    if (b->s != 2) return bfail(MTGP_ERR_UNSUPPORTED, "the proposal is defined for s = 2");
+    std::vector<FeatDesc> v(b->nfits);
+    for (int f = 0; f < b->nfits; ++f) {
+        const Handle& h = b->fits[f]->h;
+        if (h.d > kDmaxProp) return bfail(MTGP_ERR_UNSUPPORTED, "the proposal is defined for d <= 12");
+        FeatDesc& x = v[f];
+        std::memset(&x, 0, sizeof(x));
+        x.yhat = h.yhat;
+        for (int t = 0; t < h.T; ++t) x.yoff[t] = h.yoff[h.rank[t]];
+        x.poff = b->poff[f];
+        x.T = h.T;
+        x.m = h.m[0];
+        x.d = h.d;
+        x.cplx = h.cplx ? 1 : 0;
+    }
+    if (cudaMalloc(&b->fdesc, sizeof(FeatDesc) * v.size()) != cudaSuccess)
+        return bfail(MTGP_ERR_CUDA, "proposal table allocation failed");
+    cudaMemcpy(b->fdesc, v.data(), sizeof(FeatDesc) * v.size(), cudaMemcpyHostToDevice);
     return MTGP_OK;
 }
 
@@ -339,7 +529,7 @@ int mtgp_batch_destroy(mtgp_batch_t* b) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     for (auto* f : b->fits) mtgp_destroy(f);
     void* ptrs[] = {b->th_log, b->th_nat, b->g_nat, b->m1, b->m2, b->out, b->tau, b->partials, b->counters, b->pinfo,
-                    b->tstep, b->descs};
+                    b->tstep, b->descs, b->fdesc};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kSide; ++i) {
@@ -423,6 +613,35 @@ int mtgp_batch_adam(mtgp_batch_t* b, int steps, double lr, int use_graph, double
         b->gtrace = trace;
     }
     return cudaGraphLaunch(b->gexec, st) == cudaSuccess ? MTGP_OK : bfail(MTGP_ERR_CUDA, "graph launch failed");
+}
+
+int mtgp_batch_features(mtgp_batch_t* b, float* feat, cudaStream_t st) {
+    if (!b || !feat) return bfail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    for (auto* f : b->fits)
+        if (!f->h.y_set) return bfail(MTGP_ERR_STATE, "mtgp_batch_set_y must be called first");
+    int rc = ensure_fdesc(b);
+    if (rc) return rc;
+    k_batch_features<<<b->nfits, 256, 0, st>>>(static_cast<const FeatDesc*>(b->fdesc), feat);
+    return launch_status("mtgp_batch_features");
+}
+
+int mtgp_batch_targets(mtgp_batch_t* b, float* target, float* mask, cudaStream_t st) {
+    if (!b || !target || !mask) return bfail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    int rc = ensure_fdesc(b);
+    if (rc) return rc;
+    k_batch_targets<<<(b->nfits + 127) / 128, 128, 0, st>>>(static_cast<const FeatDesc*>(b->fdesc), b->th_nat, b->nfits,
+                                                            target, mask);
+    return launch_status("mtgp_batch_targets");
+}
+
+int mtgp_batch_set_theta_proposal(mtgp_batch_t* b, const float* pred, cudaStream_t st) {
+    if (!b || !pred) return bfail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    int rc = ensure_fdesc(b);
+    if (rc) return rc;
+    k_batch_propose<<<(b->nfits + 127) / 128, 128, 0, st>>>(static_cast<const FeatDesc*>(b->fdesc), pred, b->nfits,
+                                                            b->th_log, b->th_nat, b->m1, b->m2);
+    cudaMemsetAsync(b->tstep, 0, sizeof(int), st);
+    return launch_status("mtgp_batch_set_theta_proposal");
 }
 
 int mtgp_batch_autotune(mtgp_batch_t* b, int reps, int* chosen, cudaStream_t st) {

@@ -255,6 +255,25 @@ class Batch:
         check(lib().mtgp_batch_autotune(self._h, reps, chosen, _stream(stream)), "mtgp_batch_autotune")
         return list(chosen)
 
+    def features(self, stream=None) -> torch.Tensor:
+        """(nfits, 258) FP32 spectral summaries (mtgp_batch_features)."""
+        f = torch.empty((self.n, 258), dtype=torch.float32, device="cuda")
+        check(lib().mtgp_batch_features(self._h, _ptr(f), _stream(stream)), "mtgp_batch_features")
+        return f
+
+    def targets(self, stream=None):
+        """(target, mask), each (nfits, 37) FP32, from the current parameters (mtgp_batch_targets)."""
+        t = torch.empty((self.n, 37), dtype=torch.float32, device="cuda")
+        mk = torch.empty((self.n, 37), dtype=torch.float32, device="cuda")
+        check(lib().mtgp_batch_targets(self._h, _ptr(t), _ptr(mk), _stream(stream)), "mtgp_batch_targets")
+        return t, mk
+
+    def set_theta_proposal(self, pred, stream=None):
+        """Parameters from a (nfits, 37) prediction (mtgp_batch_set_theta_proposal)."""
+        self._pred = _dev(pred, torch.float32)
+        check(lib().mtgp_batch_set_theta_proposal(self._h, _ptr(self._pred), _stream(stream)),
+              "mtgp_batch_set_theta_proposal")
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             check(lib().mtgp_batch_destroy(self._h), "mtgp_batch_destroy")

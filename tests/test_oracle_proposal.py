@@ -83,3 +83,8 @@ def test_targets_round_trip_and_mask():
     e2, W2, v2, s22 = proposal.theta_from_prediction(t, d, T)
     assert np.allclose(e2, eta, rtol=1e-14) and np.allclose(v2, v, rtol=1e-14)
     assert np.allclose(W2, proposal.canonical_w(W), atol=1e-15) and s22 == pytest.approx(s2, rel=1e-14)
+    # a diverged fit (non-finite parameter) is left out entirely
+    t_bad, m_bad = proposal.targets(np.r_[eta[:-1], np.nan], W, v, s2)
+    assert np.all(t_bad == 0) and np.all(m_bad == 0)
+    t_bad, m_bad = proposal.targets(eta, W, np.r_[v[:-1], 0.0], s2)      # log 0
+    assert np.all(t_bad == 0) and np.all(m_bad == 0)
