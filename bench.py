@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu", action="store_true",
                     help="only warm-up + K steps of the workload, no extras (for ncu captures)")
-    ap.add_argument("--workload", default="nllgrad", choices=["nllgrad", "batch512", "proposal"],
+    ap.add_argument("--workload", default="nllgrad", choices=["nllgrad", "batch512", "proposal", "nested", "posterior"],
                     help="nllgrad: the headline NLL+gradient evaluation; batch512: 512 heterogeneous fits, "
                          "Adam steps in one CUDA graph vs a plain per-fit optimiser")
     ap.add_argument("--fits", type=int, default=512)
@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--eval-fits", type=int, default=256, help="proposal: held-out fits")
     ap.add_argument("--eval-steps", type=int, default=2000, help="proposal: Adam steps per held-out run")
     ap.add_argument("--eval-precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--queries", type=int, default=1 << 16, help="posterior: mean-only queries")
+    ap.add_argument("--queries-var", type=int, default=1 << 10, help="posterior: mean + variance queries")
     return ap.parse_args()
 
 
@@ -431,6 +433,108 @@ def run_batch(args):
     b.close()
 
 
+# ----------------------------------------------------------------------------- unequal sizes, posterior
+
+def _timed(fn, K, W, flush, stream):
+    """W warm-up calls, then K calls each bracketed by CUDA events; L2 flushed between calls."""
+    import torch
+    for i in range(max(W, 3)):
+        fn()
+        flush.fill_(float(i))
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for i in range(K):
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+        flush.fill_(float(i))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def run_nested(args):
+    """NLL + gradient of the nested unequal-size lattice fit (d = 16, T = 5, n = 2^20 .. 2^12, FP64)."""
+    import numpy as np
+    import torch
+
+    from paper_2603_16014_gb300 import inputs
+    from paper_2603_16014_gb300.mtgp import MTGP
+
+    torch.cuda.set_device(0)
+    p = inputs.lattice_nested()
+    model = MTGP.from_problem(p, "fp64")
+    X = model.points().cpu().numpy().view(np.uint32)
+    offs = np.concatenate([[0], np.cumsum(p.n)])
+    y = inputs.synth_y(p, [X[offs[t]:offs[t + 1]] for t in range(p.T)])
+    model.set_y(torch.from_numpy(y))
+    th = [torch.as_tensor(a, dtype=torch.float64).cuda().contiguous() for a in (p.eta, p.W, p.v, [p.sigma2])]
+    outs = model.nll_grad(*th)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ms = _timed(lambda: model.nll_grad(*th, outs=outs), args.steps, args.warmup, flush, stream)
+    model.profile(True)
+    for i in range(5):
+        model.nll_grad(*th, outs=outs)
+        flush.fill_(float(i))
+    prof = model.profile_read()
+    model.profile(False)
+    model.sync()
+    n = sorted(p.n, reverse=True)
+    entries = sum((p.T - t) * n[t] for t in range(p.T))          # pair-layout entries (t <= u)
+    line = {
+        "metric": "NLL+gradient evaluations per second (nested unequal sizes)", "value": 1e3 * len(ms) / sum(ms),
+        "unit": "evals/s", "n_gpus": 1, "steps": len(ms), "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms),
+        "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "lat_d16_T5_nested", "kind": "lattice", "d": p.d, "T": p.T, "n": n, "N": p.N,
+                   "precision": "FP64", "l2": "flushed (256 MB write) between steps"},
+        "pair_entries": entries,
+        "kernels_us_per_step": {k: v[0] / 5 * 1e3 for k, v in prof.items()},
+        "launches_per_step": {k: v[1] // 5 for k, v in prof.items()},
+        "nll": outs[0][0].item(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_posterior(args):
+    """Posterior mean (and variance) throughput on the d = 8 digital-net fit."""
+    import numpy as np
+    import torch
+
+    from paper_2603_16014_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    p, model, y = make_workload()
+    th = [torch.as_tensor(a, dtype=torch.float64).cuda().contiguous() for a in (p.eta, p.W, p.v, [p.sigma2])]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, nq, var in (("mean", args.queries, False), ("mean_var", args.queries_var, True)):
+        _, xq, task = inputs.query_points(nq, p.d, seed=3, tasks=p.T)
+        xq_d = torch.from_numpy(xq).cuda()
+        task_d = torch.from_numpy(task).cuda()
+        ms = _timed(lambda: model.posterior(*th, xq_d, task_d, variance=var), max(args.steps // 10, 2), 3, flush,
+                    stream)
+        model.sync()
+        t = sum(ms) / len(ms)
+        res[name] = {"queries": nq, "ms_per_call": t, "queries_per_s": nq / (t / 1e3)}
+    model.profile(True)
+    _, xq, task = inputs.query_points(args.queries_var, p.d, seed=3, tasks=p.T)
+    model.posterior(*th, torch.from_numpy(xq).cuda(), torch.from_numpy(task).cuda(), variance=True)
+    prof = model.profile_read()
+    model.profile(False)
+    N = p.N
+    line = {
+        "metric": "posterior queries per second (mean; mean + variance)", "value": res["mean"]["queries_per_s"],
+        "unit": "queries/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": "posterior_dnet_d8_T4_n2^16", "d": p.d, "T": p.T, "N": N,
+                   "precision": "FP32 transforms / FP64 kernel sums"},
+        "mean": res["mean"], "mean_var": res["mean_var"],
+        "kernel_pairs_per_s_mean": res["mean"]["queries_per_s"] * N,
+        "kernels_ms_mean_var_call": {k: v[0] for k, v in prof.items()},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- learned proposal
 
 def _synth_worker(job):
@@ -656,6 +760,12 @@ def main():
         return
     if args.workload == "proposal":
         run_proposal(args)
+        return
+    if args.workload == "nested":
+        run_nested(args)
+        return
+    if args.workload == "posterior":
+        run_posterior(args)
         return
     run_ours(args, rank, world, local_rank)
 
