@@ -96,17 +96,28 @@ __device__ void load_R_post(double* sR, const PostParams& p, const ThetaPtrs& th
     }
 }
 
-// one thread per query; design points and beta streamed through shared-memory tiles
+// Posterior mean, split over queries (blockIdx.x, one thread per query) and over slices of the design
+// points (blockIdx.y): slice k is chunk c of sorted task u, with k = first[u] + c.  Design points
+// and beta stream through shared-memory tiles; part[k][q] = R_{t_q u} sum_{i in slice} Q(x_q, x_ui) beta_u[i].
+struct MeanSlices {
+    long long chunk;             // points per slice (multiple of kTile)
+    int first[MTGP_TMAX + 1];    // first slice of each sorted task; first[T] = number of slices
+};
+
 __global__ void __launch_bounds__(kThreads)
-k_post_mean(const uint32_t* __restrict__ xqw, const int* __restrict__ task, int nq, const uint32_t* __restrict__ dw,
-            const double* __restrict__ beta, const double* __restrict__ tau_sorted, PostParams p, ThetaPtrs th,
-            double* __restrict__ mean) {
+k_post_mean_part(const uint32_t* __restrict__ xqw, const int* __restrict__ task, int nq, const uint32_t* __restrict__ dw,
+                 const double* __restrict__ beta, PostParams p, MeanSlices sl, ThetaPtrs th, double* __restrict__ part) {
     __shared__ double sR[MTGP_TMAX * MTGP_TMAX];
     __shared__ double s_eta[MTGP_MAX_DIM];
     __shared__ uint32_t s_x[kTile * MTGP_MAX_DIM];
     __shared__ double s_b[kTile];
     load_R_post(sR, p, th);
     if (threadIdx.x < p.d) s_eta[threadIdx.x] = th.eta[threadIdx.x];
+    const int k = blockIdx.y;
+    int u = 0;
+    while (u + 1 < p.T && sl.first[u + 1] <= k) ++u;
+    const long long i_begin = (long long)(k - sl.first[u]) * sl.chunk;
+    const long long i_end = (i_begin + sl.chunk) < p.n[u] ? (i_begin + sl.chunk) : p.n[u];
     const int d = p.d;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const bool act = q < nq;
@@ -117,22 +128,28 @@ k_post_mean(const uint32_t* __restrict__ xqw, const int* __restrict__ task, int 
         tq = p.rank[task[q]];
     }
     __syncthreads();
-    double m = 0.0;
-    for (int u = 0; u < p.T; ++u) {
-        double acc = 0.0;
-        for (long long i0 = 0; i0 < p.n[u]; i0 += kTile) {
-            int cnt = (int)((p.n[u] - i0) < kTile ? (p.n[u] - i0) : kTile);
-            __syncthreads();
-            for (int e = threadIdx.x; e < cnt * d; e += blockDim.x) s_x[e] = dw[(p.yoff[u] + i0) * d + e];
-            for (int e = threadIdx.x; e < cnt; e += blockDim.x) s_b[e] = beta[p.yoff[u] + i0 + e];
-            __syncthreads();
-            if (act) {
-                for (int i = 0; i < cnt; ++i) acc += qkernel<double>(p.kind, xq, s_x + i * d, s_eta, d) * s_b[i];
-            }
+    double acc = 0.0;
+    for (long long i0 = i_begin; i0 < i_end; i0 += kTile) {
+        const int cnt = (int)((i_end - i0) < kTile ? (i_end - i0) : kTile);
+        __syncthreads();
+        for (int e = threadIdx.x; e < cnt * d; e += blockDim.x) s_x[e] = dw[(p.yoff[u] + i0) * d + e];
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) s_b[e] = beta[p.yoff[u] + i0 + e];
+        __syncthreads();
+        if (act) {
+            for (int i = 0; i < cnt; ++i) acc += qkernel<double>(p.kind, xq, s_x + i * d, s_eta, d) * s_b[i];
         }
-        m += sR[tq * p.T + u] * acc;
     }
-    if (act) mean[q] = tau_sorted[tq] + m;
+    if (act) part[(long long)k * nq + q] = sR[tq * p.T + u] * acc;
+}
+
+// mean[q] = tau_{t_q} + sum_k part[k][q] (slices added in order)
+__global__ void k_post_mean_sum(const double* __restrict__ part, int nslices, const int* __restrict__ task, int nq,
+                                PostParams p, const double* __restrict__ tau_sorted, double* __restrict__ mean) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    double m = 0.0;
+    for (int k = 0; k < nslices; ++k) m += part[(long long)k * nq + q];
+    mean[q] = tau_sorted[p.rank[task[q]]] + m;
 }
 
 // rows of the variance batch: qrow[(b * T + u) * n + i] = R_{t_b u} Q(x_b, x_{u,i})  (equal sizes)
@@ -191,25 +208,20 @@ struct VarParams {
     long long coloff[MTGP_MAX_COLS];
 };
 
-// one CTA per query: sum_f kappa(f)^H Lambda(f)^-1 kappa(f) with kappa(f) = transformed rows / sqrt(n)
+// once per posterior call: Lambda(f) = L D L^H per frequency; stores 1/D_k (T x n doubles) then the
+// strict lower L_ik (T(T-1)/2 x n, complex for lattices), each entry index-major so threads coalesce
 template <int T, bool CPLX, typename S>
 __global__ void __launch_bounds__(kThreads)
-k_var_quad(const double* __restrict__ rows, const void* spec, const int* __restrict__ task, int q0,
-           const uint32_t* __restrict__ xqw, PostParams pp, VarParams p, ThetaPtrs th, double* __restrict__ var) {
+k_var_factor(const void* spec, PostParams pp, VarParams p, ThetaPtrs th, double* __restrict__ fac) {
     using V = Vt<CPLX>;
     __shared__ double sR[T * T];
     __shared__ double s_sig;
-    __shared__ double s_eta[MTGP_MAX_DIM];
-    __shared__ double s_red[kThreads / 32];
     load_R_post(sR, pp, th);
     if (threadIdx.x == 0) s_sig = th.sigma2[0];
-    if (threadIdx.x < pp.d) s_eta[threadIdx.x] = th.eta[threadIdx.x];
     __syncthreads();
-    const int b = blockIdx.x;
     const long long n = p.n;
-    const double inv_sqrt_n = 1.0 / sqrt((double)n);
-    double acc = 0.0;
-    for (long long f = threadIdx.x; f < n; f += blockDim.x) {
+    V* facL = reinterpret_cast<V*>(fac + (long long)T * n);
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < n; f += (long long)gridDim.x * blockDim.x) {
         V mu[T][T];
 #pragma unroll
         for (int t = 0; t < T; ++t)
@@ -232,27 +244,52 @@ k_var_quad(const double* __restrict__ rows, const void* spec, const int* __restr
 #pragma unroll
             for (int j = 0; j < k; ++j) dk -= cabs2(L[k][j]) * D[j];
             D[k] = dk;
+            fac[(long long)k * n + f] = 1.0 / dk;
 #pragma unroll
             for (int i = k + 1; i < T; ++i) {
                 V a = lam[i][k];
 #pragma unroll
                 for (int j = 0; j < k; ++j) a = vsub(a, vscale(vmul(L[i][j], cconj(L[k][j])), D[j]));
                 L[i][k] = vscale(a, 1.0 / dk);
+                facL[(long long)(i * (i - 1) / 2 + k) * n + f] = L[i][k];
             }
         }
+    }
+}
+
+// one CTA per query: sum_f kappa(f)^H Lambda(f)^-1 kappa(f) with kappa(f) = transformed rows / sqrt(n),
+// through the stored factors: w = L^-1 kappa, sum_k |w_k|^2 / D_k
+template <int T, bool CPLX, typename S>
+__global__ void __launch_bounds__(kThreads)
+k_var_quad(const double* __restrict__ rows, const double* __restrict__ fac, const int* __restrict__ task, int q0,
+           const uint32_t* __restrict__ xqw, PostParams pp, VarParams p, ThetaPtrs th, double* __restrict__ var) {
+    using V = Vt<CPLX>;
+    __shared__ double sR[T * T];
+    __shared__ double s_eta[MTGP_MAX_DIM];
+    __shared__ double s_red[kThreads / 32];
+    load_R_post(sR, pp, th);
+    if (threadIdx.x < pp.d) s_eta[threadIdx.x] = th.eta[threadIdx.x];
+    __syncthreads();
+    const int b = blockIdx.x;
+    const long long n = p.n;
+    const double inv_n = 1.0 / (double)n;
+    const V* facL = reinterpret_cast<const V*>(fac + (long long)T * n);
+    double acc = 0.0;
+    for (long long f = threadIdx.x; f < n; f += blockDim.x) {
         V w[T];
 #pragma unroll
         for (int k = 0; k < T; ++k) {
             long long e = ((long long)b * T + k) * n + f;
             V r;
-            if constexpr (CPLX) r = mk(rows[2 * e] * inv_sqrt_n, rows[2 * e + 1] * inv_sqrt_n);
-            else r = rows[e] * inv_sqrt_n;
+            if constexpr (CPLX) r = mk(rows[2 * e], rows[2 * e + 1]);
+            else r = rows[e];
 #pragma unroll
-            for (int j = 0; j < k; ++j) r = vsub(r, vmul(L[k][j], w[j]));
+            for (int j = 0; j < k; ++j) r = vsub(r, vmul(facL[(long long)(k * (k - 1) / 2 + j) * n + f], w[j]));
             w[k] = r;
-            acc += cabs2(r) / D[k];
+            acc += cabs2(r) * fac[(long long)k * n + f];
         }
     }
+    acc *= inv_n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (lane == 0) s_red[warp] = acc;
@@ -269,23 +306,30 @@ k_var_quad(const double* __restrict__ rows, const void* spec, const int* __restr
 }
 
 template <int T, bool CPLX, typename S>
-void run_var_quad(int B, const double* rows, const void* spec, const int* task, int q0, const uint32_t* xqw,
-                  PostParams pp, VarParams vp, ThetaPtrs th, double* var, cudaStream_t st) {
-    k_var_quad<T, CPLX, S><<<B, kThreads, 0, st>>>(rows, spec, task, q0, xqw, pp, vp, th, var);
+void run_var(bool factor, int B, const double* rows, const void* spec, double* fac, const int* task, int q0,
+             const uint32_t* xqw, PostParams pp, VarParams vp, ThetaPtrs th, double* var, cudaStream_t st) {
+    if (factor) {
+        long long blocks = (vp.n + kThreads - 1) / kThreads;
+        k_var_factor<T, CPLX, S><<<(int)(blocks < 4096 ? blocks : 4096), kThreads, 0, st>>>(spec, pp, vp, th, fac);
+    } else {
+        k_var_quad<T, CPLX, S><<<B, kThreads, 0, st>>>(rows, fac, task, q0, xqw, pp, vp, th, var);
+    }
 }
 
+// factor = true: per-frequency factors into fac; false: the quadratic forms of B queries
 template <bool CPLX, typename S>
-void dispatch_var(int T, int B, const double* rows, const void* spec, const int* task, int q0, const uint32_t* xqw,
-                  PostParams pp, VarParams vp, ThetaPtrs th, double* var, cudaStream_t st) {
+void dispatch_var(bool factor, int T, int B, const double* rows, const void* spec, double* fac, const int* task,
+                  int q0, const uint32_t* xqw, PostParams pp, VarParams vp, ThetaPtrs th, double* var,
+                  cudaStream_t st) {
     switch (T) {
-        case 1: run_var_quad<1, CPLX, S>(B, rows, spec, task, q0, xqw, pp, vp, th, var, st); break;
-        case 2: run_var_quad<2, CPLX, S>(B, rows, spec, task, q0, xqw, pp, vp, th, var, st); break;
-        case 3: run_var_quad<3, CPLX, S>(B, rows, spec, task, q0, xqw, pp, vp, th, var, st); break;
-        case 4: run_var_quad<4, CPLX, S>(B, rows, spec, task, q0, xqw, pp, vp, th, var, st); break;
-        case 5: run_var_quad<5, CPLX, S>(B, rows, spec, task, q0, xqw, pp, vp, th, var, st); break;
-        case 6: run_var_quad<6, CPLX, S>(B, rows, spec, task, q0, xqw, pp, vp, th, var, st); break;
-        case 7: run_var_quad<7, CPLX, S>(B, rows, spec, task, q0, xqw, pp, vp, th, var, st); break;
-        default: run_var_quad<8, CPLX, S>(B, rows, spec, task, q0, xqw, pp, vp, th, var, st); break;
+        case 1: run_var<1, CPLX, S>(factor, B, rows, spec, fac, task, q0, xqw, pp, vp, th, var, st); break;
+        case 2: run_var<2, CPLX, S>(factor, B, rows, spec, fac, task, q0, xqw, pp, vp, th, var, st); break;
+        case 3: run_var<3, CPLX, S>(factor, B, rows, spec, fac, task, q0, xqw, pp, vp, th, var, st); break;
+        case 4: run_var<4, CPLX, S>(factor, B, rows, spec, fac, task, q0, xqw, pp, vp, th, var, st); break;
+        case 5: run_var<5, CPLX, S>(factor, B, rows, spec, fac, task, q0, xqw, pp, vp, th, var, st); break;
+        case 6: run_var<6, CPLX, S>(factor, B, rows, spec, fac, task, q0, xqw, pp, vp, th, var, st); break;
+        case 7: run_var<7, CPLX, S>(factor, B, rows, spec, fac, task, q0, xqw, pp, vp, th, var, st); break;
+        default: run_var<8, CPLX, S>(factor, B, rows, spec, fac, task, q0, xqw, pp, vp, th, var, st); break;
     }
 }
 
@@ -315,6 +359,10 @@ struct PostScratch {
     long long rows_cap = 0;
     long long* offs = nullptr;   // row offsets of the variance batch (multiples of n)
     int offs_cap = 0;
+    double* fac = nullptr;       // per-frequency L D L^H factors of Lambda (variance)
+    long long fac_cap = 0;
+    double* part = nullptr;      // mean partial sums, slices x nq
+    long long part_cap = 0;
 };
 std::map<const Handle*, PostScratch> g_post;
 std::mutex g_post_mu;
@@ -330,6 +378,8 @@ void posterior_release(const Handle* h) {
     cudaFree(it->second.xq);
     cudaFree(it->second.rows);
     cudaFree(it->second.offs);
+    cudaFree(it->second.fac);
+    cudaFree(it->second.part);
     g_post.erase(it);
 }
 
@@ -379,8 +429,37 @@ int posterior_run(Handle* h, ThetaPtrs th, int nq, const double* xq, const int* 
         pp.rank[t] = t < h->T ? h->rank[t] : 0;
     }
     // tau (sorted) lives in h->tau (filled by the solver for unequal sizes, by mtgp_set_y for equal)
-    k_post_mean<<<(nq + kThreads - 1) / kThreads, kThreads, 0, st>>>(ps->xq, task, nq, ps->design, ps->beta, h->tau, pp,
-                                                                      th, mean);
+    // slices of the design points so that query blocks x slices fill the GPU several times over,
+    // with the partial sums capped at 32 M doubles
+    {
+        int dev = 0, nsm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const long long qblocks = (nq + kThreads - 1) / kThreads;
+        long long want = (16LL * nsm + qblocks - 1) / qblocks;
+        const long long cap = (32LL << 20) / nq;
+        if (want > cap) want = cap;
+        if (want < 1) want = 1;
+        long long chunk = (N + want - 1) / want;
+        chunk = (chunk + kTile - 1) / kTile * kTile;
+        MeanSlices sl;
+        sl.chunk = chunk;
+        int ns = 0;
+        for (int t = 0; t < MTGP_TMAX + 1; ++t) {
+            sl.first[t] = ns;
+            if (t < h->T) ns += (int)((h->n[t] + chunk - 1) / chunk);
+        }
+        if ((long long)ns * nq > ps->part_cap) {
+            cudaFree(ps->part);
+            ps->part_cap = (long long)ns * nq;
+            if (cudaMalloc(&ps->part, (size_t)ps->part_cap * sizeof(double)) != cudaSuccess) return MTGP_ERR_CUDA;
+        }
+        mtgp_prof_begin(h, "post_mean", st);
+        dim3 grid((unsigned)qblocks, (unsigned)ns);
+        k_post_mean_part<<<grid, kThreads, 0, st>>>(ps->xq, task, nq, ps->design, ps->beta, pp, sl, th, ps->part);
+        k_post_mean_sum<<<(unsigned)qblocks, kThreads, 0, st>>>(ps->part, ns, task, nq, pp, h->tau, mean);
+        mtgp_prof_end(h, st);
+    }
     if (!var) return MTGP_OK;
     if (!h->equal) return MTGP_ERR_UNSUPPORTED;
     const long long n = h->n[0];
@@ -414,19 +493,37 @@ int posterior_run(Handle* h, ThetaPtrs th, int nq, const double* xq, const int* 
     for (int t = 0; t < MTGP_TMAX; ++t)
         for (int u = 0; u < MTGP_TMAX; ++u) vp.colidx[t][u] = (t < h->T && u < h->T && t <= u) ? h->col_of[t][u] : 0;
     for (int c = 0; c < MTGP_MAX_COLS; ++c) vp.coloff[c] = c < h->ncols ? h->cols[c].off : 0;
+    const long long fac_need = (long long)h->T * n + (long long)h->T * (h->T - 1) / 2 * n * es;
+    if (fac_need > ps->fac_cap) {
+        cudaFree(ps->fac);
+        ps->fac_cap = fac_need;
+        if (cudaMalloc(&ps->fac, (size_t)fac_need * sizeof(double)) != cudaSuccess) return MTGP_ERR_CUDA;
+    }
+    auto var_step = [&](bool factor, int Bb, int q0) {
+        if (h->fp32) {
+            if (h->cplx) dispatch_var<true, float>(factor, h->T, Bb, ps->rows, h->spec, ps->fac, task, q0, ps->xq, pp, vp, th, var, st);
+            else dispatch_var<false, float>(factor, h->T, Bb, ps->rows, h->spec, ps->fac, task, q0, ps->xq, pp, vp, th, var, st);
+        } else {
+            if (h->cplx) dispatch_var<true, double>(factor, h->T, Bb, ps->rows, h->spec, ps->fac, task, q0, ps->xq, pp, vp, th, var, st);
+            else dispatch_var<false, double>(factor, h->T, Bb, ps->rows, h->spec, ps->fac, task, q0, ps->xq, pp, vp, th, var, st);
+        }
+    };
+    mtgp_prof_begin(h, "var_factor", st);
+    var_step(true, 0, 0);
+    mtgp_prof_end(h, st);
     for (int q0 = 0; q0 < nq; q0 += B) {
         int Bb = (nq - q0) < B ? (nq - q0) : B;
         long long work = (long long)Bb * h->T * n;
+        mtgp_prof_begin(h, "var_rows", st);
         if (h->cplx) k_var_rows<true><<<grid_for(work), 256, 0, st>>>(ps->xq, task, q0, Bb, ps->design, pp, th, ps->rows);
         else k_var_rows<false><<<grid_for(work), 256, 0, st>>>(ps->xq, task, q0, Bb, ps->design, pp, th, ps->rows);
+        mtgp_prof_end(h, st);
+        mtgp_prof_begin(h, "var_xform", st);
         launch_transform(h, ps->rows, false, h->cplx, h->m[0], offs_dev, Bb * h->T, false, st);
-        if (h->fp32) {
-            if (h->cplx) dispatch_var<true, float>(h->T, Bb, ps->rows, h->spec, task, q0, ps->xq, pp, vp, th, var, st);
-            else dispatch_var<false, float>(h->T, Bb, ps->rows, h->spec, task, q0, ps->xq, pp, vp, th, var, st);
-        } else {
-            if (h->cplx) dispatch_var<true, double>(h->T, Bb, ps->rows, h->spec, task, q0, ps->xq, pp, vp, th, var, st);
-            else dispatch_var<false, double>(h->T, Bb, ps->rows, h->spec, task, q0, ps->xq, pp, vp, th, var, st);
-        }
+        mtgp_prof_end(h, st);
+        mtgp_prof_begin(h, "var_quad", st);
+        var_step(false, Bb, q0);
+        mtgp_prof_end(h, st);
     }
     return MTGP_OK;
 }

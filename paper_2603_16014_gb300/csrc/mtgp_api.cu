@@ -138,9 +138,11 @@ int run_nll(Handle* h, ThetaPtrs th, bool grad, double* out, double* tau, double
     mtgp_prof_begin(h, "colgen", st);
     launch_colgen(h, th.eta, h->spec, st);
     mtgp_prof_end(h, st);
+    mtgp_prof_begin(h, "xform_dit", st);
     for (int g = 0; g < h->ngroups; ++g)
         launch_transform(h, h->spec, h->fp32, h->cplx, h->group_m[g], h->offs_dev + h->group_first[g],
                          h->group_count[g], false, st);
+    mtgp_prof_end(h, st);
     int nsolve;
     if (h->equal) {
         mtgp_prof_begin(h, "solve_equal", st);
@@ -157,9 +159,11 @@ int run_nll(Handle* h, ThetaPtrs th, bool grad, double* out, double* tau, double
     double* eta_part = h->partials + (long long)nsolve * NQ;
     int neta = 0;
     if (grad) {
+        mtgp_prof_begin(h, "xform_dif", st);
         for (int g = 0; g < h->ngroups; ++g)
             launch_transform(h, h->wgt, h->fp32, h->cplx, h->group_m[g], h->offs_dev + h->group_first[g],
                              h->group_count[g], true, st);
+        mtgp_prof_end(h, st);
         neta = eta_grad_blocks(h);
         mtgp_prof_begin(h, "eta_grad", st);
         launch_eta_grad(h, th.eta, h->wgt, eta_part, neta, st);

@@ -89,6 +89,37 @@ __device__ __forceinline__ S dsi2_kernel(uint32_t X) {
     return (S)1.5 - (S)b * x - (S)2.5 * pow2_neg<S>(b);
 }
 
+// FP64 forms assembled on the integer pipe.  |v| 2^-s as a double from integer fields: exact for
+// v < 2^53, truncated to 53 significant bits above; the callers' scalings never underflow.
+__device__ __forceinline__ double u64_times_pow2(unsigned long long v, int s, bool negative) {
+    if (v == 0ull) return 0.0;
+    const int lz = __clzll((long long)v);
+    const unsigned long long m = v << lz;
+    unsigned long long bits = ((unsigned long long)(1086 - lz - s) << 52) + ((m >> 11) & 0xFFFFFFFFFFFFFull);
+    if (negative) bits |= 0x8000000000000000ull;
+    return __longlong_as_double((long long)bits);
+}
+
+// SI kernel: u (1 - u) 2^64 = Y (2^32 - Y) is an exact 64-bit integer, leaving two FP64 operations.
+template <>
+__device__ __forceinline__ double si2_kernel<double>(uint32_t X) {
+    const uint32_t Y = (X > 0x80000000u) ? (0u - X) : X;
+    const double w = u64_times_pow2((unsigned long long)Y * (0x100000000ull - Y), 64, false);
+    return fma(-MTGP_2PI4_3, w * w, MTGP_PI4_45);
+}
+
+// DSI kernel: 2^33 K(X / 2^32) = 3 2^32 - 2 b X - 5 2^(32-b) is an exact integer (|.| < 2^39), so K is
+// exact and costs no FP64 operation.
+template <>
+__device__ __forceinline__ double dsi2_kernel<double>(uint32_t X) {
+    long long I = 3LL << 32;
+    if (X != 0u) {
+        const int b = __clz(X) + 1;
+        I -= 2LL * b * (long long)X + (5LL << (32 - b));
+    }
+    return u64_times_pow2((unsigned long long)(I < 0 ? -I : I), 33, I < 0);
+}
+
 template <typename S>
 __device__ __forceinline__ S kernel1d(int kind, uint32_t X) {
     return kind == MTGP_LATTICE ? si2_kernel<S>(X) : dsi2_kernel<S>(X);
