@@ -41,9 +41,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the torch-composition comparison arm")
     ap.add_argument("--ncu", action="store_true",
                     help="only warm-up + K steps of the workload, no extras (for ncu captures)")
-    ap.add_argument("--workload", default="nllgrad", choices=["nllgrad", "batch512", "proposal", "nested", "posterior"],
+    ap.add_argument("--workload", default="nllgrad", choices=["nllgrad", "batch512", "proposal", "nested", "posterior", "sweep"],
                     help="nllgrad: the headline NLL+gradient evaluation; batch512: 512 heterogeneous fits, "
                          "Adam steps in one CUDA graph vs a plain per-fit optimiser")
     ap.add_argument("--fits", type=int, default=512)
@@ -55,6 +56,7 @@ def parse():
     ap.add_argument("--eval-precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--queries", type=int, default=1 << 16, help="posterior: mean-only queries")
     ap.add_argument("--queries-var", type=int, default=1 << 10, help="posterior: mean + variance queries")
+    ap.add_argument("--sweep-m", type=int, nargs="+", default=[16, 18, 20, 22, 24], help="sweep: log2 n values")
     return ap.parse_args()
 
 
@@ -311,6 +313,12 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "nll": outs[0][0].item(),
     }
+    if world == 1 and not args.no_plain:
+        pv, pnll = plain_arm(p, model, y, 10, flush, stream)
+        line["vs_plain"] = {"plain_evals_per_s": pv, "speedup": value / pv, "plain_nll": pnll,
+                            "nll_rel_diff": abs(pnll - line["nll"]) / abs(line["nll"]),
+                            "plain": "torch composition: elementwise kernel columns, reshape FWHT (FP32), "
+                                     "batched FP64 cholesky_ex, autograd gradient"}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -433,6 +441,83 @@ def run_batch(args):
     b.close()
 
 
+# ----------------------------------------------------------------------------- plain library composition
+
+def plain_torch_nll_grad(p, Xw, yhat):
+    """Build the NLL + gradient of the digital-net workload from torch library calls (the comparison
+    arm): kernel columns by elementwise tensor ops, the Walsh-Hadamard transform by reshapes,
+    per-frequency batched FP64 Cholesky (cholesky_ex), gradient by autograd.  Xw: (T, n, d) int64
+    point words; yhat: (T, n) FP64 transformed observations.  Returns a closure computing
+    (NLL, gradients)."""
+    import torch
+    T, n, d = Xw.shape
+    dev = Xw.device
+    pairs = [(t, u) for t in range(T) for u in range(t, T)]
+    ti = torch.tensor([a for a, _ in pairs], device=dev)
+    ui = torch.tensor([b for _, b in pairs], device=dev)
+    Xcols = Xw[ti] ^ Xw[ui, :1, :]                       # (P, n, d): x_{t,i} xor x_{u,0}
+    x = Xcols.double() * 2.0 ** -32
+    with torch.no_grad():
+        b = torch.where(Xcols == 0, torch.zeros_like(x), -torch.floor(torch.log2(torch.where(Xcols == 0, 1.0, x))))
+        Kd = torch.where(Xcols == 0, torch.full_like(x, 1.5), 1.5 - b * x - 2.5 * torch.exp2(-b)).float()
+    rh = yhat.t().contiguous().unsqueeze(-1)             # (n, T, 1)
+    rh[0] = 0.0
+    N = T * n
+    eye = torch.eye(T, dtype=torch.float64, device=dev)
+    m = n.bit_length() - 1
+
+    def fwht(a):
+        P = a.shape[0]
+        h = 1
+        while h < n:
+            a = a.view(P, n // (2 * h), 2, h)
+            a = torch.stack((a[:, :, 0] + a[:, :, 1], a[:, :, 0] - a[:, :, 1]), dim=2)
+            h *= 2
+        return a.reshape(P, n)
+
+    def step(eta, W, v, s2):
+        for q in (eta, W, v, s2):
+            q.grad = None
+        cols = torch.prod(1.0 + eta.float() * Kd, dim=-1)          # (P, n) FP32
+        mu = fwht(cols).double()                                    # unnormalised spectra
+        R = W @ W.t() + torch.diag(v)
+        Mi = torch.zeros(T, T, n, dtype=torch.float64, device=dev)
+        Mi = Mi.index_put((ti, ui), mu).index_put((ui, ti), mu)
+        Lam = R.unsqueeze(0) * Mi.permute(2, 0, 1) + s2 * eye
+        L, info = torch.linalg.cholesky_ex(Lam)
+        logdet = 2.0 * torch.log(torch.diagonal(L, dim1=-2, dim2=-1)).sum()
+        z = torch.linalg.solve_triangular(L, rh, upper=False)
+        quad = (z * z).sum()
+        nll = 0.5 * (logdet + quad + N * math.log(2 * math.pi))
+        nll.backward()
+        return nll, eta.grad, W.grad, v.grad, s2.grad
+
+    return step
+
+
+def plain_arm(p, model, y, steps, flush, stream):
+    """Time the plain composition on the same fit; returns (evals/s, its NLL)."""
+    import numpy as np
+    import torch
+    X = model.points().view(torch.int32).long() & 0xFFFFFFFF      # (N, d) words
+    T, n = p.T, p.n[0]
+    Xw = X.view(T, n, p.d)
+    # yhat: the transform of y with 1/sqrt(n), computed once by the same reshape FWHT in FP64
+    yt = torch.from_numpy(np.asarray(y)).cuda().view(T, n)
+    h = 1
+    a = yt.clone()
+    while h < n:
+        a = a.view(T, n // (2 * h), 2, h)
+        a = torch.stack((a[:, :, 0] + a[:, :, 1], a[:, :, 0] - a[:, :, 1]), dim=2)
+        h *= 2
+    yhat = a.reshape(T, n) / math.sqrt(n)
+    step = plain_torch_nll_grad(p, Xw, yhat)
+    th = [torch.as_tensor(q, dtype=torch.float64).cuda().requires_grad_() for q in (p.eta, p.W, p.v, p.sigma2)]
+    ms = _timed(lambda: step(*th), steps, 3, flush, stream)
+    nll = step(*th)[0].item()
+    return 1e3 * len(ms) / sum(ms), nll
+
+
 # ----------------------------------------------------------------------------- unequal sizes, posterior
 
 def _timed(fn, K, W, flush, stream):
@@ -532,6 +617,54 @@ def run_posterior(args):
         "kernel_pairs_per_s_mean": res["mean"]["queries_per_s"] * N,
         "kernels_ms_mean_var_call": {k: v[0] for k, v in prof.items()},
     }
+    print(json.dumps(line), flush=True)
+
+
+def run_sweep(args):
+    """The d = 8, T = 4 digital-net shape at growing n: evals/s and the step's algorithmic bytes
+    against HBM bandwidth once the working set leaves L2."""
+    import numpy as np
+    import torch
+
+    from paper_2603_16014_gb300 import inputs
+    from paper_2603_16014_gb300.mtgp import MTGP
+
+    torch.cuda.set_device(0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    peaks = measured_peaks()
+    rows = []
+    for m in args.sweep_m:
+        p = inputs.dnet_equal(m=m)
+        model = MTGP.from_problem(p, "fp32")
+        y = np.random.default_rng([m, 77]).standard_normal(p.N)   # timing only: values do not matter
+        model.set_y(torch.from_numpy(y))
+        th = [torch.as_tensor(a, dtype=torch.float64).cuda().contiguous() for a in (p.eta, p.W, p.v, [p.sigma2])]
+        outs = model.nll_grad(*th)
+        ms = _timed(lambda: model.nll_grad(*th, outs=outs), args.steps, args.warmup, flush, stream)
+        model.profile(True)
+        for i in range(3):
+            model.nll_grad(*th, outs=outs)
+            flush.fill_(float(i))
+        prof = model.profile_read()
+        model.profile(False)
+        model.sync()
+        n, T = p.n[0], p.T
+        C = 1 + T * (T - 1) // 2
+        step_bytes = n * (8 * T + 2 * C * 4 + 2 * C * 4)
+        t = sum(ms) / len(ms)
+        rows.append({"m": m, "n": n, "ms_per_eval": t, "evals_per_s": 1e3 / t, "algorithmic_bytes": step_bytes,
+                     "achieved_gbs": step_bytes / (t / 1e3) / 1e9,
+                     "hbm_frac": step_bytes / (t / 1e3) / 1e9 / peaks["hbm_gbs"],
+                     "kernels_us": {k: v[0] / 3 * 1e3 for k, v in prof.items()}})
+        model.close()
+        del outs
+        torch.cuda.empty_cache()
+    line = {"metric": "NLL+gradient evaluations per second vs n (d=8 digital net, T=4, FP32 transforms)",
+            "value": rows[-1]["evals_per_s"], "unit": "evals/s", "n_gpus": 1, "higher_is_better": True,
+            "data": "synthetic (white-noise responses)", "hbm_peak_gbs": peaks["hbm_gbs"],
+            "config": {"workload": "dnet_d8_T4_sweep", "l2": "flushed (256 MB write) between steps"},
+            "sweep": rows}
     print(json.dumps(line), flush=True)
 
 
@@ -766,6 +899,9 @@ def main():
         return
     if args.workload == "posterior":
         run_posterior(args)
+        return
+    if args.workload == "sweep":
+        run_sweep(args)
         return
     run_ours(args, rank, world, local_rank)
 

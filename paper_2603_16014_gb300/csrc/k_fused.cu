@@ -93,18 +93,6 @@ __device__ void load_R_f(double* sR, const FusedParams& p, const ThetaPtrs& th) 
 }
 
 // deterministic block reduction of one value (all threads call; result valid in thread 0)
-__device__ __forceinline__ double block_sum(double v, double* scratch) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) scratch[warp] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += scratch[w];
-    return r;
-}
-
 template <typename S>
 __device__ __forceinline__ S block_sum_s(S v, S* scratch) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -116,13 +104,6 @@ __device__ __forceinline__ S block_sum_s(S v, S* scratch) {
     if (threadIdx.x == 0)
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += scratch[w];
     return r;
-}
-
-// sum of column q of a (nrows x ncols) partial array, fixed order, all threads call
-__device__ double sum_partials(const double* part, int nrows, int ncols, int q, double* scratch) {
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nrows; b += blockDim.x) v += part[(long long)b * ncols + q];
-    return block_sum(v, scratch);
 }
 
 // totals of the ncols columns of an (nrows x ncols) partial array into out[q]: warp w sums columns
@@ -227,6 +208,18 @@ __device__ __forceinline__ void chunk_point(int kind, int d, uint32_t lo, const 
     }
 }
 
+// chunk points as a table: s_z[j * 2^a + lo] = coordinate j of point base + lo (all threads call)
+constexpr int kZTab = 2048;
+__device__ __forceinline__ void chunk_table(int kind, int d, int a, const uint32_t* s_zhi, const uint32_t* s_gen,
+                                            int gen_cols, uint32_t* s_z) {
+    const int HA = 1 << a;
+    for (int e = threadIdx.x; e < HA * d; e += blockDim.x) {
+        const int j = e >> a, lo = e & (HA - 1);
+        const uint32_t zl = point_word(kind, (uint32_t)lo, j, s_gen, gen_cols);
+        s_z[e] = (kind == MTGP_LATTICE) ? s_zhi[j] + zl : (s_zhi[j] ^ zl);
+    }
+}
+
 __device__ __forceinline__ void load_design_smem(const FusedParams& p, const uint32_t* gen, const uint32_t* shift,
                                                  const double* eta, long long base, uint32_t* s_gen, uint32_t* s_sh,
                                                  uint32_t* s_zhi) {
@@ -256,24 +249,45 @@ __device__ __forceinline__ void fused_a_body(const FitDesc& f, int blk) {
     const int HA = 1 << p.a;
     const long long base = (long long)blk << p.a;
     const int d = p.d;
+    __shared__ uint32_t s_z[kZTab];
     if (threadIdx.x < d) s_eta[threadIdx.x] = (S)eta[threadIdx.x];
     load_design_smem(p, gen, shift, eta, base, s_gen, s_sh, s_zhi);
     __syncthreads();
-    for (int lo = threadIdx.x; lo < HA; lo += blockDim.x) {
-        uint32_t z[DMAX];
-        chunk_point<DMAX>(p.kind, d, (uint32_t)lo, s_zhi, s_gen, p.gen_cols, z);
-        for (int c = 0; c < p.C; ++c) {
+    if (HA * d <= kZTab) {
+        // chunk points once per (coordinate, element), then one work item per (column, element)
+        chunk_table(p.kind, d, p.a, s_zhi, s_gen, p.gen_cols, s_z);
+        __syncthreads();
+        for (int e = threadIdx.x; e < HA * p.C; e += blockDim.x) {
+            const int c = e >> p.a, lo = e & (HA - 1);
             const int t = p.colt[c], u = p.colu[c];
             S q = (S)1;
 #pragma unroll
             for (int j = 0; j < DMAX; ++j) {
                 if (j < d) {
-                    uint32_t X = pair_word(p.kind, z[j], s_sh[t * d + j], s_sh[u * d + j]);
+                    uint32_t X = pair_word(p.kind, s_z[(j << p.a) + lo], s_sh[t * d + j], s_sh[u * d + j]);
                     q *= (S)1 + s_eta[j] * kernel1d<S>(p.kind, X);
                 }
             }
-            if constexpr (CPLX) buf[c * HA + lo] = mk(q, (S)0);
-            else buf[c * HA + lo] = q;
+            if constexpr (CPLX) buf[e] = mk(q, (S)0);
+            else buf[e] = q;
+        }
+    } else {
+        for (int lo = threadIdx.x; lo < HA; lo += blockDim.x) {
+            uint32_t z[DMAX];
+            chunk_point<DMAX>(p.kind, d, (uint32_t)lo, s_zhi, s_gen, p.gen_cols, z);
+            for (int c = 0; c < p.C; ++c) {
+                const int t = p.colt[c], u = p.colu[c];
+                S q = (S)1;
+#pragma unroll
+                for (int j = 0; j < DMAX; ++j) {
+                    if (j < d) {
+                        uint32_t X = pair_word(p.kind, z[j], s_sh[t * d + j], s_sh[u * d + j]);
+                        q *= (S)1 + s_eta[j] * kernel1d<S>(p.kind, X);
+                    }
+                }
+                if constexpr (CPLX) buf[c * HA + lo] = mk(q, (S)0);
+                else buf[c * HA + lo] = q;
+            }
         }
     }
     __syncthreads();
@@ -310,7 +324,6 @@ __device__ __forceinline__ void fused_b_body(const FitDesc& f, int blk) {
     E* buf = reinterpret_cast<E*>(smem_raw);
     __shared__ double sR[T * T];
     __shared__ double s_sig;
-    __shared__ double s_scr[32];
     __shared__ double s_tot[NQ];
     load_R_f(sR, p, th);
     if (threadIdx.x == 0) s_sig = th.sigma2[0];
@@ -451,9 +464,9 @@ __device__ __forceinline__ void fused_c_body(const FitDesc& f, int blk) {
     __shared__ uint32_t s_zhi[MTGP_MAX_DIM];
     __shared__ uint32_t s_sh[MTGP_TMAX * MTGP_MAX_DIM];
     __shared__ uint32_t s_gen[MTGP_MAX_DIM * 32];
-    __shared__ double s_scr[32];
     __shared__ double s_tot[3 + MTGP_MAX_COLS];
     __shared__ double s_etot[MTGP_MAX_DIM];
+    __shared__ uint32_t s_z[kZTab];
     const int HA = 1 << p.a;
     const long long base = (long long)blk << p.a;
     const int d = p.d;
@@ -471,31 +484,41 @@ __device__ __forceinline__ void fused_c_body(const FitDesc& f, int blk) {
     S part[DMAX];
 #pragma unroll
     for (int j = 0; j < DMAX; ++j) part[j] = (S)0;
-    for (int lo = threadIdx.x; lo < HA; lo += blockDim.x) {
-        uint32_t z[DMAX];
-        chunk_point<DMAX>(p.kind, d, (uint32_t)lo, s_zhi, s_gen, p.gen_cols, z);
-        for (int c = 0; c < p.C; ++c) {
-            const S w = el_re(buf[c * HA + lo]);
-            const int t = p.colt[c], u = p.colu[c];
-            S kv[DMAX], pre[DMAX];
-            S pr = (S)1;
+    // dL/deta_j += w K_j prod_{k<j} (1 + eta_k K_k) prod_{k>j} (1 + eta_k K_k) per (column, element)
+    auto item = [&](const uint32_t* zc, int zstride, int c, S w) {
+        const int t = p.colt[c], u = p.colu[c];
+        S kv[DMAX], pre[DMAX];
+        S pr = (S)1;
 #pragma unroll
-            for (int j = 0; j < DMAX; ++j) {
-                if (j < d) {
-                    uint32_t X = pair_word(p.kind, z[j], s_sh[t * d + j], s_sh[u * d + j]);
-                    kv[j] = kernel1d<S>(p.kind, X);
-                    pre[j] = pr;
-                    pr *= (S)1 + s_eta[j] * kv[j];
-                }
+        for (int j = 0; j < DMAX; ++j) {
+            if (j < d) {
+                uint32_t X = pair_word(p.kind, zc[j * zstride], s_sh[t * d + j], s_sh[u * d + j]);
+                kv[j] = kernel1d<S>(p.kind, X);
+                pre[j] = pr;
+                pr *= (S)1 + s_eta[j] * kv[j];
             }
-            S suf = w;
+        }
+        S suf = w;
 #pragma unroll
-            for (int j = DMAX - 1; j >= 0; --j) {
-                if (j < d) {
-                    part[j] += kv[j] * pre[j] * suf;
-                    suf *= (S)1 + s_eta[j] * kv[j];
-                }
+        for (int j = DMAX - 1; j >= 0; --j) {
+            if (j < d) {
+                part[j] += kv[j] * pre[j] * suf;
+                suf *= (S)1 + s_eta[j] * kv[j];
             }
+        }
+    };
+    if (HA * d <= kZTab) {
+        chunk_table(p.kind, d, p.a, s_zhi, s_gen, p.gen_cols, s_z);
+        __syncthreads();
+        for (int e = threadIdx.x; e < HA * p.C; e += blockDim.x) {
+            const int c = e >> p.a, lo = e & (HA - 1);
+            item(s_z + lo, HA, c, el_re(buf[e]));
+        }
+    } else {
+        for (int lo = threadIdx.x; lo < HA; lo += blockDim.x) {
+            uint32_t z[DMAX];
+            chunk_point<DMAX>(p.kind, d, (uint32_t)lo, s_zhi, s_gen, p.gen_cols, z);
+            for (int c = 0; c < p.C; ++c) item(z, 1, c, el_re(buf[c * HA + lo]));
         }
     }
     __shared__ S s_scr_s[32];
@@ -559,7 +582,6 @@ __global__ void __launch_bounds__(512) k_batch_c(const FitDesc* fits, const int2
 namespace {
 
 size_t elem_size_of(bool fp32, bool cplx) { return (fp32 ? 4 : 8) * (cplx ? 2 : 1); }
-size_t elem_size(const Handle* h) { return elem_size_of(h->fp32, h->cplx); }
 
 // Raise a kernel's dynamic shared-memory limit to `bytes` (the default limit counts static shared
 // memory too, so any dynamic size may need it); remembered per kernel so each value is set once.
@@ -668,7 +690,12 @@ size_t smem_b(int T, int C, int lgH, size_t es) {
     const size_t red = (size_t)(3 + T * (T + 1) / 2) * kBThreads * sizeof(double);
     return s > red ? s : red;
 }
-int threads_ac(int a) { return (1 << a) < 512 ? ((1 << a) < 64 ? 64 : (1 << a)) : 512; }
+// A and C threads: with the chunk-point table the (column, element) items are spread over twice the
+// chunk length, otherwise one thread per element; between 64 and 512
+int threads_ac(int a, int d) {
+    const int t = ((1 << a) * d <= kZTab) ? (2 << a) : (1 << a);
+    return t < 512 ? (t < 64 ? 64 : t) : 512;
+}
 
 template <typename S, bool CPLX, int DMAX>
 void phase_ac(bool is_c, const FitDesc* single, const FitDesc* fits, const int2* items, int nitems, int grid,
@@ -767,7 +794,7 @@ void fused_make_desc(const Handle* h, ThetaPtrs th, double* out, double* tau, do
     std::memcpy(desc, &f, sizeof(FitDesc));
 }
 
-int fused_threads(int phase, int a) { return phase == 1 ? kBThreads : threads_ac(a); }
+int fused_threads(int phase, int a, int d) { return phase == 1 ? kBThreads : threads_ac(a, d); }
 
 namespace {
 template <typename F>
@@ -819,7 +846,7 @@ size_t fused_smem(int phase, int T, int C, int m, int a, bool fp32, bool cplx) {
     const size_t es = elem_size_of(fp32, cplx);
     return phase == 1 ? smem_b(T, C, m - a, es) : smem_ac(C, a, es);
 }
-int fused_threads_ac(int a) { return threads_ac(a); }
+int fused_threads_ac(int a, int d) { return threads_ac(a, d); }
 
 bool fused_supported(const Handle* h) {
     int a, lgL;
@@ -841,7 +868,7 @@ void launch_fused(const Handle* h, ThetaPtrs th, bool grad, bool store_alpha, do
     const FitDesc f = make_desc(h, th, o, grad, store_alpha, a, lgL);
     const int C = h->ncols;
     mtgp_prof_begin(h, "fused_a", st);
-    fused_phase(0, h->fp32, h->cplx, h->T, h->d, &f, nullptr, nullptr, 0, f.na, threads_ac(a),
+    fused_phase(0, h->fp32, h->cplx, h->T, h->d, &f, nullptr, nullptr, 0, f.na, threads_ac(a, h->d),
                 fused_smem(0, h->T, C, f.p.m, a, h->fp32, h->cplx), st);
     mtgp_prof_end(h, st);
     mtgp_prof_begin(h, "fused_b", st);
@@ -850,7 +877,7 @@ void launch_fused(const Handle* h, ThetaPtrs th, bool grad, bool store_alpha, do
     mtgp_prof_end(h, st);
     if (!grad) return;
     mtgp_prof_begin(h, "fused_c", st);
-    fused_phase(2, h->fp32, h->cplx, h->T, h->d, &f, nullptr, nullptr, 0, f.na, threads_ac(a),
+    fused_phase(2, h->fp32, h->cplx, h->T, h->d, &f, nullptr, nullptr, 0, f.na, threads_ac(a, h->d),
                 fused_smem(2, h->T, C, f.p.m, a, h->fp32, h->cplx), st);
     mtgp_prof_end(h, st);
 }

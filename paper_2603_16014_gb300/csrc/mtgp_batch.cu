@@ -174,7 +174,7 @@ int build_plan(mtgp_batch_s* b) {
             const int nblk = ph == 1 ? (1 << a) : (1 << (m - a));
             for (int j = 0; j < nblk; ++j) items[k].push_back(make_int2(f, j));
             const size_t sm = fused_smem(ph, h.T, h.ncols, m, a, h.fp32, h.cplx);
-            const int th = fused_threads(ph, a);
+            const int th = fused_threads(ph, a, h.d);
             auto& r = res[k];
             r.first = std::max(r.first, sm);
             r.second = std::max(r.second, th);
@@ -691,7 +691,7 @@ int mtgp_batch_autotune(mtgp_batch_t* b, int reps, int* chosen, cudaStream_t st)
                 for (int ph = 0; ph < 3; ++ph) {
                     const int grid = ph == 1 ? (1 << a) : (1 << (m - a));
                     fused_phase(ph, h.fp32, h.cplx, h.T, h.d, desc.data(), nullptr, nullptr, 0, grid,
-                                fused_threads(ph, a), fused_smem(ph, h.T, h.ncols, m, a, h.fp32, h.cplx), st);
+                                fused_threads(ph, a, h.d), fused_smem(ph, h.T, h.ncols, m, a, h.fp32, h.cplx), st);
                 }
                 cudaEventRecord(e1, st);
                 cudaEventSynchronize(e1);

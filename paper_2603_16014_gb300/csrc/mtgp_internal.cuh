@@ -209,7 +209,7 @@ void fused_make_desc(const Handle* h, ThetaPtrs th, double* out, double* tau, do
 void fused_phase(int phase, bool fp32, bool cplx, int T, int dmax, const void* single, const void* fits,
                  const int2* items, int nitems, int grid, int threads, size_t smem, cudaStream_t st);
 size_t fused_smem(int phase, int T, int C, int m, int a, bool fp32, bool cplx);
-int fused_threads(int phase, int a);
+int fused_threads(int phase, int a, int d);
 int fused_resident_blocks(int phase, bool fp32, bool cplx, int T, int dmax, int threads, size_t smem);
 
 // records the message returned by mtgp_last_error_string for the calling thread (mtgp_api.cu)
