@@ -166,20 +166,6 @@ __device__ void load_R_f(double* sR, const FusedParams& p, const ThetaPtrs& th) 
     }
 }
 
-// deterministic block reduction of one value (all threads call; result valid in thread 0)
-template <typename S>
-__device__ __forceinline__ S block_sum_s(S v, S* scratch) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) scratch[warp] = v;
-    __syncthreads();
-    S r = (S)0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += scratch[w];
-    return r;
-}
-
 // totals of the ncols columns of an (nrows x ncols) partial array into out[q]: warp w sums columns
 // q = w, w + nwarps, ...; lane l adds rows l, l + 32, ... (fixed order), then a shuffle tree.
 __device__ void reduce_columns(const double* part, int nrows, int ncols, double* out) {
@@ -305,6 +291,26 @@ __device__ __forceinline__ void load_design_smem(const FusedParams& p, const uin
     if (threadIdx.x < d) s_zhi[threadIdx.x] = point_word(p.kind, (uint32_t)base, threadIdx.x, s_gen, p.gen_cols);
 }
 
+// Programmatic dependent launch.  The wait returns once the grids this one depends on have finished
+// and their writes are visible (at once when the launch did not allow early start); the trigger lets
+// the next grid in the stream begin its independent prologue.  A, B and C each put the work that
+// reads only handle constants (design words, task covariance, observations) before the wait.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// parameters that are non-finite or negative (eta, v, sigma2) flag ST_NUMERIC; run by block 0 of A
+__device__ __forceinline__ void check_theta_block(const ThetaPtrs& th, int d, int T, int* status) {
+    int bad = 0;
+    for (int j = threadIdx.x; j < d; j += blockDim.x)
+        if (!isfinite(th.eta[j]) || th.eta[j] < 0.0) bad = 1;
+    for (int e = threadIdx.x; e < T * th.s; e += blockDim.x)
+        if (!isfinite(th.W[e])) bad = 1;
+    for (int t = threadIdx.x; t < T; t += blockDim.x)
+        if (!isfinite(th.v[t]) || th.v[t] < 0.0) bad = 1;
+    if (threadIdx.x == 0 && (!isfinite(th.sigma2[0]) || th.sigma2[0] < 0.0)) bad = 1;
+    if (bad) set_status(status, ST_NUMERIC);
+}
+
 template <typename S, bool CPLX, int DMAX>
 __device__ __forceinline__ void fused_a_body(const FitDesc& f, int blk) {
     using E = typename El<S, CPLX>::T;
@@ -324,13 +330,17 @@ __device__ __forceinline__ void fused_a_body(const FitDesc& f, int blk) {
     const long long base = (long long)blk << p.a;
     const int d = p.d;
     __shared__ uint32_t s_z[kZTab];
-    if (threadIdx.x < d) s_eta[threadIdx.x] = (S)eta[threadIdx.x];
+    const bool ztab = HA * d <= kZTab;
     load_design_smem(p, gen, shift, eta, base, s_gen, s_sh, s_zhi);
     __syncthreads();
-    if (HA * d <= kZTab) {
-        // chunk points once per (coordinate, element), then one work item per (column, element)
-        chunk_table(p.kind, d, p.a, s_zhi, s_gen, p.gen_cols, s_z);
-        __syncthreads();
+    if (ztab) chunk_table(p.kind, d, p.a, s_zhi, s_gen, p.gen_cols, s_z);  // chunk points, once per (coordinate, element)
+    pdl_wait();  // parameters and the spectra buffer belong to earlier work in the stream
+    pdl_trigger();
+    if (blk == 0) check_theta_block(f.th, d, p.T, f.status);
+    if (threadIdx.x < d) s_eta[threadIdx.x] = (S)eta[threadIdx.x];
+    __syncthreads();
+    if (ztab) {
+        // one work item per (column, element)
         for (int e = threadIdx.x; e < HA * p.C; e += blockDim.x) {
             const int c = e >> p.a, lo = e & (HA - 1);
             const int t = p.colt[c], u = p.colu[c];
@@ -416,6 +426,8 @@ __device__ __forceinline__ void fused_b_body(const FitDesc& f, int blk) {
 #pragma unroll
         for (int t = 0; t < T; ++t) rh0[t] = (r < tile && f != 0) ? ld<CPLX>(yhat, (long long)t * p.n + f) : czero<V>();
     }
+    pdl_wait();  // the spectra come from kernel A
+    pdl_trigger();
     const E* in = reinterpret_cast<const E*>(spec);
     for (int e = threadIdx.x; e < tile * p.C; e += blockDim.x) {
         const int c = e >> lgT;
@@ -546,6 +558,13 @@ __device__ __forceinline__ void fused_c_body(const FitDesc& f, int blk) {
     const int d = p.d;
     if (threadIdx.x < d) s_eta[threadIdx.x] = (S)eta[threadIdx.x];
     load_design_smem(p, gen, shift, eta, base, s_gen, s_sh, s_zhi);
+    const bool ztab = HA * d <= kZTab;
+    if (ztab) {
+        __syncthreads();
+        chunk_table(p.kind, d, p.a, s_zhi, s_gen, p.gen_cols, s_z);
+    }
+    pdl_wait();  // the adjoint weights and kernel B's partial sums
+    pdl_trigger();
     const E* in = reinterpret_cast<const E*>(wgt);
     for (int e = threadIdx.x; e < HA * p.C; e += blockDim.x) {
         const int c = e >> p.a;
@@ -581,9 +600,7 @@ __device__ __forceinline__ void fused_c_body(const FitDesc& f, int blk) {
             }
         }
     };
-    if (HA * d <= kZTab) {
-        chunk_table(p.kind, d, p.a, s_zhi, s_gen, p.gen_cols, s_z);
-        __syncthreads();
+    if (ztab) {
         for (int e = threadIdx.x; e < HA * p.C; e += blockDim.x) {
             const int c = e >> p.a, lo = e & (HA - 1);
             item(s_z + lo, HA, c, el_re(buf[e]));
@@ -595,10 +612,25 @@ __device__ __forceinline__ void fused_c_body(const FitDesc& f, int blk) {
             for (int c = 0; c < p.C; ++c) item(z, 1, c, el_re(buf[c * HA + lo]));
         }
     }
-    __shared__ S s_scr_s[32];
-    for (int j = 0; j < d; ++j) {
-        S v = block_sum_s<S>(j < DMAX ? part[j] : (S)0, s_scr_s);
-        if (threadIdx.x == 0) partials_c[(long long)blk * d + j] = (double)v;
+    // the d block sums together: a shuffle tree per warp, one shared row per warp, warps added in
+    // order by thread j (the same order as one block sum per coordinate, one barrier instead of 2d)
+    __shared__ S s_red[16][DMAX];
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j) {
+            if (j < d) {
+                S v = part[j];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                if (lane == 0) s_red[warp][j] = v;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < d) {
+            S v = (S)0;
+            for (int w = 0; w < nw; ++w) v += s_red[w][threadIdx.x];
+            partials_c[(long long)blk * d + threadIdx.x] = (double)v;
+        }
     }
     if (!last_block(counter, f.na)) return;
     const int NQ = 3 + p.T * (p.T + 1) / 2;
@@ -771,13 +803,29 @@ int threads_ac(int a, int d) {
     return t < 512 ? (t < 64 ? 64 : t) : 512;
 }
 
+// a single-fit launch that may start while the previous kernel in the stream finishes
+template <typename... KArgs>
+void launch_pdl(void (*kernel)(KArgs...), int grid, int threads, size_t smem, cudaStream_t st, const FitDesc& f) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, f);
+}
+
 template <typename S, bool CPLX, int DMAX>
 void phase_ac(bool is_c, const FitDesc* single, const FitDesc* fits, const int2* items, int nitems, int grid,
               int threads, size_t smem, cudaStream_t st) {
     if (!is_c) {
         if (single) {
             set_smem(k_fused_a<S, CPLX, DMAX>, smem);
-            k_fused_a<S, CPLX, DMAX><<<grid, threads, smem, st>>>(*single);
+            launch_pdl(k_fused_a<S, CPLX, DMAX>, grid, threads, smem, st, *single);
         } else {
             set_smem(k_batch_a<S, CPLX, DMAX>, smem);
             k_batch_a<S, CPLX, DMAX><<<grid, threads, smem, st>>>(fits, items, nitems);
@@ -785,7 +833,7 @@ void phase_ac(bool is_c, const FitDesc* single, const FitDesc* fits, const int2*
     } else {
         if (single) {
             set_smem(k_fused_c<S, CPLX, DMAX>, smem);
-            k_fused_c<S, CPLX, DMAX><<<grid, threads, smem, st>>>(*single);
+            launch_pdl(k_fused_c<S, CPLX, DMAX>, grid, threads, smem, st, *single);
         } else {
             set_smem(k_batch_c<S, CPLX, DMAX>, smem);
             k_batch_c<S, CPLX, DMAX><<<grid, threads, smem, st>>>(fits, items, nitems);
@@ -807,7 +855,7 @@ void phase_b_t(const FitDesc* single, const FitDesc* fits, const int2* items, in
                cudaStream_t st) {
     if (single) {
         set_smem(k_fused_b<T, CPLX, S>, smem);
-        k_fused_b<T, CPLX, S><<<grid, kBThreads, smem, st>>>(*single);
+        launch_pdl(k_fused_b<T, CPLX, S>, grid, kBThreads, smem, st, *single);
     } else {
         set_smem(k_batch_b<T, CPLX, S>, smem);
         k_batch_b<T, CPLX, S><<<grid, kBThreads, smem, st>>>(fits, items, nitems);

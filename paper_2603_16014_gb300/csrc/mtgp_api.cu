@@ -128,13 +128,14 @@ int validate_theta(const Handle* h, const double* eta, const double* W, int s, c
 // NLL (and gradient) at theta; leaves alpha = Lambda^-1 rhat in h->alpha and tau in h->tau.
 int run_nll(Handle* h, ThetaPtrs th, bool grad, double* out, double* tau, double* g_eta, double* g_W, double* g_v,
             double* g_s2, cudaStream_t st, bool store_alpha = false) {
-    k_check_theta<<<1, 64, 0, st>>>(th, h->d, h->T, h->status);
     if (h->equal && fused_supported(h)) {
+        // kernel A's block 0 checks the parameters
         launch_fused(h, th, grad, store_alpha, out, tau, g_eta, g_W, g_v, g_s2, st);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
         return MTGP_OK;
     }
+    k_check_theta<<<1, 64, 0, st>>>(th, h->d, h->T, h->status);
     mtgp_prof_begin(h, "colgen", st);
     launch_colgen(h, th.eta, h->spec, st);
     mtgp_prof_end(h, st);

@@ -121,6 +121,15 @@ def test_errors_surface_through_status():
         model.nll(p.eta, np.zeros_like(p.W), -np.ones(p.T), 1e-6)
         model.sync()
     model.sync()
+    # a non-finite parameter is flagged by the fused kernels' own check
+    with pytest.raises(MTGPError) as ei:
+        model.nll_grad(np.r_[np.nan, p.eta[1:]], p.W, p.v, p.sigma2)
+        model.sync()
+    assert ei.value.code == 3
+    model.sync()
+    out, _ = model.nll(p.eta, p.W, p.v, p.sigma2)  # and the handle stays usable
+    model.sync()
+    assert np.isfinite(out[0].item())
     # unequal sizes: variance not supported in this build, mean is
     q = inputs.make_problem("dnet", 2, (5, 3), seed=3)
     mq = _model(q, "fp64")
