@@ -31,6 +31,9 @@ METRIC = "NLL+grad evals/s (T=4, N=4·2^16) vs plain; % HBM peak; fit time w/ pr
 UNIT = "evals/s"
 WORKLOAD = "dnet_d8_T4_n2^16_nll_grad"
 FP64_PEAK_TFLOPS = 1.25       # GB300 dense FP64, nominal
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_fused_b launch on this workload, from one ncu
+# capture (caches flushed by ncu between passes); valid while the kernel is unchanged
+FUSED_B_DRAM_BYTES = 3998208
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -294,7 +297,7 @@ def run_ours(args, rank, world, local_rank):
         achieved = flops / dom_avg_s / 1e12
         roof = {"bound": "alu", "kernel": "k_fused_b (transform stages a..m-1 + FP64 per-frequency solve + adjoint stages)",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": FUSED_B_DRAM_BYTES,
                 "flops_per_launch": flops, "avg_launch_us": dom_avg_s * 1e6,
                 "peak_source": "GB300 dense FP64 nominal (1.25 TFLOP/s); FMA probe measured 1.20"}
     else:

@@ -168,11 +168,21 @@ __device__ void load_R_f(double* sR, const FusedParams& p, const ThetaPtrs& th) 
 
 // totals of the ncols columns of an (nrows x ncols) partial array into out[q]: warp w sums columns
 // q = w, w + nwarps, ...; lane l adds rows l, l + 32, ... (fixed order), then a shuffle tree.
+// The loads of 8 rows are issued before their additions (same order, one memory round trip per 8).
 __device__ void reduce_columns(const double* part, int nrows, int ncols, double* out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int q = warp; q < ncols; q += nw) {
         double v = 0.0;
-        for (int b = lane; b < nrows; b += 32) v += part[(long long)b * ncols + q];
+        for (int b0 = lane; b0 < nrows; b0 += 256) {
+            double t[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int b = b0 + 32 * k;
+                t[k] = b < nrows ? part[(long long)b * ncols + q] : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v += t[k];
+        }
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) out[q] = v;
     }
