@@ -111,6 +111,10 @@ k_solve_equal(const void* spec, void* wgt, const double* yhat, SolveParams p, Th
 
 constexpr int kTreeThreads = 256;
 constexpr int kTreeWarps = kTreeThreads / 32;
+// A CTA owns kTreeCW consecutive residue classes; lane l works on class l mod kTreeCW in slot
+// (warp, l / kTreeCW), and the kTreeSlots slots of a class split its nodes.
+constexpr int kTreeCW = 8;
+constexpr int kTreeSlots = kTreeThreads / kTreeCW;
 
 struct TreeParams {
     int T, s, grad, clamp;
@@ -134,34 +138,59 @@ __device__ void load_R_tree(double* sR, const TreeParams& p, const ThetaPtrs& th
 
 __device__ __forceinline__ int gidx(int t, int u, int T) { return t * T - t * (t - 1) / 2 + (u - t); }
 
+// Parts a reduction of rr terms for each of ma targets is split into, so that ma * parts fills the
+// kTreeSlots slots of a class when ma is small (all sizes are powers of two).
+__device__ __forceinline__ int split_parts(long long ma, long long rr) {
+    if (ma >= kTreeSlots) return 1;
+    long long P = kTreeSlots / ma;
+    return (int)(P < rr ? P : rr);
+}
+
 // Forward solve L u = r on the class graph (right-looking), accumulating sum |u_j|^2 / D_j.
 // Node (t, f) is eliminated at stage t; its ancestor in task a > t is (a, f mod n_a) and
-// L[(a, .), (t, f)] = conj(S_{ta}[f]) / D_{(t,f)}.
+// L[(a, .), (t, f)] = conj(S_{ta}[f]) / D_{(t,f)}.  The diagonal slot of S holds 1 / D.
 template <bool CPLX>
-__device__ void tree_forward(const TreeParams& p, const double* Sb, double* rb, long long rho, bool act, int warp,
-                             double& quad) {
+__device__ void tree_forward(const TreeParams& p, const double* Sb, double* rb, long long rho, bool act, int slot,
+                             double& quad, Vt<CPLX> (*s_part)[kTreeSlots][MTGP_TMAX]) {
     using V = Vt<CPLX>;
     const long long nT = p.nT;
+    const int cls = (int)(rho % kTreeCW);
     for (int t = 0; t < p.T; ++t) {
         const long long mt = p.n[t] / nT;
         if (act) {
-            for (long long k = warp; k < mt; k += kTreeWarps) {
+            for (long long k = slot; k < mt; k += kTreeSlots) {
                 long long f = rho + k * nT;
-                double D = creal(ld<CPLX>(Sb, p.po[t][t] + f));
-                quad += cabs2(ld<CPLX>(rb, p.yoff[t] + f)) / D;
+                quad += cabs2(ld<CPLX>(rb, p.yoff[t] + f)) * creal(ld<CPLX>(Sb, p.po[t][t] + f));
             }
-            for (int a = t + 1; a < p.T; ++a) {
-                const long long ma = p.n[a] / nT, rr = p.n[t] / p.n[a];
-                for (long long gi = warp; gi < ma; gi += kTreeWarps) {
-                    V acc = czero<V>();
-                    for (long long q = 0; q < rr; ++q) {
-                        long long f = rho + (gi + q * ma) * nT;
-                        double D = creal(ld<CPLX>(Sb, p.po[t][t] + f));
-                        acc = vadd(acc, vscale(vmul(cconj(ld<CPLX>(Sb, p.po[t][a] + f)), ld<CPLX>(rb, p.yoff[t] + f)), 1.0 / D));
-                    }
+        }
+        for (int a = t + 1; a < p.T; ++a) {
+            const long long ma = p.n[a] / nT, rr = p.n[t] / p.n[a];
+            const int P = split_parts(ma, rr);
+            for (long long u = slot; u < ma * P; u += kTreeSlots) {
+                if (!act) break;
+                const long long gi = u / P, part = u % P, q0 = part * (rr / P), q1 = q0 + rr / P;
+                V acc = czero<V>();
+                for (long long q = q0; q < q1; ++q) {
+                    long long f = rho + (gi + q * ma) * nT;
+                    const double iD = creal(ld<CPLX>(Sb, p.po[t][t] + f));
+                    acc = vadd(acc, vmul(cconj(ld<CPLX>(Sb, p.po[t][a] + f)), vscale(ld<CPLX>(rb, p.yoff[t] + f), iD)));
+                }
+                if (P == 1) {
                     long long g = rho + gi * nT;
                     st<CPLX>(rb, p.yoff[a] + g, vsub(ld<CPLX>(rb, p.yoff[a] + g), acc));
+                } else {
+                    s_part[cls][u][0] = acc;
                 }
+            }
+            if (P > 1) {
+                __syncthreads();
+                if (act && slot < ma) {
+                    V acc = czero<V>();
+                    for (int part = 0; part < P; ++part) acc = vadd(acc, s_part[cls][slot * P + part][0]);
+                    long long g = rho + slot * nT;
+                    st<CPLX>(rb, p.yoff[a] + g, vsub(ld<CPLX>(rb, p.yoff[a] + g), acc));
+                }
+                __syncthreads();
             }
         }
         __syncthreads();
@@ -171,39 +200,44 @@ __device__ void tree_forward(const TreeParams& p, const double* Sb, double* rb, 
 // Backward solve L^H alpha = D^-1 u (top-down) and, when wantZ, the selected inverse on the
 // pattern:  Z[j, a'] = -sum_{a in anc(j)} conj(L[a, j]) Z[a, a']  (a' in anc(j)),
 //           Z[j, j]  = 1/D_j - sum_{a in anc(j)} conj(L[a, j]) Z[a, j].
-// Z is stored like S: Z_{ta'}[f] = Z[(t, f), (a', f mod n_a')].
+// Z is stored like S: Z_{ta'}[f] = Z[(t, f), (a', f mod n_a')].  The diagonal slot of S holds 1 / D.
 template <bool CPLX>
 __device__ void tree_backward(const TreeParams& p, const double* Sb, double* Zb, const double* rb, double* ab,
-                              long long rho, bool act, int warp, bool wantZ) {
+                              long long rho, bool act, int slot, bool wantZ) {
     using V = Vt<CPLX>;
     const long long nT = p.nT;
     for (int t = p.T - 1; t >= 0; --t) {
         const long long mt = p.n[t] / nT;
         if (act) {
-            for (long long k = warp; k < mt; k += kTreeWarps) {
+            for (long long k = slot; k < mt; k += kTreeSlots) {
                 long long f = rho + k * nT;
-                double invD = 1.0 / creal(ld<CPLX>(Sb, p.po[t][t] + f));
+                const double invD = creal(ld<CPLX>(Sb, p.po[t][t] + f));
+                V l[MTGP_TMAX];
+#pragma unroll
+                for (int a1 = 0; a1 < MTGP_TMAX; ++a1)
+                    l[a1] = (a1 > t && a1 < p.T) ? vscale(ld<CPLX>(Sb, p.po[t][a1] + f), invD) : czero<V>();
                 V a = vscale(ld<CPLX>(rb, p.yoff[t] + f), invD);
-                for (int a2 = t + 1; a2 < p.T; ++a2) {
-                    V l = vscale(ld<CPLX>(Sb, p.po[t][a2] + f), invD);
-                    a = vsub(a, vmul(l, ld<CPLX>(ab, p.yoff[a2] + (f & (p.n[a2] - 1)))));
-                }
+#pragma unroll
+                for (int a2 = 0; a2 < MTGP_TMAX; ++a2)
+                    if (a2 > t && a2 < p.T) a = vsub(a, vmul(l[a2], ld<CPLX>(ab, p.yoff[a2] + (f & (p.n[a2] - 1)))));
                 st<CPLX>(ab, p.yoff[t] + f, a);
                 if (wantZ) {
                     double zd = invD;
-                    for (int a2 = t + 1; a2 < p.T; ++a2) {
-                        V z = czero<V>();
-                        for (int a1 = t + 1; a1 < p.T; ++a1) {
-                            V l = vscale(ld<CPLX>(Sb, p.po[t][a1] + f), invD);
-                            V zz = (a1 <= a2) ? ld<CPLX>(Zb, p.po[a1][a2] + (f & (p.n[a1] - 1)))
-                                              : cconj(ld<CPLX>(Zb, p.po[a2][a1] + (f & (p.n[a2] - 1))));
-                            z = vsub(z, vmul(l, zz));
+#pragma unroll
+                    for (int a2 = 0; a2 < MTGP_TMAX; ++a2) {
+                        if (a2 > t && a2 < p.T) {
+                            V z = czero<V>();
+#pragma unroll
+                            for (int a1 = 0; a1 < MTGP_TMAX; ++a1) {
+                                if (a1 > t && a1 < p.T) {
+                                    V zz = (a1 <= a2) ? ld<CPLX>(Zb, p.po[a1][a2] + (f & (p.n[a1] - 1)))
+                                                      : cconj(ld<CPLX>(Zb, p.po[a2][a1] + (f & (p.n[a2] - 1))));
+                                    z = vsub(z, vmul(l[a1], zz));
+                                }
+                            }
+                            st<CPLX>(Zb, p.po[t][a2] + f, z);
+                            zd -= creal(vmul(l[a2], cconj(z)));
                         }
-                        st<CPLX>(Zb, p.po[t][a2] + f, z);
-                    }
-                    for (int a1 = t + 1; a1 < p.T; ++a1) {
-                        V l = vscale(ld<CPLX>(Sb, p.po[t][a1] + f), invD);
-                        zd -= creal(vmul(l, cconj(ld<CPLX>(Zb, p.po[t][a1] + f))));
                     }
                     st<CPLX>(Zb, p.po[t][t] + f, cfromreal<V>(zd));
                 }
@@ -213,8 +247,8 @@ __device__ void tree_backward(const TreeParams& p, const double* Sb, double* Zb,
     }
 }
 
-// A CTA owns 32 consecutive residue classes rho mod n_T (one per lane); its warps split the nodes
-// of each class, so a warp's accesses touch 32 consecutive frequencies.  The first class (rho = 0)
+// A CTA owns kTreeCW consecutive residue classes rho mod n_T; the kTreeSlots slots of a class split
+// its nodes, so a warp's accesses touch runs of kTreeCW consecutive frequencies.  The first class (rho = 0)
 // also carries the optimal means (theorem item 4): it is solved once with yhat to get Pi and
 // E K~^-1 y, then every class is solved with rhat.
 template <bool CPLX, typename S>
@@ -233,9 +267,12 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
     if (threadIdx.x == 0) s_sig = th.sigma2[0];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int slot = warp * (32 / kTreeCW) + lane / kTreeCW;
     const long long nT = p.nT;
-    const long long rho = (long long)blockIdx.x * 32 + lane;
+    const int cls = lane % kTreeCW;
+    const long long rho = (long long)blockIdx.x * kTreeCW + cls;
     const bool act = rho < nT;
+    __shared__ V s_part[kTreeCW][kTreeSlots][MTGP_TMAX];  // partial sums of split reductions
     double acc[3 + MTGP_MAX_COLS];
     for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
     int bad = 0;
@@ -246,7 +283,7 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
         for (int u = t; u < T; ++u) {
             const double sc = sqrt((double)p.n[u] / (double)p.n[t]) * sR[t * T + u];
             if (!act) continue;
-            for (long long k = warp; k < mt; k += kTreeWarps) {
+            for (long long k = slot; k < mt; k += kTreeSlots) {
                 long long f = rho + k * nT;
                 V mu = load_spec<S, CPLX>(spec, p.po[t][u] + f);
                 V val;
@@ -263,30 +300,62 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
     }
     __syncthreads();
 
-    // elimination in task order: pivots are the Schur complements S_t of Algorithm 1
+    // elimination in task order: pivots are the Schur complements S_t of Algorithm 1.  A pivot's
+    // diagonal slot is replaced by 1 / D once its log is taken; for each target node (a, g) the
+    // factors L = conj(S_{ta}) / D of the rr nodes above it are formed once and applied to every
+    // a2 >= a.
     for (int t = 0; t < T; ++t) {
         const long long mt = p.n[t] / nT;
         if (act) {
-            for (long long k = warp; k < mt; k += kTreeWarps) {
+            for (long long k = slot; k < mt; k += kTreeSlots) {
                 long long f = rho + k * nT;
                 double D = creal(ld<CPLX>(Sb, p.po[t][t] + f));
                 if (!(D > 0.0) || !isfinite(D)) bad = 1;
                 else acc[0] += log(D);
+                st<CPLX>(Sb, p.po[t][t] + f, cfromreal<V>(1.0 / D));
             }
-            for (int a = t + 1; a < T; ++a) {
-                const long long ma = p.n[a] / nT, rr = p.n[t] / p.n[a];
-                for (int a2 = a; a2 < T; ++a2) {
-                    for (long long gi = warp; gi < ma; gi += kTreeWarps) {
-                        V s = czero<V>();
-                        for (long long q = 0; q < rr; ++q) {
-                            long long f = rho + (gi + q * ma) * nT;
-                            double D = creal(ld<CPLX>(Sb, p.po[t][t] + f));
-                            s = vadd(s, vscale(vmul(cconj(ld<CPLX>(Sb, p.po[t][a] + f)), ld<CPLX>(Sb, p.po[t][a2] + f)), 1.0 / D));
-                        }
-                        long long g = rho + gi * nT;
-                        st<CPLX>(Sb, p.po[a][a2] + g, vsub(ld<CPLX>(Sb, p.po[a][a2] + g), s));
+        }
+        __syncthreads();
+        for (int a = t + 1; a < T; ++a) {
+            const long long ma = p.n[a] / nT, rr = p.n[t] / p.n[a];
+            const int P = split_parts(ma, rr);
+            for (long long u = slot; u < ma * P; u += kTreeSlots) {
+                if (!act) break;
+                const long long gi = u / P, part = u % P, q0 = part * (rr / P), q1 = q0 + rr / P;
+                V sacc[MTGP_TMAX];
+#pragma unroll
+                for (int a2 = 0; a2 < MTGP_TMAX; ++a2) sacc[a2] = czero<V>();
+                for (long long q = q0; q < q1; ++q) {
+                    long long f = rho + (gi + q * ma) * nT;
+                    const double iD = creal(ld<CPLX>(Sb, p.po[t][t] + f));
+                    const V l = vscale(cconj(ld<CPLX>(Sb, p.po[t][a] + f)), iD);
+#pragma unroll
+                    for (int a2 = 0; a2 < MTGP_TMAX; ++a2)
+                        if (a2 >= a && a2 < T) sacc[a2] = vadd(sacc[a2], vmul(l, ld<CPLX>(Sb, p.po[t][a2] + f)));
+                }
+                if (P == 1) {
+                    long long g = rho + gi * nT;
+#pragma unroll
+                    for (int a2 = 0; a2 < MTGP_TMAX; ++a2)
+                        if (a2 >= a && a2 < T) st<CPLX>(Sb, p.po[a][a2] + g, vsub(ld<CPLX>(Sb, p.po[a][a2] + g), sacc[a2]));
+                } else {
+#pragma unroll
+                    for (int a2 = 0; a2 < MTGP_TMAX; ++a2)
+                        if (a2 >= a && a2 < T) s_part[cls][u][a2] = sacc[a2];
+                }
+            }
+            if (P > 1) {
+                // parts of one target added in order by the target's slot
+                __syncthreads();
+                if (act && slot < ma) {
+                    long long g = rho + slot * nT;
+                    for (int a2 = a; a2 < T; ++a2) {
+                        V acc = czero<V>();
+                        for (int part = 0; part < P; ++part) acc = vadd(acc, s_part[cls][slot * P + part][a2]);
+                        st<CPLX>(Sb, p.po[a][a2] + g, vsub(ld<CPLX>(Sb, p.po[a][a2] + g), acc));
                     }
                 }
+                __syncthreads();
             }
         }
         __syncthreads();
@@ -298,14 +367,14 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
         if (act0) {
             for (int t = 0; t < T; ++t) {
                 const long long mt = p.n[t] / nT;
-                for (long long k = warp; k < mt; k += kTreeWarps)
+                for (long long k = slot; k < mt; k += kTreeSlots)
                     st<CPLX>(rb, p.yoff[t] + k * nT, ld<CPLX>(yhat, p.yoff[t] + k * nT));
             }
         }
         __syncthreads();
         double qd = 0.0;
-        tree_forward<CPLX>(p, Sb, rb, rho, act0, warp, qd);
-        tree_backward<CPLX>(p, Sb, Zb, rb, ab, rho, act0, warp, true);
+        tree_forward<CPLX>(p, Sb, rb, rho, act0, slot, qd, s_part);
+        tree_backward<CPLX>(p, Sb, Zb, rb, ab, rho, act0, slot, true);
         if (threadIdx.x == 0) {
             double Pi[MTGP_TMAX][MTGP_TMAX], b[MTGP_TMAX];
             for (int t = 0; t < T; ++t) {
@@ -353,7 +422,7 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
     if (act) {
         for (int t = 0; t < T; ++t) {
             const long long mt = p.n[t] / nT;
-            for (long long k = warp; k < mt; k += kTreeWarps) {
+            for (long long k = slot; k < mt; k += kTreeSlots) {
                 long long f = rho + k * nT;
                 V y = ld<CPLX>(yhat, p.yoff[t] + f);
                 if (f == 0) y = vsub(y, cfromreal<V>(sqrt((double)p.n[t]) * s_tau[t]));
@@ -362,8 +431,8 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
         }
     }
     __syncthreads();
-    tree_forward<CPLX>(p, Sb, rb, rho, act, warp, acc[1]);
-    tree_backward<CPLX>(p, Sb, Zb, rb, ab, rho, act, warp, p.grad != 0);
+    tree_forward<CPLX>(p, Sb, rb, rho, act, slot, acc[1], s_part);
+    tree_backward<CPLX>(p, Sb, Zb, rb, ab, rho, act, slot, p.grad != 0);
 
     if (p.grad && act) {
         for (int t = 0; t < T; ++t) {
@@ -371,7 +440,7 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
             for (int u = t; u < T; ++u) {
                 const double sc = sqrt((double)p.n[u] / (double)p.n[t]);
                 const int q = 3 + gidx(t, u, T);
-                for (long long k = warp; k < mt; k += kTreeWarps) {
+                for (long long k = slot; k < mt; k += kTreeSlots) {
                     long long f = rho + k * nT;
                     V at = ld<CPLX>(ab, p.yoff[t] + f);
                     V au = ld<CPLX>(ab, p.yoff[u] + (f & (p.n[u] - 1)));
@@ -480,7 +549,7 @@ int eq_blocks(const Handle* h) {
 }  // namespace
 
 int solve_equal_blocks(const Handle* h) { return eq_blocks(h); }
-int solve_tree_blocks(const Handle* h) { return (int)((h->n[h->T - 1] + 31) / 32); }
+int solve_tree_blocks(const Handle* h) { return (int)((h->n[h->T - 1] + kTreeCW - 1) / kTreeCW); }
 
 template <int T, bool CPLX, typename S>
 static void run_eq(const Handle* h, ThetaPtrs th, SolveParams sp, double* partials, cudaStream_t st) {

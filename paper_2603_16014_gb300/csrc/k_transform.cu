@@ -13,37 +13,18 @@
 // global loads and stores are contiguous runs of L elements.
 #include <cstdio>
 
-#include "mtgp_internal.cuh"
+#include "butterfly.cuh"
 
 namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxTileBytes = 64 * 1024;
 
-template <typename S>
-struct TwidT;
-template <>
-struct TwidT<float> { using T = cx<float>; };
-template <>
-struct TwidT<double> { using T = cx<double>; };
-
-template <typename S, bool CPLX>
-struct Elem;
-template <typename S>
-struct Elem<S, false> { using T = S; };
-template <typename S>
-struct Elem<S, true> { using T = cx<S>; };
-
-template <typename S>
-__device__ __forceinline__ S bfly_mul(S x, cx<S>) { return x; }
-template <typename S>
-__device__ __forceinline__ cx<S> bfly_mul(cx<S> x, cx<S> w) { return x * w; }
-
 template <typename S, bool CPLX, bool DIF>
 __global__ void __launch_bounds__(kThreads)
-k_xform_pass(typename Elem<S, CPLX>::T* __restrict__ base, const long long* __restrict__ offs, int m,
+k_xform_pass(typename El<S, CPLX>::T* __restrict__ base, const long long* __restrict__ offs, int m,
              int s0, int s1, int lgL, const cx<S>* __restrict__ tw, int mtw) {
-    using E = typename Elem<S, CPLX>::T;
+    using E = typename El<S, CPLX>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     E* buf = reinterpret_cast<E*>(smem_raw);
     const int lgH = s1 - s0;
@@ -59,34 +40,7 @@ k_xform_pass(typename Elem<S, CPLX>::T* __restrict__ base, const long long* __re
         buf[e] = a[hibase + ((long long)h << s0) + lo0 + lo];
     }
     __syncthreads();
-    const int nb = (H * L) >> 1;
-    for (int st = 0; st < lgH; ++st) {
-        const int s = DIF ? (s1 - 1 - st) : (s0 + st);
-        const int ls = s - s0;
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-            int lo = b & (L - 1);
-            int hb = b >> lgL;
-            int hlo = hb & ((1 << ls) - 1);
-            int h1 = ((hb >> ls) << (ls + 1)) | hlo;
-            int h2 = h1 + (1 << ls);
-            E x1 = buf[(h1 << lgL) + lo];
-            E x2 = buf[(h2 << lgL) + lo];
-            cx<S> w;
-            if (CPLX) {
-                long long e = lo0 + lo + ((long long)hlo << s0);
-                w = tw[e << (mtw - 1 - s)];
-            }
-            if (!DIF) {
-                E t = bfly_mul(x2, w);
-                buf[(h1 << lgL) + lo] = x1 + t;
-                buf[(h2 << lgL) + lo] = x1 - t;
-            } else {
-                buf[(h1 << lgL) + lo] = x1 + x2;
-                buf[(h2 << lgL) + lo] = bfly_mul(x1 - x2, w);
-            }
-        }
-        __syncthreads();
-    }
+    smem_stages<S, CPLX, DIF>(buf, 1, H * L, lgH, lgL, s0, lo0, tw, mtw);
     for (int e = threadIdx.x; e < H * L; e += blockDim.x) {
         int h = e >> lgL, lo = e & (L - 1);
         a[hibase + ((long long)h << s0) + lo0 + lo] = buf[e];
@@ -96,7 +50,7 @@ k_xform_pass(typename Elem<S, CPLX>::T* __restrict__ base, const long long* __re
 template <typename S, bool CPLX, bool DIF>
 void run_pass(void* base, const long long* offs, int narr, int m, int s0, int s1, const void* tw, int mtw,
               cudaStream_t st) {
-    using E = typename Elem<S, CPLX>::T;
+    using E = typename El<S, CPLX>::T;
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_xform_pass<S, CPLX, DIF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
