@@ -102,6 +102,22 @@ def test_posterior_vs_dense_oracle(kind, d, m, precision):
         assert np.allclose(var.cpu().numpy(), var_ref, rtol=0, atol=tol * prior.max())
 
 
+@pytest.mark.parametrize("nq", [1, 2, 257, 4099])
+def test_posterior_mean_slicing_edge_cases(nq):
+    """The mean splits queries and design points over CTAs: one query (every point slice in its own
+    CTA), ragged query counts, per-task slices of unequal tasks with partial last slices."""
+    p = inputs.make_problem("lattice", 3, (9, 7, 5), seed=48, eta=0.6, v=0.1, sigma2=1e-4)
+    X = _points_oracle(p)
+    y = inputs.synth_y(p, X)
+    Xq, xq, tq = inputs.query_points(nq, 3, seed=6, tasks=3)
+    mean_ref, _, prior = dense.posterior(p.kind, X, y, p.eta, p.W, p.v, p.sigma2, Xq, tq)
+    model = _model(p, "fp64")
+    model.set_y(torch.from_numpy(y))
+    mean, _ = model.posterior(p.eta, p.W, p.v, p.sigma2, torch.from_numpy(xq), torch.from_numpy(tq), variance=False)
+    model.sync()
+    assert np.allclose(mean.cpu().numpy(), mean_ref, rtol=0, atol=TOL_NLL["fp64"] * prior.max())
+
+
 def test_errors_surface_through_status():
     p = inputs.make_problem("dnet", 2, (5, 5), seed=3, sigma2=1e-4)
     from paper_2603_16014_gb300._lib import MTGPError
