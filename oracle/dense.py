@@ -70,6 +70,24 @@ def nll(kind, X_tasks, y, eta, W, v, sigma2):
                 tau=tau, alpha=a, Pi=Pi)
 
 
+def gcv(kind, X_tasks, y, eta, W, v, sigma2):
+    """GCV loss (Eq. 3.3, second form) at the GCV mean (Eq. 3.4, second form), by dense inverses:
+    tau solves (E K~^-2 E^T) tau = E K~^-2 y, r = y - E^T tau, L = r^T K~^-2 r / trace(K~^-1)^2.
+    Returns dict L, num (r^T K~^-2 r), trace (trace K~^-1), tau."""
+    R = task_covariance(W, v)
+    K = gram(kind, X_tasks, eta, R, sigma2)
+    n = [len(X) for X in X_tasks]
+    E = summing_matrix(n)
+    Kinv = np.linalg.inv(K)
+    Kinv = 0.5 * (Kinv + Kinv.T)
+    K2 = Kinv @ Kinv
+    tau = np.linalg.solve(E @ K2 @ E.T, E @ K2 @ y)
+    r = y - E.T @ tau
+    num = float(r @ K2 @ r)
+    tr = float(np.trace(Kinv))
+    return dict(L=num / tr ** 2, num=num, trace=tr, tau=tau)
+
+
 def nll_grad(kind, X_tasks, y, eta, W, v, sigma2):
     """Analytic gradient of L (Eq. 3.3) w.r.t. eta (d), W (T x s), v (T), sigma2, at the optimal tau.
 

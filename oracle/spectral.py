@@ -323,6 +323,73 @@ def nll_equal(kind, gen, shift, m, y, eta, W, v, sigma2):
                 logdet=logdet, tau=tau)
 
 
+def gcv_by_class(kind, gen, shift, m, y, eta, W, v, sigma2):
+    """GCV loss via the residue classes mod n_T: tau_GCV from (H H^*) tau = E K~^-2 y with
+    H = (sqrt(n_t) (Lambda~^-1)_{(t,0), k}) over the nodes k of class 0 (Theorem FMTGP item 4),
+    then num = ||Lambda~^-1 rhat||^2 and trace = trace(Lambda~^-1) summed over classes."""
+    order = sorted_order(m)
+    n_user = [1 << int(x) for x in m]
+    offs = np.concatenate([[0], np.cumsum(n_user)])
+    X = [design_points(kind, gen, shift[t], n_user[t]) for t in order]
+    ys = [np.asarray(y[offs[t]:offs[t + 1]], dtype=np.float64) for t in order]
+    R = task_covariance(W, v)[np.ix_(order, order)]
+    n = [n_user[t] for t in order]
+    T = len(n)
+    lam = lambda_blocks(kind, X, eta, R, sigma2)
+    yhat = [vdag(kind, ys[t].astype(np.complex128), int(np.log2(n[t]))) for t in range(T)]
+    nT = n[-1]
+    nodes0, M0 = class_matrix(lam, n, 0)
+    Minv0 = np.linalg.inv(M0)
+    pos0 = [nodes0.index((t, 0)) for t in range(T)]
+    H = np.array([np.sqrt(n[t]) * Minv0[pos0[t], :] for t in range(T)])
+    yv0 = np.array([yhat[t][f] for (t, f) in nodes0])
+    HH = (H @ H.conj().T).real
+    b = (H @ (Minv0 @ yv0)).real
+    tau_s = np.linalg.solve(HH, b)
+    rhat = [yh.copy() for yh in yhat]
+    for t in range(T):
+        rhat[t][0] -= np.sqrt(n[t]) * tau_s[t]
+    num = 0.0
+    tr = 0.0
+    for rho in range(nT):
+        nodes, M = class_matrix(lam, n, rho)
+        Minv = np.linalg.inv(M)
+        rv = np.array([rhat[t][f] for (t, f) in nodes])
+        a = Minv @ rv
+        num += float(np.vdot(a, a).real)
+        tr += float(np.trace(Minv).real)
+    tau = np.empty(T)
+    tau[order] = tau_s
+    return dict(L=num / tr ** 2, num=num, trace=tr, tau=tau)
+
+
+def gcv_equal(kind, gen, shift, m, y, eta, W, v, sigma2):
+    """Equal sizes: tau_GCV is the vector of sample means (Pi-like matrix n Lambda(0)^-2) and the
+    per-frequency T x T inverses give num = sum_f ||Lambda(f)^-1 rhat(f)||^2, trace = sum_f tr."""
+    T = len(m)
+    mm = int(m[0])
+    n = 1 << mm
+    X = [design_points(kind, gen, shift[t], n) for t in range(T)]
+    R = task_covariance(W, v)
+    lam = lambda_blocks(kind, X, eta, R, sigma2)
+    Lam = np.zeros((n, T, T), dtype=np.complex128)
+    for t in range(T):
+        for u in range(t, T):
+            Lam[:, t, u] = lam[(t, u)]
+            Lam[:, u, t] = np.conj(lam[(t, u)])
+        Lam[:, t, t] = lam[(t, t)].real
+    ys = np.asarray(y, dtype=np.float64).reshape(T, n)
+    yhat = vdag(kind, ys.astype(np.complex128), mm)
+    tau = yhat[:, 0].real / np.sqrt(n)
+    rhat = yhat.copy()
+    rhat[:, 0] = 0.0
+    Z = np.linalg.inv(Lam)
+    a = (Z @ rhat.T[:, :, None])[:, :, 0]
+    num = float(np.sum(np.abs(a) ** 2))
+    tr = float(np.sum(np.real(np.trace(Z, axis1=1, axis2=2))))
+    return dict(L=num / tr ** 2, num=num, trace=tr, tau=tau)
+
+
 def posterior_by_class(kind, gen, shift, m, y, eta, W, v, sigma2, Xq, task_q):
     """Posterior mean / variance (Eq. 3.2) at a few queries using the per-class solver for K~^-1."""
     out = nll_by_class(kind, gen, shift, m, y, eta, W, v, sigma2, want_alpha=True)

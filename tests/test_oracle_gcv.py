@@ -1,0 +1,72 @@
+"""Pins for the GCV oracle (Eq. 3.3 second form, Eq. 3.4 second form): scale invariance, the
+closed form when K~ = sigma2 I, stationarity of the numerator at tau_GCV, sample means for equal
+sizes, and the spectral routes against the dense definition."""
+import numpy as np
+import pytest
+
+from oracle import dense, spectral
+from paper_2603_16014_gb300 import inputs
+
+
+def _setup(kind, d, m, seed):
+    p = inputs.make_problem(kind, d, m, seed=seed, eta=0.7, v=0.2, sigma2=1e-3)
+    X = dense.all_points(p.kind, p.gen, p.shift, p.m)
+    return p, X, inputs.synth_y(p, X)
+
+
+def test_gcv_scale_invariance_and_sigma_only_closed_form():
+    p, X, y = _setup("lattice", 2, (5, 4), 1)
+    g = dense.gcv(p.kind, X, y, p.eta, p.W, p.v, p.sigma2)
+    c = 7.3
+    g2 = dense.gcv(p.kind, X, y, p.eta, p.W * np.sqrt(c), p.v * c, p.sigma2 * c)
+    assert g2["L"] == pytest.approx(g["L"], rel=1e-11)
+    # R = 0: K~ = sigma2 I, tau = task sample means, L = sum (y - ybar_t)^2 / N^2
+    z = dense.gcv(p.kind, X, y, p.eta, np.zeros_like(p.W), np.zeros(p.T), 0.5)
+    offs = np.concatenate([[0], np.cumsum(p.n)])
+    means = [y[offs[t]:offs[t + 1]].mean() for t in range(p.T)]
+    ss = sum(((y[offs[t]:offs[t + 1]] - means[t]) ** 2).sum() for t in range(p.T))
+    assert np.allclose(z["tau"], means, rtol=1e-12)
+    assert z["L"] == pytest.approx(ss / p.N ** 2, rel=1e-12)
+
+
+def test_gcv_mean_minimises_numerator():
+    p, X, y = _setup("dnet", 2, (5, 3, 3), 2)
+    g = dense.gcv(p.kind, X, y, p.eta, p.W, p.v, p.sigma2)
+    R = dense.task_covariance(p.W, p.v)
+    K = dense.gram(p.kind, X, p.eta, R, p.sigma2)
+    Ki = np.linalg.inv(K)
+    E = dense.summing_matrix(p.n)
+
+    def num(tau):
+        r = y - E.T @ tau
+        return r @ Ki @ Ki @ r
+
+    h = 1e-4
+    for t in range(p.T):
+        e = np.zeros(p.T)
+        e[t] = h
+        assert abs(num(g["tau"] + e) - num(g["tau"] - e)) <= 1e-6 * num(g["tau"])
+        assert num(g["tau"] + e) > num(g["tau"])
+
+
+@pytest.mark.parametrize("kind", ["lattice", "dnet"])
+def test_gcv_equal_sizes_sample_means_and_spectral(kind):
+    p, X, y = _setup(kind, 3, (5, 5, 5), 3)
+    g = dense.gcv(p.kind, X, y, p.eta, p.W, p.v, p.sigma2)
+    means = y.reshape(p.T, -1).mean(axis=1)
+    assert np.allclose(g["tau"], means, rtol=1e-9, atol=1e-12)
+    s = spectral.gcv_equal(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2)
+    for k in ("L", "num", "trace"):
+        assert s[k] == pytest.approx(g[k], rel=1e-9), k
+    c = spectral.gcv_by_class(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2)
+    assert c["L"] == pytest.approx(g["L"], rel=1e-9)
+
+
+@pytest.mark.parametrize("kind,m", [("lattice", (6, 4, 2)), ("dnet", (5, 5, 3)), ("lattice", (3, 5, 4))])
+def test_gcv_unequal_sizes_by_class(kind, m):
+    p, X, y = _setup(kind, 2, m, 4)
+    g = dense.gcv(p.kind, X, y, p.eta, p.W, p.v, p.sigma2)
+    c = spectral.gcv_by_class(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2)
+    for k in ("L", "num", "trace"):
+        assert c[k] == pytest.approx(g[k], rel=1e-9), k
+    assert np.allclose(c["tau"], g["tau"], rtol=1e-9, atol=1e-12)
