@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the torch-composition comparison arm")
     ap.add_argument("--ncu", action="store_true",
                     help="only warm-up + K steps of the workload, no extras (for ncu captures)")
-    ap.add_argument("--workload", default="nllgrad", choices=["nllgrad", "batch512", "proposal", "nested", "posterior", "sweep"],
+    ap.add_argument("--workload", default="nllgrad", choices=["nllgrad", "batch512", "proposal", "nested", "posterior", "sweep", "gcv"],
                     help="nllgrad: the headline NLL+gradient evaluation; batch512: 512 heterogeneous fits, "
                          "Adam steps in one CUDA graph vs a plain per-fit optimiser")
     ap.add_argument("--fits", type=int, default=512)
@@ -691,6 +691,41 @@ def run_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+def run_gcv(args):
+    """GCV loss evaluations per second (no gradient) on the default digital-net fit and on the nested
+    lattice fit."""
+    import numpy as np
+    import torch
+
+    from paper_2603_16014_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    p, model, y = make_workload()
+    th = [torch.as_tensor(a, dtype=torch.float64).cuda().contiguous() for a in (p.eta, p.W, p.v, [p.sigma2])]
+    ms = _timed(lambda: model.gcv(*th), args.steps, args.warmup, flush, stream)
+    res["dnet_d8_T4_n2^16"] = {"evals_per_s": 1e3 * len(ms) / sum(ms), "ms": sum(ms) / len(ms),
+                               "L_gcv": model.gcv(*th)[0][0].item()}
+    model.close()
+    from paper_2603_16014_gb300.mtgp import MTGP
+    q = inputs.lattice_nested()
+    mq = MTGP.from_problem(q, "fp64")
+    X = mq.points().cpu().numpy().view(np.uint32)
+    offs = np.concatenate([[0], np.cumsum(q.n)])
+    yq = inputs.synth_y(q, [X[offs[t]:offs[t + 1]] for t in range(q.T)])
+    mq.set_y(torch.from_numpy(yq))
+    thq = [torch.as_tensor(a, dtype=torch.float64).cuda().contiguous() for a in (q.eta, q.W, q.v, [q.sigma2])]
+    ms = _timed(lambda: mq.gcv(*thq), max(args.steps // 5, 3), args.warmup, flush, stream)
+    res["lat_d16_T5_nested"] = {"evals_per_s": 1e3 * len(ms) / sum(ms), "ms": sum(ms) / len(ms),
+                                "L_gcv": mq.gcv(*thq)[0][0].item()}
+    line = {"metric": "GCV loss evaluations per second", "value": res["dnet_d8_T4_n2^16"]["evals_per_s"],
+            "unit": "evals/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "gcv", "l2": "flushed (256 MB write) between steps"}, "results": res}
+    print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- learned proposal
 
 def _synth_worker(job):
@@ -925,6 +960,9 @@ def main():
         return
     if args.workload == "sweep":
         run_sweep(args)
+        return
+    if args.workload == "gcv":
+        run_gcv(args)
         return
     run_ours(args, rank, world, local_rank)
 

@@ -175,6 +175,18 @@ int mtgp_nll_equal_static(int kind, int d, int T, int m, const uint32_t* gen, in
                           double* tau, int* status, cudaStream_t stream);
 
 /*
+ * GCV loss (Sec. 2.2 and 3.2, Eq. 3.3, second form) at the GCV mean (Eq. 3.4, second form):
+ *   tau solves (E K~^-2 E^T) tau = E K~^-2 y, r = y - E^T tau,
+ *   L_GCV = r^T K~^-2 r / trace(K~^-1)^2 = ||Lambda~^-1 rhat||^2 / trace(Lambda~^-1)^2.
+ * For equal sizes tau is the vector of sample means; for nested sizes E K~^-2 E^T = H H^* with H
+ * from the residue class 0 of Lambda~^-1 (Theorem FMTGP item 4).  Arguments as mtgp_nll; out
+ * (device, 3 doubles) receives [L_GCV, r^T K~^-2 r, trace(K~^-1)], tau (device, T, caller order,
+ * nullable) the GCV mean.  No gradient.  Errors as mtgp_nll.
+ */
+int mtgp_gcv(mtgp_t* h, const double* eta, const double* W, int s, const double* v, const double* sigma2,
+             double* out, double* tau, cudaStream_t stream);
+
+/*
  * Batched fits: many independent fits with equal task sizes (each fit: kind, d, T tasks of 2^m
  * points) evaluated and optimised together.  No counterpart in the paper beyond its optimisation
  * loop (Sec. 4.1 fits each model by a first-order optimiser on the MLE loss (3.3)); here every

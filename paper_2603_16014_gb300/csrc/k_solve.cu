@@ -26,7 +26,7 @@ __device__ __forceinline__ void store_spec(void* p, long long i, Vt<CPLX> v) { s
 
 struct SolveParams {
     int T, s, nT;
-    int grad, clamp, store_alpha;
+    int grad, clamp, store_alpha, gcv;
     long long n[MTGP_TMAX];
     int order[MTGP_TMAX];
     int colidx[MTGP_TMAX][MTGP_TMAX];
@@ -77,6 +77,21 @@ k_solve_equal(const void* spec, void* wgt, const double* yhat, SolveParams p, Th
             for (int u = t; u < T; ++u) mu[t][u] = load_spec<S, CPLX>(spec, p.coloff[p.colidx[t][u]] + f);
             rh[t] = (f == 0) ? czero<V>() : ld<CPLX>(yhat, p.yoff[t] + f);
         }
+        if (p.gcv) {
+            // ||Lambda(f)^-1 rhat(f)||^2 and trace Lambda(f)^-1: the gradient pass yields
+            // sum_t G_tt = trace Z - ||alpha||^2 in its third accumulator
+            double scr[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) scr[q] = 0.0;
+            solve_freq<T, CPLX>(mu, rh, sR, sig, p.clamp != 0, true, lacc, scr, w, al, true, bad);
+            double a2 = 0.0;
+#pragma unroll
+            for (int t = 0; t < T; ++t) a2 += cabs2(al[t]);
+            acc[1] += scr[1];
+            acc[2] += a2;
+            acc[3] += scr[2] + a2;
+            continue;
+        }
         solve_freq<T, CPLX>(mu, rh, sR, sig, p.clamp != 0, p.grad != 0, lacc, acc, w, al, p.store_alpha != 0, bad);
         if (p.store_alpha) {
 #pragma unroll
@@ -117,7 +132,7 @@ constexpr int kTreeCW = 8;
 constexpr int kTreeSlots = kTreeThreads / kTreeCW;
 
 struct TreeParams {
-    int T, s, grad, clamp;
+    int T, s, grad, clamp, gcv;
     long long nT;
     long long n[MTGP_TMAX];
     long long po[MTGP_TMAX][MTGP_TMAX];  // pair (t <= u) element offset in spec / wgt / S / Z
@@ -254,7 +269,7 @@ __device__ void tree_backward(const TreeParams& p, const double* Sb, double* Zb,
 template <bool CPLX, typename S>
 __global__ void __launch_bounds__(kTreeThreads)
 k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double* Zb, double* rb, double* ab,
-             double* tau_out, TreeParams p, ThetaPtrs th, double* partials, int* status) {
+             double* tau_out, TreeParams p, ThetaPtrs th, double* partials, int* status, double* Hb) {
     using V = Vt<CPLX>;
     const int T = p.T;
     const int NG = T * (T + 1) / 2;
@@ -375,13 +390,59 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
         double qd = 0.0;
         tree_forward<CPLX>(p, Sb, rb, rho, act0, slot, qd, s_part);
         tree_backward<CPLX>(p, Sb, Zb, rb, ab, rho, act0, slot, true);
+        // GCV: the class-0 columns c_t = Lambda_0^-1 e_(t,0) (rows 0..T-1 of Hb) and
+        // Lambda_0^-1 yhat_0 (row T), over the class-0 nodes (t, k nT) flattened task by task
+        long long P0 = 0, off0[MTGP_TMAX];
+        for (int t = 0; t < T; ++t) {
+            off0[t] = P0;
+            P0 += p.n[t] / nT;
+        }
+        auto save_row = [&](int row) {
+            if (!act0) return;
+            for (int t = 0; t < T; ++t)
+                for (long long k = slot; k < p.n[t] / nT; k += kTreeSlots)
+                    st<CPLX>(Hb, (long long)row * P0 + off0[t] + k, ld<CPLX>(ab, p.yoff[t] + k * nT));
+        };
+        if (p.gcv) {
+            save_row(T);
+            for (int c = 0; c < T; ++c) {
+                __syncthreads();
+                if (act0) {
+                    for (int t = 0; t < T; ++t)
+                        for (long long k = slot; k < p.n[t] / nT; k += kTreeSlots)
+                            st<CPLX>(rb, p.yoff[t] + k * nT, (t == c && k == 0) ? cfromreal<V>(1.0) : czero<V>());
+                }
+                __syncthreads();
+                tree_forward<CPLX>(p, Sb, rb, rho, act0, slot, qd, s_part);
+                tree_backward<CPLX>(p, Sb, Zb, rb, ab, rho, act0, slot, false);
+                save_row(c);
+            }
+            __syncthreads();
+        }
         if (threadIdx.x == 0) {
             double Pi[MTGP_TMAX][MTGP_TMAX], b[MTGP_TMAX];
-            for (int t = 0; t < T; ++t) {
-                b[t] = sqrt((double)p.n[t]) * creal(ld<CPLX>(ab, p.yoff[t]));
-                for (int u = 0; u < T; ++u) {
-                    double z = (t <= u) ? creal(ld<CPLX>(Zb, p.po[t][u])) : creal(ld<CPLX>(Zb, p.po[u][t]));
-                    Pi[t][u] = sqrt((double)p.n[t] * (double)p.n[u]) * z;
+            if (!p.gcv) {
+                // Pi = E K~^-1 E^T and E K~^-1 yhat from class 0 (Theorem FMTGP item 4)
+                for (int t = 0; t < T; ++t) {
+                    b[t] = sqrt((double)p.n[t]) * creal(ld<CPLX>(ab, p.yoff[t]));
+                    for (int u = 0; u < T; ++u) {
+                        double z = (t <= u) ? creal(ld<CPLX>(Zb, p.po[t][u])) : creal(ld<CPLX>(Zb, p.po[u][t]));
+                        Pi[t][u] = sqrt((double)p.n[t] * (double)p.n[u]) * z;
+                    }
+                }
+            } else {
+                // H H^* and E K~^-2 yhat with H_{t,k} = sqrt(n_t) conj(c_t[k]) (Theorem FMTGP item 4)
+                for (int t = 0; t < T; ++t) {
+                    double bt = 0.0;
+                    for (long long q = 0; q < P0; ++q)
+                        bt += creal(vmul(cconj(ld<CPLX>(Hb, (long long)t * P0 + q)), ld<CPLX>(Hb, (long long)T * P0 + q)));
+                    b[t] = sqrt((double)p.n[t]) * bt;
+                    for (int u = 0; u <= t; ++u) {
+                        double hh = 0.0;
+                        for (long long q = 0; q < P0; ++q)
+                            hh += creal(vmul(cconj(ld<CPLX>(Hb, (long long)t * P0 + q)), ld<CPLX>(Hb, (long long)u * P0 + q)));
+                        Pi[t][u] = Pi[u][t] = sqrt((double)p.n[t] * (double)p.n[u]) * hh;
+                    }
                 }
             }
             // Pi tau = b by Cholesky (Pi = E K~^-1 E^T is SPD)
@@ -432,7 +493,19 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
     }
     __syncthreads();
     tree_forward<CPLX>(p, Sb, rb, rho, act, slot, acc[1], s_part);
-    tree_backward<CPLX>(p, Sb, Zb, rb, ab, rho, act, slot, p.grad != 0);
+    tree_backward<CPLX>(p, Sb, Zb, rb, ab, rho, act, slot, p.grad != 0 || p.gcv != 0);
+
+    if (p.gcv && act) {
+        // ||Lambda~^-1 rhat||^2 and trace Lambda~^-1 over this class's nodes
+        for (int t = 0; t < T; ++t) {
+            const long long mt = p.n[t] / nT;
+            for (long long k = slot; k < mt; k += kTreeSlots) {
+                long long f = rho + k * nT;
+                acc[2] += cabs2(ld<CPLX>(ab, p.yoff[t] + f));
+                acc[3] += creal(ld<CPLX>(Zb, p.po[t][t] + f));
+            }
+        }
+    }
 
     if (p.grad && act) {
         for (int t = 0; t < T; ++t) {
@@ -482,7 +555,7 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
 // --------------------------------------------------------------------------- finalize
 
 struct FinParams {
-    int T, d, s, equal, cplx, NQ, nsolve, neta, grad;
+    int T, d, s, equal, cplx, NQ, nsolve, neta, grad, gcv;
     long long N;
     long long n0;
     int order[MTGP_TMAX];
@@ -510,9 +583,16 @@ __global__ void k_finalize(const double* partials, const double* eta_partials, c
     __syncthreads();
     if (threadIdx.x != 0) return;
     const double LOG2PI = 1.8378770664093453;
-    out[0] = 0.5 * (tot[0] + tot[1] + (double)p.N * LOG2PI);
-    out[1] = tot[1];
-    out[2] = tot[0];
+    if (p.gcv) {
+        // GCV loss ||Lambda~^-1 rhat||^2 / trace(Lambda~^-1)^2, its numerator and the trace
+        out[0] = tot[2] / (tot[3] * tot[3]);
+        out[1] = tot[2];
+        out[2] = tot[3];
+    } else {
+        out[0] = 0.5 * (tot[0] + tot[1] + (double)p.N * LOG2PI);
+        out[1] = tot[1];
+        out[2] = tot[0];
+    }
     if (tau) {
         for (int t = 0; t < p.T; ++t) {
             double tv;
@@ -571,12 +651,13 @@ static void dispatch_eq(const Handle* h, ThetaPtrs th, SolveParams sp, double* p
     }
 }
 
-void launch_solve_equal(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st) {
+void launch_solve_equal(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st, bool gcv) {
     SolveParams sp;
     sp.T = h->T;
     sp.s = th.s;
     sp.nT = 0;
-    sp.grad = grad ? 1 : 0;
+    sp.grad = (grad && !gcv) ? 1 : 0;
+    sp.gcv = gcv ? 1 : 0;
     sp.clamp = h->fp32 ? 1 : 0;
     sp.store_alpha = 1;
     for (int t = 0; t < MTGP_TMAX; ++t) {
@@ -595,11 +676,12 @@ void launch_solve_equal(const Handle* h, ThetaPtrs th, bool grad, double* partia
     }
 }
 
-void launch_solve_tree(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st) {
+void launch_solve_tree(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st, bool gcv) {
     TreeParams tp;
     tp.T = h->T;
     tp.s = th.s;
-    tp.grad = grad ? 1 : 0;
+    tp.grad = (grad && !gcv) ? 1 : 0;
+    tp.gcv = gcv ? 1 : 0;
     tp.clamp = h->fp32 ? 1 : 0;
     tp.nT = h->n[h->T - 1];
     for (int t = 0; t < MTGP_TMAX; ++t) {
@@ -611,18 +693,19 @@ void launch_solve_tree(const Handle* h, ThetaPtrs th, bool grad, double* partial
     }
     int blocks = solve_tree_blocks(h);
     if (h->fp32) {
-        if (h->cplx) k_solve_tree<true, float><<<blocks, kTreeThreads, 0, st>>>(h->spec, h->wgt, h->yhat, h->S, h->Z, h->r, h->alpha, h->tau, tp, th, partials, h->status);
-        else k_solve_tree<false, float><<<blocks, kTreeThreads, 0, st>>>(h->spec, h->wgt, h->yhat, h->S, h->Z, h->r, h->alpha, h->tau, tp, th, partials, h->status);
+        if (h->cplx) k_solve_tree<true, float><<<blocks, kTreeThreads, 0, st>>>(h->spec, h->wgt, h->yhat, h->S, h->Z, h->r, h->alpha, h->tau, tp, th, partials, h->status, h->gcv_h);
+        else k_solve_tree<false, float><<<blocks, kTreeThreads, 0, st>>>(h->spec, h->wgt, h->yhat, h->S, h->Z, h->r, h->alpha, h->tau, tp, th, partials, h->status, h->gcv_h);
     } else {
-        if (h->cplx) k_solve_tree<true, double><<<blocks, kTreeThreads, 0, st>>>(h->spec, h->wgt, h->yhat, h->S, h->Z, h->r, h->alpha, h->tau, tp, th, partials, h->status);
-        else k_solve_tree<false, double><<<blocks, kTreeThreads, 0, st>>>(h->spec, h->wgt, h->yhat, h->S, h->Z, h->r, h->alpha, h->tau, tp, th, partials, h->status);
+        if (h->cplx) k_solve_tree<true, double><<<blocks, kTreeThreads, 0, st>>>(h->spec, h->wgt, h->yhat, h->S, h->Z, h->r, h->alpha, h->tau, tp, th, partials, h->status, h->gcv_h);
+        else k_solve_tree<false, double><<<blocks, kTreeThreads, 0, st>>>(h->spec, h->wgt, h->yhat, h->S, h->Z, h->r, h->alpha, h->tau, tp, th, partials, h->status, h->gcv_h);
     }
 }
 
 void launch_finalize(const Handle* h, ThetaPtrs th, bool grad, const double* partials, int nsolve,
                      const double* eta_partials, int neta, double* out, double* tau, double* g_eta, double* g_W,
-                     double* g_v, double* g_s2, cudaStream_t st) {
+                     double* g_v, double* g_s2, cudaStream_t st, bool gcv) {
     FinParams fp;
+    fp.gcv = gcv ? 1 : 0;
     fp.T = h->T;
     fp.d = h->d;
     fp.s = th.s;

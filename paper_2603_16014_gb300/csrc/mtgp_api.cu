@@ -105,7 +105,8 @@ cudaError_t dalloc(Handle* h, T** p, size_t count) {
 
 void free_all(Handle* h) {
     void* ptrs[] = {h->gen, h->shift, h->cols_dev, h->offs_dev, h->yoffs_dev, h->twid, h->twid32, h->yhat, h->spec,
-                    h->wgt, h->S, h->Z, h->r, h->alpha, h->tau, h->partials, h->status, h->out_tmp, h->counters};
+                    h->wgt, h->S, h->Z, h->r, h->alpha, h->tau, h->partials, h->status, h->out_tmp, h->counters,
+                    h->gcv_h};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->prof) {
@@ -409,6 +410,56 @@ int mtgp_nll_grad(mtgp_t* hs, const double* eta, const double* W, int s, const d
     if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
     ThetaPtrs th{eta, W, s, v, sigma2};
     return run_nll(h, th, true, out, tau, g_eta, g_W, g_v, g_sigma2, st);
+}
+
+// GCV loss at the GCV mean: generic path (column generation, transforms, per-frequency or tree
+// solve in GCV mode, finalize)
+static int run_gcv(Handle* h, ThetaPtrs th, double* out, double* tau, cudaStream_t st) {
+    if (!h->equal && !h->gcv_h) {
+        long long P0 = 0;
+        for (int t = 0; t < h->T; ++t) P0 += h->n[t] / h->n[h->T - 1];
+        const size_t bytes = sizeof(double) * (size_t)(h->T + 1) * (size_t)P0 * (h->cplx ? 2 : 1);
+        CK(cudaMalloc(&h->gcv_h, bytes));
+        h->ws_bytes += (long long)bytes;
+    }
+    k_check_theta<<<1, 64, 0, st>>>(th, h->d, h->T, h->status);
+    mtgp_prof_begin(h, "colgen", st);
+    launch_colgen(h, th.eta, h->spec, st);
+    mtgp_prof_end(h, st);
+    mtgp_prof_begin(h, "xform_dit", st);
+    for (int g = 0; g < h->ngroups; ++g)
+        launch_transform(h, h->spec, h->fp32, h->cplx, h->group_m[g], h->offs_dev + h->group_first[g],
+                         h->group_count[g], false, st);
+    mtgp_prof_end(h, st);
+    int nsolve;
+    if (h->equal) {
+        mtgp_prof_begin(h, "solve_equal_gcv", st);
+        launch_solve_equal(h, th, false, h->partials, st, true);
+        mtgp_prof_end(h, st);
+        nsolve = solve_equal_blocks(h);
+    } else {
+        mtgp_prof_begin(h, "solve_tree_gcv", st);
+        launch_solve_tree(h, th, false, h->partials, st, true);
+        mtgp_prof_end(h, st);
+        nsolve = solve_tree_blocks(h);
+    }
+    mtgp_prof_begin(h, "finalize", st);
+    launch_finalize(h, th, false, h->partials, nsolve, nullptr, 0, out, tau, nullptr, nullptr, nullptr, nullptr, st,
+                    true);
+    mtgp_prof_end(h, st);
+    CK(cudaGetLastError());
+    return MTGP_OK;
+}
+
+int mtgp_gcv(mtgp_t* hs, const double* eta, const double* W, int s, const double* v, const double* sigma2,
+             double* out, double* tau, cudaStream_t st) {
+    if (!hs || !out) return fail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    Handle* h = &hs->h;
+    int rc = validate_theta(h, eta, W, s, v, sigma2);
+    if (rc) return rc;
+    if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
+    ThetaPtrs th{eta, W, s, v, sigma2};
+    return run_gcv(h, th, out, tau, st);
 }
 
 int mtgp_posterior(mtgp_t* hs, const double* eta, const double* W, int s, const double* v, const double* sigma2,

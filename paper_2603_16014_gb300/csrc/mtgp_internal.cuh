@@ -185,12 +185,16 @@ void launch_twiddles(Handle* h, cudaStream_t st);
 
 // k_solve.cu
 int solve_equal_blocks(const Handle* h);
-void launch_solve_equal(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st);
-void launch_solve_tree(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st);
+// gcv = true: the GCV loss instead of the MLE loss (no gradient); partial columns 2 and 3 then hold
+// ||Lambda^-1 rhat||^2 and trace(Lambda^-1)
+void launch_solve_equal(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st,
+                        bool gcv = false);
+void launch_solve_tree(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st,
+                       bool gcv = false);
 int solve_tree_blocks(const Handle* h);
 void launch_finalize(const Handle* h, ThetaPtrs th, bool grad, const double* partials, int nsolve,
                      const double* eta_partials, int neta, double* out, double* tau, double* g_eta,
-                     double* g_W, double* g_v, double* g_s2, cudaStream_t st);
+                     double* g_W, double* g_v, double* g_s2, cudaStream_t st, bool gcv = false);
 
 // k_fused.cu (equal sizes)
 bool fused_supported(const Handle* h);
@@ -270,6 +274,7 @@ struct Handle {
     long long partials_len;
     int* status;
     double* out_tmp;     // NLL outputs of calls that only need the solve (posterior)
+    double* gcv_h;       // GCV, unequal sizes: class-0 columns of Lambda^-1 (T + 1 rows, on first use)
     unsigned* counters;  // last-block election counters of the fused kernels (reset by the last block)
     struct Prof* prof;   // kernel timing log (host side)
     long long ws_bytes;

@@ -103,6 +103,16 @@ class MTGP:
                                   _ptr(ge), _ptr(gW), _ptr(gv), _ptr(gs), _stream(stream)), "mtgp_nll_grad")
         return outs
 
+    def gcv(self, eta, W, v, sigma2, stream=None):
+        """Returns (out, tau): out = [L_GCV, r^T K~^-2 r, trace K~^-1] (device float64), tau (T,) at
+        the GCV mean."""
+        eta, W, v, s2 = self._theta(eta, W, v, sigma2)
+        out = torch.empty(3, dtype=torch.float64, device="cuda")
+        tau = torch.empty(self.T, dtype=torch.float64, device="cuda")
+        check(lib().mtgp_gcv(self._h, _ptr(eta), _ptr(W), W.shape[1], _ptr(v), _ptr(s2), _ptr(out), _ptr(tau),
+                             _stream(stream)), "mtgp_gcv")
+        return out, tau
+
     def posterior(self, eta, W, v, sigma2, xq, task, variance=True, stream=None):
         eta, W, v, s2 = self._theta(eta, W, v, sigma2)
         xq = _dev(xq).reshape(-1, self.d)
