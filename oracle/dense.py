@@ -178,3 +178,18 @@ def posterior(kind, X_tasks, y, eta, W, v, sigma2, Xq, task_q):
     prior = np.array([R[task_q[i], task_q[i]] * product_kernel(kind, Xq[i], Xq[i], eta) for i in range(nq)])
     var = prior - np.einsum("ij,ji->i", kq, Kinv_kq)
     return mean, var, prior
+
+
+def cubature(kind, X_tasks, y, eta, W, v, sigma2, gamma=1.0):
+    """Multitask Bayesian cubature (Sec. 3.5, multitask cubature theorem) for the task integrals
+    mu_t = int f(t, x) dx, with int Q(x, x') dx' = gamma: at tau = tau_MLE,
+        mu_hat = tau + gamma R E K~^-1 (y - E^T tau),   Sigma = gamma R - gamma^2 R Pi R,
+    Pi = E K~^-1 E^T, written out with dense solves.  Returns (mu_hat, Sigma, tau)."""
+    out = nll(kind, X_tasks, y, eta, W, v, sigma2)
+    R = task_covariance(W, v)
+    n = [len(X) for X in X_tasks]
+    E = summing_matrix(n)
+    tau = out["tau"]
+    mu = tau + gamma * R @ (E @ out["alpha"])
+    Sigma = gamma * R - gamma ** 2 * R @ out["Pi"] @ R
+    return mu, Sigma, tau
