@@ -175,6 +175,18 @@ int mtgp_nll_equal_static(int kind, int d, int T, int m, const uint32_t* gen, in
                           double* tau, int* status, cudaStream_t stream);
 
 /*
+ * Multitask Bayesian cubature (Sec. 3.5, multitask cubature theorem) for the task integrals
+ * mu_t = int f(t, x) dx under the fitted MTGP at the MLE mean.  The product kernels of Eq. 2.4 with
+ * the SI or DSI factors integrate to gamma = 1 in each argument, so
+ *   mu_hat = tau + R E K~^-1 (y - E^T tau)   (= tau_MLE up to rounding),
+ *   Sigma  = R - R Pi R,  Pi = E K~^-1 E^T = n Lambda(0)^-1 (equal sizes) or from residue class 0.
+ * mu (device, T) and Sigma (device, T x T row-major) in caller task order; a weighted combination
+ * chi^T mu has mean chi^T mu_hat and variance chi^T Sigma chi.  Arguments and errors as mtgp_nll.
+ */
+int mtgp_cubature(mtgp_t* h, const double* eta, const double* W, int s, const double* v, const double* sigma2,
+                  double* mu, double* Sigma, cudaStream_t stream);
+
+/*
  * GCV loss (Sec. 2.2 and 3.2, Eq. 3.3, second form) at the GCV mean (Eq. 3.4, second form):
  *   tau solves (E K~^-2 E^T) tau = E K~^-2 y, r = y - E^T tau,
  *   L_GCV = r^T K~^-2 r / trace(K~^-1)^2 = ||Lambda~^-1 rhat||^2 / trace(Lambda~^-1)^2.

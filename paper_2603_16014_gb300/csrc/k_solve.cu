@@ -133,6 +133,7 @@ constexpr int kTreeSlots = kTreeThreads / kTreeCW;
 
 struct TreeParams {
     int T, s, grad, clamp, gcv;
+    double* pi_out;  // when set: Pi = E K~^-1 E^T (sorted order, T x T) from class 0
     long long nT;
     long long n[MTGP_TMAX];
     long long po[MTGP_TMAX][MTGP_TMAX];  // pair (t <= u) element offset in spec / wgt / S / Z
@@ -445,6 +446,9 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
                     }
                 }
             }
+            if (p.pi_out && !p.gcv)
+                for (int t = 0; t < T; ++t)
+                    for (int u = 0; u < T; ++u) p.pi_out[t * T + u] = Pi[t][u];
             // Pi tau = b by Cholesky (Pi = E K~^-1 E^T is SPD)
             for (int k = 0; k < T; ++k) {
                 double dk = Pi[k][k];
@@ -682,6 +686,7 @@ void launch_solve_tree(const Handle* h, ThetaPtrs th, bool grad, double* partial
     tp.s = th.s;
     tp.grad = (grad && !gcv) ? 1 : 0;
     tp.gcv = gcv ? 1 : 0;
+    tp.pi_out = h->pi_buf;
     tp.clamp = h->fp32 ? 1 : 0;
     tp.nT = h->n[h->T - 1];
     for (int t = 0; t < MTGP_TMAX; ++t) {

@@ -94,6 +94,93 @@ __global__ void k_check_y(const double* y, long long N, int* status) {
         }
 }
 
+// Multitask Bayesian cubature (Sec. 3.5, multitask cubature theorem, gamma = 1 for the product kernels
+// of Eq. 2.4): mu = tau + R E K~^-1 (y - E^T tau) with (E K~^-1 r)_t = sqrt(n_t) alpha_t(0), and
+// Sigma = R - R Pi R, Pi = E K~^-1 E^T = n Lambda(0)^-1 (equal sizes) or from the tree solver.
+struct CubParams {
+    int T, s, equal, cplx, fp32, clamp;
+    long long n[MTGP_TMAX], yoff[MTGP_TMAX];
+    int order[MTGP_TMAX], rank[MTGP_TMAX];
+    int colidx[MTGP_TMAX][MTGP_TMAX];
+    long long coloff[MTGP_MAX_COLS];
+};
+
+__global__ void k_cubature(CubParams p, ThetaPtrs th, const void* spec, const double* alpha, const double* tau_sorted,
+                           const double* pi_sorted, double* mu, double* Sigma, int* status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int T = p.T;
+    double R[MTGP_TMAX][MTGP_TMAX], Pi[MTGP_TMAX][MTGP_TMAX];  // caller order
+    for (int t = 0; t < T; ++t)
+        for (int u = 0; u < T; ++u) {
+            double r = 0.0;
+            for (int k = 0; k < th.s; ++k) r += th.W[t * th.s + k] * th.W[u * th.s + k];
+            R[t][u] = r + (t == u ? th.v[t] : 0.0);
+        }
+    if (p.equal) {
+        // Lambda(0) in sorted order from the transformed first columns at frequency 0
+        double L[MTGP_TMAX][MTGP_TMAX];
+        const double sig = th.sigma2[0];
+        for (int t = 0; t < T; ++t)
+            for (int u = t; u < T; ++u) {
+                const long long e = p.coloff[p.colidx[t][u]];
+                double mu0;
+                if (p.fp32) mu0 = p.cplx ? (double)((const float*)spec)[2 * e] : (double)((const float*)spec)[e];
+                else mu0 = p.cplx ? ((const double*)spec)[2 * e] : ((const double*)spec)[e];
+                if (t == u && p.clamp && mu0 < 0.0) mu0 = 0.0;
+                const double v = R[p.order[t]][p.order[u]] * mu0 + (t == u ? sig : 0.0);
+                L[t][u] = L[u][t] = v;
+            }
+        // Pi = n Lambda(0)^-1 by Cholesky
+        for (int k = 0; k < T; ++k) {
+            double dk = L[k][k];
+            for (int j = 0; j < k; ++j) dk -= L[k][j] * L[k][j];
+            if (!(dk > 0.0)) {
+                set_status(status, ST_NOT_PD);
+                dk = 1.0;
+            }
+            dk = sqrt(dk);
+            L[k][k] = dk;
+            for (int i = k + 1; i < T; ++i) {
+                double a = L[i][k];
+                for (int j = 0; j < k; ++j) a -= L[i][j] * L[k][j];
+                L[i][k] = a / dk;
+            }
+        }
+        for (int c = 0; c < T; ++c) {
+            double x[MTGP_TMAX];
+            for (int k = 0; k < T; ++k) {
+                double a = (k == c) ? 1.0 : 0.0;
+                for (int j = 0; j < k; ++j) a -= L[k][j] * x[j];
+                x[k] = a / L[k][k];
+            }
+            for (int k = T - 1; k >= 0; --k) {
+                double a = x[k];
+                for (int i = k + 1; i < T; ++i) a -= L[i][k] * x[i];
+                x[k] = a / L[k][k];
+            }
+            for (int k = 0; k < T; ++k) Pi[p.order[k]][p.order[c]] = (double)p.n[0] * x[k];
+        }
+    } else {
+        for (int t = 0; t < T; ++t)
+            for (int u = 0; u < T; ++u) Pi[p.order[t]][p.order[u]] = pi_sorted[t * T + u];
+    }
+    for (int t = 0; t < T; ++t) {
+        double m = tau_sorted[p.rank[t]];
+        for (int u = 0; u < T; ++u) {
+            const int su = p.rank[u];
+            const double a0 = p.cplx ? alpha[2 * p.yoff[su]] : alpha[p.yoff[su]];
+            m += R[t][u] * sqrt((double)p.n[su]) * a0;
+        }
+        mu[t] = m;
+        for (int u = 0; u < T; ++u) {
+            double rpr = 0.0;
+            for (int a = 0; a < T; ++a)
+                for (int b = 0; b < T; ++b) rpr += R[t][a] * Pi[a][b] * R[b][u];
+            Sigma[t * T + u] = R[t][u] - rpr;
+        }
+    }
+}
+
 template <typename T>
 cudaError_t dalloc(Handle* h, T** p, size_t count) {
     size_t bytes = count * sizeof(T);
@@ -106,7 +193,7 @@ cudaError_t dalloc(Handle* h, T** p, size_t count) {
 void free_all(Handle* h) {
     void* ptrs[] = {h->gen, h->shift, h->cols_dev, h->offs_dev, h->yoffs_dev, h->twid, h->twid32, h->yhat, h->spec,
                     h->wgt, h->S, h->Z, h->r, h->alpha, h->tau, h->partials, h->status, h->out_tmp, h->counters,
-                    h->gcv_h};
+                    h->gcv_h, h->pi_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->prof) {
@@ -447,6 +534,42 @@ static int run_gcv(Handle* h, ThetaPtrs th, double* out, double* tau, cudaStream
     launch_finalize(h, th, false, h->partials, nsolve, nullptr, 0, out, tau, nullptr, nullptr, nullptr, nullptr, st,
                     true);
     mtgp_prof_end(h, st);
+    CK(cudaGetLastError());
+    return MTGP_OK;
+}
+
+int mtgp_cubature(mtgp_t* hs, const double* eta, const double* W, int s, const double* v, const double* sigma2,
+                  double* mu, double* Sigma, cudaStream_t st) {
+    if (!hs || !mu || !Sigma) return fail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    Handle* h = &hs->h;
+    int rc = validate_theta(h, eta, W, s, v, sigma2);
+    if (rc) return rc;
+    if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
+    if (!h->equal && !h->pi_buf) {
+        CK(cudaMalloc(&h->pi_buf, sizeof(double) * MTGP_TMAX * MTGP_TMAX));
+        h->ws_bytes += (long long)sizeof(double) * MTGP_TMAX * MTGP_TMAX;
+    }
+    ThetaPtrs th{eta, W, s, v, sigma2};
+    // the MLE solve leaves alpha, tau (sorted), the transformed spectra (equal sizes) or Pi (nested)
+    rc = run_nll(h, th, false, h->out_tmp, nullptr, nullptr, nullptr, nullptr, nullptr, st, true);
+    if (rc) return rc;
+    CubParams cp;
+    std::memset(&cp, 0, sizeof(cp));
+    cp.T = h->T;
+    cp.s = s;
+    cp.equal = h->equal ? 1 : 0;
+    cp.cplx = h->cplx ? 1 : 0;
+    cp.fp32 = h->fp32 ? 1 : 0;
+    cp.clamp = h->fp32 ? 1 : 0;
+    for (int t = 0; t < MTGP_TMAX; ++t) {
+        cp.n[t] = t < h->T ? h->n[t] : 1;
+        cp.yoff[t] = t < h->T ? h->yoff[t] : 0;
+        cp.order[t] = t < h->T ? h->order[t] : 0;
+        cp.rank[t] = t < h->T ? h->rank[t] : 0;
+        for (int u = 0; u < MTGP_TMAX; ++u) cp.colidx[t][u] = (t < h->T && u < h->T && t <= u) ? h->col_of[t][u] : 0;
+    }
+    for (int c = 0; c < MTGP_MAX_COLS; ++c) cp.coloff[c] = c < h->ncols ? h->cols[c].off : 0;
+    k_cubature<<<1, 32, 0, st>>>(cp, th, h->spec, h->alpha, h->tau, h->pi_buf, mu, Sigma, h->status);
     CK(cudaGetLastError());
     return MTGP_OK;
 }

@@ -275,6 +275,7 @@ struct Handle {
     int* status;
     double* out_tmp;     // NLL outputs of calls that only need the solve (posterior)
     double* gcv_h;       // GCV, unequal sizes: class-0 columns of Lambda^-1 (T + 1 rows, on first use)
+    double* pi_buf;      // cubature, unequal sizes: Pi = E K~^-1 E^T from the tree solver (T x T, on first use)
     unsigned* counters;  // last-block election counters of the fused kernels (reset by the last block)
     struct Prof* prof;   // kernel timing log (host side)
     long long ws_bytes;

@@ -113,6 +113,15 @@ class MTGP:
                              _stream(stream)), "mtgp_gcv")
         return out, tau
 
+    def cubature(self, eta, W, v, sigma2, stream=None):
+        """Returns (mu_hat (T,), Sigma (T, T)): posterior mean and covariance of the task integrals."""
+        eta, W, v, s2 = self._theta(eta, W, v, sigma2)
+        mu = torch.empty(self.T, dtype=torch.float64, device="cuda")
+        Sigma = torch.empty((self.T, self.T), dtype=torch.float64, device="cuda")
+        check(lib().mtgp_cubature(self._h, _ptr(eta), _ptr(W), W.shape[1], _ptr(v), _ptr(s2), _ptr(mu), _ptr(Sigma),
+                                  _stream(stream)), "mtgp_cubature")
+        return mu, Sigma
+
     def posterior(self, eta, W, v, sigma2, xq, task, variance=True, stream=None):
         eta, W, v, s2 = self._theta(eta, W, v, sigma2)
         xq = _dev(xq).reshape(-1, self.d)
