@@ -88,30 +88,13 @@ def gcv(kind, X_tasks, y, eta, W, v, sigma2):
     return dict(L=num / tr ** 2, num=num, trace=tr, tau=tau)
 
 
-def nll_grad(kind, X_tasks, y, eta, W, v, sigma2):
-    """Analytic gradient of L (Eq. 3.3) w.r.t. eta (d), W (T x s), v (T), sigma2, at the optimal tau.
-
-    dL/dtheta = tr(K~^-1 dK~/dtheta) - a^T (dK~/dtheta) a, each dK~ written out densely:
-      dK~/d eta_j   = R_{tt'} K(x_j, x'_j) prod_{l != j} (1 + eta_l K(x_l, x'_l))
-      dK~/d W_{ts}  = (dR/dW_{ts})_{tt'} Q,   dR/dW_{ts} = e_t W_{:,s}^T + W_{:,s} e_t^T
-      dK~/d v_t     = (e_t e_t^T)_{tt'} Q
-      dK~/d sigma2  = I
-    Returns (out_dict_of_nll, g_eta, g_W, g_v, g_sigma2) for L (the NLL gradient is half of it).
-    """
-    out = nll(kind, X_tasks, y, eta, W, v, sigma2)
-    R = task_covariance(W, v)
-    K = gram(kind, X_tasks, eta, R, sigma2)
-    Kinv = np.linalg.inv(K)
-    Kinv = 0.5 * (Kinv + Kinv.T)
-    a = out["alpha"]
+def _param_contractions(kind, X_tasks, eta, W, R, K, contract):
+    """contract(dK~/dtheta) for every parameter: eta (d), W (T x s), v (T), sigma2, with the dense
+    derivatives of K~ written out (see nll_grad)."""
     T = len(X_tasks)
     n = [len(X) for X in X_tasks]
     off = np.concatenate([[0], np.cumsum(n)])
     d = len(eta)
-
-    def contract(dK):
-        return float(np.sum(Kinv * dK) - a @ dK @ a)
-
     # univariate kernel blocks per dimension
     K1 = [[None] * T for _ in range(T)]
     for t in range(T):
@@ -151,6 +134,57 @@ def nll_grad(kind, X_tasks, y, eta, W, v, sigma2):
         dR[t, t] = 1.0
         g_v[t] = contract(blockwise(dR))
     g_s2 = contract(np.eye(K.shape[0]))
+    return g_eta, g_W, g_v, g_s2
+
+
+def gcv_grad(kind, X_tasks, y, eta, W, v, sigma2):
+    """Analytic gradient of the GCV loss (Eq. 3.3, second form) at the GCV mean (fixed by the envelope
+    theorem: tau_GCV minimises the numerator, the trace does not depend on tau).  With a = K~^-1 r,
+    b = K~^-1 a, A = a^T a, B = trace K~^-1:
+        dL = dA / B^2 - 2 A dB / B^3,  dA = -2 a^T dK~ b,  dB = -trace(K~^-2 dK~),
+    i.e. dL = sum(G * dK~) with G = -(a b^T + b a^T) / B^2 + (2 A / B^3) K~^-2.
+    Returns (gcv dict, g_eta, g_W, g_v, g_sigma2)."""
+    out = gcv(kind, X_tasks, y, eta, W, v, sigma2)
+    R = task_covariance(W, v)
+    K = gram(kind, X_tasks, eta, R, sigma2)
+    n = [len(X) for X in X_tasks]
+    E = summing_matrix(n)
+    Kinv = np.linalg.inv(K)
+    Kinv = 0.5 * (Kinv + Kinv.T)
+    r = y - E.T @ out["tau"]
+    a = Kinv @ r
+    b = Kinv @ a
+    A, B = float(a @ a), float(np.trace(Kinv))
+    G = -(np.outer(a, b) + np.outer(b, a)) / B ** 2 + (2.0 * A / B ** 3) * (Kinv @ Kinv)
+
+    def contract(dK):
+        return float(np.sum(G * dK))
+
+    g_eta, g_W, g_v, g_s2 = _param_contractions(kind, X_tasks, eta, W, R, K, contract)
+    return out, g_eta, g_W, g_v, g_s2
+
+
+def nll_grad(kind, X_tasks, y, eta, W, v, sigma2):
+    """Analytic gradient of L (Eq. 3.3) w.r.t. eta (d), W (T x s), v (T), sigma2, at the optimal tau.
+
+    dL/dtheta = tr(K~^-1 dK~/dtheta) - a^T (dK~/dtheta) a, each dK~ written out densely:
+      dK~/d eta_j   = R_{tt'} K(x_j, x'_j) prod_{l != j} (1 + eta_l K(x_l, x'_l))
+      dK~/d W_{ts}  = (dR/dW_{ts})_{tt'} Q,   dR/dW_{ts} = e_t W_{:,s}^T + W_{:,s} e_t^T
+      dK~/d v_t     = (e_t e_t^T)_{tt'} Q
+      dK~/d sigma2  = I
+    Returns (out_dict_of_nll, g_eta, g_W, g_v, g_sigma2) for L (the NLL gradient is half of it).
+    """
+    out = nll(kind, X_tasks, y, eta, W, v, sigma2)
+    R = task_covariance(W, v)
+    K = gram(kind, X_tasks, eta, R, sigma2)
+    Kinv = np.linalg.inv(K)
+    Kinv = 0.5 * (Kinv + Kinv.T)
+    a = out["alpha"]
+
+    def contract(dK):
+        return float(np.sum(Kinv * dK) - a @ dK @ a)
+
+    g_eta, g_W, g_v, g_s2 = _param_contractions(kind, X_tasks, eta, W, R, K, contract)
     return out, g_eta, g_W, g_v, g_s2
 
 

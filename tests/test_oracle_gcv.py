@@ -70,3 +70,32 @@ def test_gcv_unequal_sizes_by_class(kind, m):
     for k in ("L", "num", "trace"):
         assert c[k] == pytest.approx(g[k], rel=1e-9), k
     assert np.allclose(c["tau"], g["tau"], rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind,m", [("lattice", (4, 4)), ("dnet", (4, 3, 3))])
+def test_gcv_gradient_matches_central_differences(kind, m):
+    p, X, y = _setup(kind, 2, m, 5)
+    out, ge, gW, gv, gs = dense.gcv_grad(p.kind, X, y, p.eta, p.W, p.v, p.sigma2)
+
+    def L(eta, W, v, s2):
+        return dense.gcv(p.kind, X, y, eta, W, v, s2)["L"]
+
+    h = 1e-4          # relative step: truncation ~1e-8, roundoff eps L / (h theta) well below 1e-5
+    for j in range(p.d):
+        e = np.zeros(p.d)
+        e[j] = h * p.eta[j]
+        fd = (L(p.eta + e, p.W, p.v, p.sigma2) - L(p.eta - e, p.W, p.v, p.sigma2)) / (2 * e[j])
+        assert fd == pytest.approx(ge[j], rel=1e-5, abs=1e-9 * out["L"])
+    for (t, k) in [(0, 0), (p.T - 1, 1)]:
+        E = np.zeros_like(p.W)
+        E[t, k] = h
+        fd = (L(p.eta, p.W + E, p.v, p.sigma2) - L(p.eta, p.W - E, p.v, p.sigma2)) / (2 * h)
+        assert fd == pytest.approx(gW[t, k], rel=1e-5, abs=1e-9 * out["L"])
+    for t in range(p.T):
+        e = np.zeros(p.T)
+        e[t] = h * p.v[t]
+        fd = (L(p.eta, p.W, p.v + e, p.sigma2) - L(p.eta, p.W, p.v - e, p.sigma2)) / (2 * e[t])
+        assert fd == pytest.approx(gv[t], rel=1e-5, abs=1e-9 * out["L"])
+    hs = h * p.sigma2
+    fd = (L(p.eta, p.W, p.v, p.sigma2 + hs) - L(p.eta, p.W, p.v, p.sigma2 - hs)) / (2 * hs)
+    assert fd == pytest.approx(gs, rel=1e-5, abs=1e-9 * out["L"])
