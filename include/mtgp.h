@@ -199,6 +199,18 @@ int mtgp_gcv(mtgp_t* h, const double* eta, const double* W, int s, const double*
              double* out, double* tau, cudaStream_t stream);
 
 /*
+ * GCV loss and its gradient with respect to (eta, W, v, sigma2), equal task sizes (others:
+ * MTGP_ERR_UNSUPPORTED).  tau_GCV minimises the numerator and the trace does not depend on tau, so
+ * the gradient holds tau fixed.  With alpha = Lambda^-1 rhat, beta = Lambda^-1 alpha, A = ||alpha||^2
+ * and B = trace Lambda^-1: dL = trace(G dLambda), G = -(alpha beta^H + beta alpha^H) / B^2 +
+ * (2A / B^3) Lambda^-2, evaluated per frequency after the value pass.  Outputs as mtgp_gcv plus the
+ * gradient arrays of mtgp_nll_grad (of L_GCV itself, not halved).
+ */
+int mtgp_gcv_grad(mtgp_t* h, const double* eta, const double* W, int s, const double* v, const double* sigma2,
+                  double* out, double* tau, double* g_eta, double* g_W, double* g_v, double* g_sigma2,
+                  cudaStream_t stream);
+
+/*
  * Batched fits: many independent fits with equal task sizes (each fit: kind, d, T tasks of 2^m
  * points) evaluated and optimised together.  No counterpart in the paper beyond its optimisation
  * loop (Sec. 4.1 fits each model by a first-order optimiser on the MLE loss (3.3)); here every

@@ -48,6 +48,7 @@ _SIGS = {
     "mtgp_batch_autotune": (_i, [_p, _i, _p, _p]),
     "mtgp_gcv": (_i, [_p, _p, _p, _i, _p, _p, _p, _p, _p]),
     "mtgp_cubature": (_i, [_p, _p, _p, _i, _p, _p, _p, _p, _p]),
+    "mtgp_gcv_grad": (_i, [_p, _p, _p, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p]),
     "mtgp_batch_features": (_i, [_p, _p, _p]),
     "mtgp_batch_targets": (_i, [_p, _p, _p, _p]),
     "mtgp_batch_set_theta_proposal": (_i, [_p, _p, _p]),

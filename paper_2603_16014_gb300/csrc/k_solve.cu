@@ -26,7 +26,8 @@ __device__ __forceinline__ void store_spec(void* p, long long i, Vt<CPLX> v) { s
 
 struct SolveParams {
     int T, s, nT;
-    int grad, clamp, store_alpha, gcv;
+    int grad, clamp, store_alpha, gcv;  // gcv: 1 loss value, 2 gradient (needs gcv_ab)
+    const double* gcv_ab;               // [A, B] of the GCV loss (device), for gcv = 2
     long long n[MTGP_TMAX];
     int order[MTGP_TMAX];
     int colidx[MTGP_TMAX][MTGP_TMAX];
@@ -47,6 +48,86 @@ __device__ void load_R(double* sR, const SolveParams& p, const ThetaPtrs& th) {
 }
 
 constexpr int kEqThreads = 128;
+
+// GCV gradient at one frequency: with Z = Lambda(f)^-1, alpha = Z rhat, beta = Z alpha and the totals
+// A = sum ||alpha||^2, B = sum trace Z (c1 = 1 / B^2, c2 = 2 A / B^3), the loss differential is
+// trace(G dLambda) with G = -c1 (alpha beta^H + beta alpha^H) + c2 Z^2; G is contracted and turned
+// into adjoint weights exactly as the MLE path does with G = Z - alpha alpha^H.
+template <int T, bool CPLX>
+__device__ void gcv_grad_freq(Vt<CPLX> (&mu)[T][T], const Vt<CPLX> (&rh)[T], const double* sR, double sig, bool clamp,
+                              double c1, double c2, double* acc, Vt<CPLX> (&w)[T][T], int& bad) {
+    using V = Vt<CPLX>;
+    double mu0 = creal(mu[0][0]);
+    double ind0 = 1.0;
+    if (clamp && mu0 < 0.0) {
+        mu0 = 0.0;
+        ind0 = 0.0;
+    }
+    V S[T][T], L[T][T];
+    double D[T], iD[T];
+    for (int i = 0; i < T; ++i) {
+        D[i] = sR[i * T + i] * mu0 + sig;
+        for (int j = 0; j < i; ++j) S[i][j] = vscale(cconj(mu[j][i]), sR[j * T + i]);
+    }
+    for (int k = 0; k < T; ++k) {
+        if (!(D[k] > 0.0) || !isfinite(D[k])) {
+            bad = 1;
+            D[k] = 1.0;
+        }
+        iD[k] = 1.0 / D[k];
+        for (int i = k + 1; i < T; ++i) L[i][k] = vscale(S[i][k], iD[k]);
+        for (int i = k + 1; i < T; ++i) {
+            D[i] -= creal(vmul(L[i][k], cconj(S[i][k])));
+            for (int j = k + 1; j < i; ++j) S[i][j] = vsub(S[i][j], vmul(L[i][k], cconj(S[j][k])));
+        }
+    }
+    // Z by columns: L D L^H z = e_c
+    V Z[T][T];
+    for (int c = 0; c < T; ++c) {
+        V x[T];
+        for (int k = 0; k < T; ++k) {
+            V r = (k == c) ? cfromreal<V>(1.0) : czero<V>();
+            for (int j = 0; j < k; ++j) r = vsub(r, vmul(L[k][j], x[j]));
+            x[k] = r;
+        }
+        for (int k = 0; k < T; ++k) x[k] = vscale(x[k], iD[k]);
+        for (int k = T - 1; k >= 0; --k)
+            for (int i = k + 1; i < T; ++i) x[k] = vsub(x[k], vmul(cconj(L[i][k]), x[i]));
+        for (int k = 0; k < T; ++k) Z[k][c] = x[k];
+    }
+    V al[T], be[T];
+    for (int i = 0; i < T; ++i) {
+        V a = czero<V>();
+        for (int k = 0; k < T; ++k) a = vadd(a, vmul(Z[i][k], rh[k]));
+        al[i] = a;
+    }
+    for (int i = 0; i < T; ++i) {
+        V b = czero<V>();
+        for (int k = 0; k < T; ++k) b = vadd(b, vmul(Z[i][k], al[k]));
+        be[i] = b;
+    }
+    double wdiag = 0.0;
+    int q = 3;
+    for (int t = 0; t < T; ++t) {
+        for (int uu = t; uu < T; ++uu) {
+            V z2 = czero<V>();
+            for (int k = 0; k < T; ++k) z2 = vadd(z2, vmul(Z[uu][k], Z[k][t]));
+            const V ga = vadd(vmul(al[uu], cconj(be[t])), vmul(be[uu], cconj(al[t])));
+            const V g = vsub(vscale(z2, c2), vscale(ga, c1));
+            if (uu == t) {
+                const double gd = creal(g);
+                acc[2] += gd;
+                acc[q] = fma(gd, mu0, acc[q]);
+                wdiag = fma(sR[t * T + t], gd, wdiag);
+            } else {
+                acc[q] += creal(vmul(g, mu[t][uu]));
+                w[t][uu] = vscale(g, 2.0 * sR[t * T + uu]);
+            }
+            ++q;
+        }
+    }
+    w[0][0] = cfromreal<V>(wdiag * ind0);
+}
 
 template <int T, bool CPLX, typename S>
 __global__ void __launch_bounds__(kEqThreads)
@@ -76,6 +157,16 @@ k_solve_equal(const void* spec, void* wgt, const double* yhat, SolveParams p, Th
 #pragma unroll
             for (int u = t; u < T; ++u) mu[t][u] = load_spec<S, CPLX>(spec, p.coloff[p.colidx[t][u]] + f);
             rh[t] = (f == 0) ? czero<V>() : ld<CPLX>(yhat, p.yoff[t] + f);
+        }
+        if (p.gcv == 2) {
+            const double A = p.gcv_ab[0], B = p.gcv_ab[1];
+            gcv_grad_freq<T, CPLX>(mu, rh, sR, sig, p.clamp != 0, 1.0 / (B * B), 2.0 * A / (B * B * B), acc, w, bad);
+#pragma unroll
+            for (int t = 0; t < T; ++t)
+#pragma unroll
+                for (int u = t; u < T; ++u)
+                    if (u != t || t == 0) store_spec<S, CPLX>(wgt, p.coloff[p.colidx[t][u]] + f, w[t][u]);
+            continue;
         }
         if (p.gcv) {
             // ||Lambda(f)^-1 rhat(f)||^2 and trace Lambda(f)^-1: the gradient pass yields
@@ -587,7 +678,9 @@ __global__ void k_finalize(const double* partials, const double* eta_partials, c
     __syncthreads();
     if (threadIdx.x != 0) return;
     const double LOG2PI = 1.8378770664093453;
-    if (p.gcv) {
+    if (p.gcv == 2) {
+        // GCV gradient pass: the loss was written by the value pass
+    } else if (p.gcv) {
         // GCV loss ||Lambda~^-1 rhat||^2 / trace(Lambda~^-1)^2, its numerator and the trace
         out[0] = tot[2] / (tot[3] * tot[3]);
         out[1] = tot[2];
@@ -607,8 +700,10 @@ __global__ void k_finalize(const double* partials, const double* eta_partials, c
     }
     if (!p.grad) return;
     const int T = p.T;
-    g_s2[0] = 0.5 * tot[2];
-    for (int j = 0; j < p.d; ++j) g_eta[j] = 0.5 * etot[j];
+    // MLE: gradients of NLL = L / 2; GCV: gradients of the loss itself
+    const double sc = (p.gcv == 2) ? 2.0 : 1.0;
+    g_s2[0] = 0.5 * sc * tot[2];
+    for (int j = 0; j < p.d; ++j) g_eta[j] = 0.5 * sc * etot[j];
     for (int tc = 0; tc < T; ++tc) {
         int t = p.rank[tc];
         for (int k = 0; k < p.s; ++k) {
@@ -618,9 +713,9 @@ __global__ void k_finalize(const double* partials, const double* eta_partials, c
                 double G = (t <= u) ? tot[3 + gidx(t, u, T)] : tot[3 + gidx(u, t, T)];
                 g += G * th.W[uc * p.s + k];
             }
-            g_W[tc * p.s + k] = g;
+            g_W[tc * p.s + k] = sc * g;
         }
-        g_v[tc] = 0.5 * tot[3 + gidx(t, t, T)];
+        g_v[tc] = 0.5 * sc * tot[3 + gidx(t, t, T)];
     }
 }
 
@@ -655,13 +750,15 @@ static void dispatch_eq(const Handle* h, ThetaPtrs th, SolveParams sp, double* p
     }
 }
 
-void launch_solve_equal(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st, bool gcv) {
+void launch_solve_equal(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st, int gcv,
+                        const double* gcv_ab) {
     SolveParams sp;
     sp.T = h->T;
     sp.s = th.s;
     sp.nT = 0;
     sp.grad = (grad && !gcv) ? 1 : 0;
-    sp.gcv = gcv ? 1 : 0;
+    sp.gcv = gcv;
+    sp.gcv_ab = gcv_ab;
     sp.clamp = h->fp32 ? 1 : 0;
     sp.store_alpha = 1;
     for (int t = 0; t < MTGP_TMAX; ++t) {
@@ -708,9 +805,9 @@ void launch_solve_tree(const Handle* h, ThetaPtrs th, bool grad, double* partial
 
 void launch_finalize(const Handle* h, ThetaPtrs th, bool grad, const double* partials, int nsolve,
                      const double* eta_partials, int neta, double* out, double* tau, double* g_eta, double* g_W,
-                     double* g_v, double* g_s2, cudaStream_t st, bool gcv) {
+                     double* g_v, double* g_s2, cudaStream_t st, int gcv) {
     FinParams fp;
-    fp.gcv = gcv ? 1 : 0;
+    fp.gcv = gcv;
     fp.T = h->T;
     fp.d = h->d;
     fp.s = th.s;

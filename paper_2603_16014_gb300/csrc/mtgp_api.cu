@@ -521,7 +521,7 @@ static int run_gcv(Handle* h, ThetaPtrs th, double* out, double* tau, cudaStream
     int nsolve;
     if (h->equal) {
         mtgp_prof_begin(h, "solve_equal_gcv", st);
-        launch_solve_equal(h, th, false, h->partials, st, true);
+        launch_solve_equal(h, th, false, h->partials, st, 1);
         mtgp_prof_end(h, st);
         nsolve = solve_equal_blocks(h);
     } else {
@@ -531,8 +531,7 @@ static int run_gcv(Handle* h, ThetaPtrs th, double* out, double* tau, cudaStream
         nsolve = solve_tree_blocks(h);
     }
     mtgp_prof_begin(h, "finalize", st);
-    launch_finalize(h, th, false, h->partials, nsolve, nullptr, 0, out, tau, nullptr, nullptr, nullptr, nullptr, st,
-                    true);
+    launch_finalize(h, th, false, h->partials, nsolve, nullptr, 0, out, tau, nullptr, nullptr, nullptr, nullptr, st, 1);
     mtgp_prof_end(h, st);
     CK(cudaGetLastError());
     return MTGP_OK;
@@ -572,6 +571,47 @@ int mtgp_cubature(mtgp_t* hs, const double* eta, const double* W, int s, const d
     k_cubature<<<1, 32, 0, st>>>(cp, th, h->spec, h->alpha, h->tau, h->pi_buf, mu, Sigma, h->status);
     CK(cudaGetLastError());
     return MTGP_OK;
+}
+
+// GCV gradient, equal sizes: the value pass, then a second per-frequency pass with the totals, the
+// adjoint transforms and the eta pass of the MLE gradient
+static int run_gcv_grad(Handle* h, ThetaPtrs th, double* out, double* tau, double* g_eta, double* g_W, double* g_v,
+                        double* g_s2, cudaStream_t st) {
+    int rc = run_gcv(h, th, out, tau, st);
+    if (rc) return rc;
+    mtgp_prof_begin(h, "solve_equal_gcv_grad", st);
+    launch_solve_equal(h, th, true, h->partials, st, 2, out + 1);
+    mtgp_prof_end(h, st);
+    const int nsolve = solve_equal_blocks(h);
+    const int NQ = 3 + h->T * (h->T + 1) / 2;
+    double* eta_part = h->partials + (long long)nsolve * NQ;
+    mtgp_prof_begin(h, "xform_dif", st);
+    for (int g = 0; g < h->ngroups; ++g)
+        launch_transform(h, h->wgt, h->fp32, h->cplx, h->group_m[g], h->offs_dev + h->group_first[g],
+                         h->group_count[g], true, st);
+    mtgp_prof_end(h, st);
+    const int neta = eta_grad_blocks(h);
+    mtgp_prof_begin(h, "eta_grad", st);
+    launch_eta_grad(h, th.eta, h->wgt, eta_part, neta, st);
+    mtgp_prof_end(h, st);
+    mtgp_prof_begin(h, "finalize", st);
+    launch_finalize(h, th, true, h->partials, nsolve, eta_part, neta, out, nullptr, g_eta, g_W, g_v, g_s2, st, 2);
+    mtgp_prof_end(h, st);
+    CK(cudaGetLastError());
+    return MTGP_OK;
+}
+
+int mtgp_gcv_grad(mtgp_t* hs, const double* eta, const double* W, int s, const double* v, const double* sigma2,
+                  double* out, double* tau, double* g_eta, double* g_W, double* g_v, double* g_sigma2,
+                  cudaStream_t st) {
+    if (!hs || !out || !g_eta || !g_W || !g_v || !g_sigma2) return fail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    Handle* h = &hs->h;
+    if (!h->equal) return fail(MTGP_ERR_UNSUPPORTED, "the GCV gradient needs equal task sizes in this build");
+    int rc = validate_theta(h, eta, W, s, v, sigma2);
+    if (rc) return rc;
+    if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
+    ThetaPtrs th{eta, W, s, v, sigma2};
+    return run_gcv_grad(h, th, out, tau, g_eta, g_W, g_v, g_sigma2, st);
 }
 
 int mtgp_gcv(mtgp_t* hs, const double* eta, const double* W, int s, const double* v, const double* sigma2,

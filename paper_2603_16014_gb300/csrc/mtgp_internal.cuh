@@ -185,16 +185,17 @@ void launch_twiddles(Handle* h, cudaStream_t st);
 
 // k_solve.cu
 int solve_equal_blocks(const Handle* h);
-// gcv = true: the GCV loss instead of the MLE loss (no gradient); partial columns 2 and 3 then hold
-// ||Lambda^-1 rhat||^2 and trace(Lambda^-1)
+// gcv = 1: the GCV loss instead of the MLE loss; partial columns 2 and 3 then hold ||Lambda^-1 rhat||^2
+// and trace(Lambda^-1).  gcv = 2 (equal sizes): the GCV gradient pass, reading [A, B] from gcv_ab,
+// with the MLE gradient's partial layout and adjoint weights.
 void launch_solve_equal(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st,
-                        bool gcv = false);
+                        int gcv = 0, const double* gcv_ab = nullptr);
 void launch_solve_tree(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st,
                        bool gcv = false);
 int solve_tree_blocks(const Handle* h);
 void launch_finalize(const Handle* h, ThetaPtrs th, bool grad, const double* partials, int nsolve,
                      const double* eta_partials, int neta, double* out, double* tau, double* g_eta,
-                     double* g_W, double* g_v, double* g_s2, cudaStream_t st, bool gcv = false);
+                     double* g_W, double* g_v, double* g_s2, cudaStream_t st, int gcv = 0);
 
 // k_fused.cu (equal sizes)
 bool fused_supported(const Handle* h);

@@ -113,6 +113,19 @@ class MTGP:
                              _stream(stream)), "mtgp_gcv")
         return out, tau
 
+    def gcv_grad(self, eta, W, v, sigma2, stream=None):
+        """Returns (out, tau, g_eta, g_W, g_v, g_sigma2): the GCV loss and its gradient (equal sizes)."""
+        eta, W, v, s2 = self._theta(eta, W, v, sigma2)
+        out = torch.empty(3, dtype=torch.float64, device="cuda")
+        tau = torch.empty(self.T, dtype=torch.float64, device="cuda")
+        ge = torch.empty(self.d, dtype=torch.float64, device="cuda")
+        gW = torch.empty_like(W)
+        gv = torch.empty(self.T, dtype=torch.float64, device="cuda")
+        gs = torch.empty(1, dtype=torch.float64, device="cuda")
+        check(lib().mtgp_gcv_grad(self._h, _ptr(eta), _ptr(W), W.shape[1], _ptr(v), _ptr(s2), _ptr(out), _ptr(tau),
+                                  _ptr(ge), _ptr(gW), _ptr(gv), _ptr(gs), _stream(stream)), "mtgp_gcv_grad")
+        return out, tau, ge, gW, gv, gs
+
     def cubature(self, eta, W, v, sigma2, stream=None):
         """Returns (mu_hat (T,), Sigma (T, T)): posterior mean and covariance of the task integrals."""
         eta, W, v, s2 = self._theta(eta, W, v, sigma2)

@@ -69,3 +69,36 @@ def test_gcv_nested_lattice_d16_vs_class_oracle():
     assert abs(out[0] - ref["L"]) <= 1e-8 * abs(ref["L"]), (out[0], ref["L"])
     assert abs(out[2] - ref["trace"]) <= 1e-8 * abs(ref["trace"])
     assert np.allclose(tau, ref["tau"], rtol=1e-8, atol=1e-10)
+
+
+@pytest.mark.parametrize("kind,m,precision", [("lattice", (6, 6), "fp64"), ("dnet", (5, 5, 5), "fp64"),
+                                              ("dnet", (6, 6, 6, 6), "fp32")])
+def test_gcv_gradient_vs_dense(kind, m, precision):
+    from paper_2603_16014_gb300.mtgp import MTGP
+    p = inputs.make_problem(kind, 3, m, seed=22, eta=0.7, v=0.2, sigma2=1e-4,
+                            recipe="walshcos32" if kind == "dnet" else "cos16", mmax=max(max(m), 8))
+    X = dense.all_points(p.kind, p.gen, p.shift, p.m)
+    y = inputs.synth_y(p, X)
+    ref, ge, gW, gv, gs = dense.gcv_grad(p.kind, X, y, p.eta, p.W, p.v, p.sigma2)
+    model = MTGP.from_problem(p, precision)
+    model.set_y(torch.from_numpy(y))
+    out, tau, e_, W_, v_, s_ = model.gcv_grad(p.eta, p.W, p.v, p.sigma2)
+    model.sync()
+    tol = 1e-7 if precision == "fp64" else 1e-4
+    gref = np.concatenate([ge, gW.ravel(), gv, [gs]])
+    got = np.concatenate([e_.cpu().numpy(), W_.cpu().numpy().ravel(), v_.cpu().numpy(), s_.cpu().numpy()])
+    assert abs(out[0].item() - ref["L"]) <= TOL[precision] * abs(ref["L"])
+    assert np.allclose(got, gref, rtol=tol, atol=tol * np.abs(gref).max()), np.max(np.abs(got - gref) / np.abs(gref).max())
+    model.close()
+
+
+def test_gcv_gradient_unequal_sizes_unsupported():
+    from paper_2603_16014_gb300._lib import MTGPError
+    from paper_2603_16014_gb300.mtgp import MTGP
+    p = inputs.make_problem("lattice", 2, (5, 3), seed=2)
+    model = MTGP.from_problem(p, "fp64")
+    model.set_y(torch.zeros(p.N, dtype=torch.float64))
+    with pytest.raises(MTGPError) as ei:
+        model.gcv_grad(p.eta, p.W, p.v, p.sigma2)
+    assert ei.value.code == 5
+    model.close()
