@@ -171,6 +171,17 @@ def make_workload(seed: int = 0):
     return p, model, y
 
 
+def timed_oracle(fn, seconds: float, min_reps: int = 1):
+    """Repeat an oracle call for at least `seconds` (and min_reps times); returns (reps, elapsed s)."""
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        fn()
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and reps >= min_reps:
+            return reps, el
+
+
 def cpu_baseline(seconds: float = 10.0):
     """The oracle (spectral FP64, numpy) on full NLL + gradient evaluations of the same workload."""
     import numpy as np
@@ -460,6 +471,25 @@ def run_batch(args):
                    "plain": f"torch Adam through the autograd NLL, fit by fit, {k_plain} steps per fit scaled to {steps}"},
         "final_nll_mean": float(np.mean(final_batch)),
     }
+    # FP64 roofline of the batched step: the per-frequency solves of every fit
+    step_s = graph_ms / steps / 1e3
+    flops = sum(p.n[0] * solve_flops_per_freq(p.T, p.kind == "lattice", True) for p in probs)
+    bytes_ = sum(p.n[0] * (8 * p.T + 4 * (1 + p.T * (p.T - 1) // 2) * 4) for p in probs)
+    peaks = measured_peaks()
+    line["roofline"] = {"bound": "alu", "kernel": "batched fused kernels (FP64 per-frequency solves)",
+                        "achieved": flops / step_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": flops / step_s / 1e12 / FP64_PEAK_TFLOPS, "flops_per_step": flops,
+                        "step_hbm_view": {"algorithmic_bytes": bytes_, "achieved_gbs": bytes_ / step_s / 1e9,
+                                          "frac": bytes_ / step_s / 1e9 / peaks["hbm_gbs"]}}
+    if not args.no_cpu_baseline:
+        from oracle import spectral
+        sample = probs[::32]
+        sy = ys[::32]
+        reps, el = timed_oracle(lambda: [spectral.nll_grad_equal(q.kind, q.gen, q.shift, q.m, yq, *default_theta(q))
+                                         for q, yq in zip(sample, sy)], 10.0)
+        line["cpu_baseline"] = {"value": reps * len(sample) / el, "unit": "fit-evals/s", "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": f"{reps} x NLL+gradient of {len(sample)} of the fits "
+                                                            f"(every 32nd) by the per-frequency oracle, {el:.1f} s"}
     print(json.dumps(line), flush=True)
     b.close()
 
@@ -560,6 +590,16 @@ def _timed(fn, K, W, flush, stream):
     return [a.elapsed_time(b) for a, b in ev]
 
 
+def nested_oracle_baseline(p, y):
+    """The per-residue-class oracle (dense Cholesky per class, FP64 numpy) on the full nested fit;
+    it computes the NLL without a gradient."""
+    from oracle import spectral
+    reps, el = timed_oracle(lambda: spectral.nll_by_class(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2),
+                            10.0)
+    return {"value": reps / el, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{reps} full NLL evaluations (no gradient) of the nested fit by the per-class oracle, {el:.1f} s"}
+
+
 def run_nested(args):
     """NLL + gradient of the nested unequal-size lattice fit (d = 16, T = 5, n = 2^20 .. 2^12, FP64)."""
     import numpy as np
@@ -596,6 +636,7 @@ def run_nested(args):
         "config": {"workload": "lat_d16_T5_nested", "kind": "lattice", "d": p.d, "T": p.T, "n": n, "N": p.N,
                    "precision": "FP64", "l2": "flushed (256 MB write) between steps"},
         "pair_entries": entries,
+        "cpu_baseline": nested_oracle_baseline(p, y) if not args.no_cpu_baseline else None,
         "kernels_us_per_step": {k: v[0] / 5 * 1e3 for k, v in prof.items()},
         "launches_per_step": {k: v[1] // 5 for k, v in prof.items()},
         "nll": outs[0][0].item(),
@@ -631,8 +672,22 @@ def run_posterior(args):
     prof = model.profile_read()
     model.profile(False)
     N = p.N
+    pairs_s = res["mean"]["queries_per_s"] * N
+    fp64_ops = pairs_s * (2 * p.d + 1)           # per pair: d (DFMA, DMUL) factor steps + one DFMA with beta
+    roof = {"bound": "alu", "kernel": "k_post_mean_part", "achieved": fp64_ops / 1e12, "unit": "T FP64 instr/s",
+            "peak": FP64_PEAK_TFLOPS / 2, "frac": fp64_ops / 1e12 / (FP64_PEAK_TFLOPS / 2),
+            "peak_source": "FP64 instruction issue rate = nominal 1.25 TFLOP/s / 2 flops per DFMA"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import dense, spectral
+        Xq, _, tq = inputs.query_points(64, p.d, seed=3, tasks=p.T)
+        reps, el = timed_oracle(lambda: spectral.posterior_mean_equal(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v,
+                                                                      p.sigma2, Xq, tq), 10.0)
+        cpu = {"value": 64 * reps / el, "unit": "queries/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{reps} x 64 posterior means by the per-frequency oracle (setup included each time), {el:.1f} s"}
     line = {
         "metric": "posterior queries per second (mean; mean + variance)", "value": res["mean"]["queries_per_s"],
+        "roofline": roof, "cpu_baseline": cpu,
         "unit": "queries/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
         "config": {"workload": "posterior_dnet_d8_T4_n2^16", "d": p.d, "T": p.T, "N": N,
                    "precision": "FP32 transforms / FP64 kernel sums"},
@@ -720,6 +775,16 @@ def run_gcv(args):
     ms = _timed(lambda: mq.gcv(*thq), max(args.steps // 5, 3), args.warmup, flush, stream)
     res["lat_d16_T5_nested"] = {"evals_per_s": 1e3 * len(ms) / sum(ms), "ms": sum(ms) / len(ms),
                                 "L_gcv": mq.gcv(*thq)[0][0].item()}
+    if not args.no_cpu_baseline:
+        from oracle import spectral
+        p0 = inputs.dnet_equal()
+        from oracle import dense
+        X0 = dense.all_points(p0.kind, p0.gen, p0.shift, p0.m)
+        y0 = inputs.synth_y(p0, X0)
+        reps, el = timed_oracle(lambda: spectral.gcv_equal(p0.kind, p0.gen, p0.shift, p0.m, y0, p0.eta, p0.W, p0.v,
+                                                           p0.sigma2), 10.0)
+        res["cpu_baseline"] = {"value": reps / el, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": f"{reps} GCV loss evaluations of dnet_d8_T4_n2^16 (per-frequency oracle), {el:.1f} s"}
     line = {"metric": "GCV loss evaluations per second", "value": res["dnet_d8_T4_n2^16"]["evals_per_s"],
             "unit": "evals/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
             "config": {"workload": "gcv", "l2": "flushed (256 MB write) between steps"}, "results": res}

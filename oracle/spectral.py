@@ -417,6 +417,36 @@ def posterior_by_class(kind, gen, shift, m, y, eta, W, v, sigma2, Xq, task_q):
     return mean, var
 
 
+def posterior_mean_equal(kind, gen, shift, m, y, eta, W, v, sigma2, Xq, task_q):
+    """Posterior mean (Eq. 3.2) for equal sizes: alpha(f) = Lambda(f)^-1 rhat(f) per frequency,
+    beta_t = V alpha_t (= K~^-1 r per task), mean_t(x) = tau_t + sum_u R_tu sum_i Q(x, x_ui) beta_u[i]."""
+    T = len(m)
+    mm = int(m[0])
+    n = 1 << mm
+    X = [design_points(kind, gen, shift[t], n) for t in range(T)]
+    R = task_covariance(W, v)
+    lam = lambda_blocks(kind, X, eta, R, sigma2)
+    Lam = np.zeros((n, T, T), dtype=np.complex128)
+    for t in range(T):
+        for u in range(t, T):
+            Lam[:, t, u] = lam[(t, u)]
+            Lam[:, u, t] = np.conj(lam[(t, u)])
+        Lam[:, t, t] = lam[(t, t)].real
+    ys = np.asarray(y, dtype=np.float64).reshape(T, n)
+    yhat = vdag(kind, ys.astype(np.complex128), mm)
+    tau = yhat[:, 0].real / np.sqrt(n)
+    rhat = yhat.copy()
+    rhat[:, 0] = 0.0
+    alpha = np.linalg.solve(Lam, rhat.T[:, :, None])[:, :, 0].T        # (T, n)
+    beta = vmul(kind, alpha, mm).real
+    mean = np.empty(len(task_q))
+    for qi in range(len(task_q)):
+        t = int(task_q[qi])
+        mean[qi] = tau[t] + sum(R[t, u] * float(product_kernel(kind, X[u], Xq[qi][None, :], eta) @ beta[u])
+                                for u in range(T))
+    return mean
+
+
 def nll_grad_equal(kind, gen, shift, m, y, eta, W, v, sigma2):
     """Equal sizes: L (Eq. 3.3) and its gradient by per-frequency traces, dL/dtheta = sum_f tr(G(f) dLambda(f)),
     G(f) = Lambda(f)^-1 - alpha(f) alpha(f)^H, every dLambda(f)/dtheta formed explicitly:

@@ -187,3 +187,14 @@ def test_equal_spectral_gradient_matches_dense(kind, m, d):
     assert abs(got[0]["L"] - ref[0]["L"]) < 1e-9 * abs(ref[0]["L"])
     for a, b in zip(got[1:], ref[1:]):
         assert np.allclose(a, b, rtol=1e-8, atol=1e-8 * (1 + np.abs(np.asarray(ref[1])).max()))
+
+
+@pytest.mark.parametrize("kind", ["lattice", "dnet"])
+def test_posterior_mean_equal_matches_dense(kind):
+    p = inputs.make_problem(kind, 2, (5, 5, 5), seed=17, eta=0.6, v=0.1, sigma2=1e-4)
+    X = dense.all_points(p.kind, p.gen, p.shift, p.m)
+    y = inputs.synth_y(p, X)
+    Xq, xq, tq = inputs.query_points(9, 2, seed=3, tasks=3)
+    mean_ref, _, prior = dense.posterior(p.kind, X, y, p.eta, p.W, p.v, p.sigma2, Xq, tq)
+    mean = spectral.posterior_mean_equal(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2, Xq, tq)
+    assert np.allclose(mean, mean_ref, rtol=0, atol=1e-9 * prior.max())
