@@ -24,15 +24,15 @@ def all_points(kind, gen, shift, m):
     return [design_points(kind, gen, shift[t], 1 << int(m[t])) for t in range(len(m))]
 
 
-def gram(kind, X_tasks, eta, R, sigma2):
-    """Dense K~ (N x N), tasks in the given order, each in radical-inverse order."""
+def gram(kind, X_tasks, eta, R, sigma2, alpha=2):
+    """Dense K~ (N x N), tasks in the given order, each in radical-inverse order (alpha: SI smoothness)."""
     T = len(X_tasks)
     n = [len(X) for X in X_tasks]
     off = np.concatenate([[0], np.cumsum(n)])
     K = np.empty((off[-1], off[-1]))
     for t in range(T):
         for u in range(T):
-            Q = product_kernel(kind, X_tasks[t][:, None, :], X_tasks[u][None, :, :], eta)
+            Q = product_kernel(kind, X_tasks[t][:, None, :], X_tasks[u][None, :, :], eta, alpha=alpha)
             K[off[t]:off[t + 1], off[u]:off[u + 1]] = R[t, u] * Q
     K[np.diag_indices_from(K)] += sigma2
     return K
@@ -49,10 +49,10 @@ def summing_matrix(n):
     return E
 
 
-def nll(kind, X_tasks, y, eta, W, v, sigma2):
+def nll(kind, X_tasks, y, eta, W, v, sigma2, alpha=2):
     """Returns dict with L (Eq. 3.3), nll, quad, logdet, tau (Eq. 3.4) by dense Cholesky."""
     R = task_covariance(W, v)
-    K = gram(kind, X_tasks, eta, R, sigma2)
+    K = gram(kind, X_tasks, eta, R, sigma2, alpha)
     n = [len(X) for X in X_tasks]
     N = sum(n)
     E = summing_matrix(n)
@@ -88,7 +88,7 @@ def gcv(kind, X_tasks, y, eta, W, v, sigma2):
     return dict(L=num / tr ** 2, num=num, trace=tr, tau=tau)
 
 
-def _param_contractions(kind, X_tasks, eta, W, R, K, contract):
+def _param_contractions(kind, X_tasks, eta, W, R, K, contract, alpha=2):
     """contract(dK~/dtheta) for every parameter: eta (d), W (T x s), v (T), sigma2, with the dense
     derivatives of K~ written out (see nll_grad)."""
     T = len(X_tasks)
@@ -99,7 +99,7 @@ def _param_contractions(kind, X_tasks, eta, W, R, K, contract):
     K1 = [[None] * T for _ in range(T)]
     for t in range(T):
         for u in range(T):
-            K1[t][u] = [kernel_1d(kind, X_tasks[t][:, None, j], X_tasks[u][None, :, j]) for j in range(d)]
+            K1[t][u] = [kernel_1d(kind, X_tasks[t][:, None, j], X_tasks[u][None, :, j], alpha) for j in range(d)]
     g_eta = np.zeros(d)
     for j in range(d):
         dK = np.zeros_like(K)
@@ -111,7 +111,7 @@ def _param_contractions(kind, X_tasks, eta, W, R, K, contract):
                         blk = blk * (1.0 + eta[l] * K1[t][u][l])
                 dK[off[t]:off[t + 1], off[u]:off[u + 1]] = R[t, u] * blk
         g_eta[j] = contract(dK)
-    Qfull = gram(kind, X_tasks, eta, np.ones((T, T)), 0.0)
+    Qfull = gram(kind, X_tasks, eta, np.ones((T, T)), 0.0, alpha)
 
     def blockwise(dR):
         dK = np.empty_like(K)
@@ -164,7 +164,7 @@ def gcv_grad(kind, X_tasks, y, eta, W, v, sigma2):
     return out, g_eta, g_W, g_v, g_s2
 
 
-def nll_grad(kind, X_tasks, y, eta, W, v, sigma2):
+def nll_grad(kind, X_tasks, y, eta, W, v, sigma2, alpha=2):
     """Analytic gradient of L (Eq. 3.3) w.r.t. eta (d), W (T x s), v (T), sigma2, at the optimal tau.
 
     dL/dtheta = tr(K~^-1 dK~/dtheta) - a^T (dK~/dtheta) a, each dK~ written out densely:
@@ -174,9 +174,9 @@ def nll_grad(kind, X_tasks, y, eta, W, v, sigma2):
       dK~/d sigma2  = I
     Returns (out_dict_of_nll, g_eta, g_W, g_v, g_sigma2) for L (the NLL gradient is half of it).
     """
-    out = nll(kind, X_tasks, y, eta, W, v, sigma2)
+    out = nll(kind, X_tasks, y, eta, W, v, sigma2, alpha)
     R = task_covariance(W, v)
-    K = gram(kind, X_tasks, eta, R, sigma2)
+    K = gram(kind, X_tasks, eta, R, sigma2, alpha)
     Kinv = np.linalg.inv(K)
     Kinv = 0.5 * (Kinv + Kinv.T)
     a = out["alpha"]
@@ -184,7 +184,7 @@ def nll_grad(kind, X_tasks, y, eta, W, v, sigma2):
     def contract(dK):
         return float(np.sum(Kinv * dK) - a @ dK @ a)
 
-    g_eta, g_W, g_v, g_s2 = _param_contractions(kind, X_tasks, eta, W, R, K, contract)
+    g_eta, g_W, g_v, g_s2 = _param_contractions(kind, X_tasks, eta, W, R, K, contract, alpha)
     return out, g_eta, g_W, g_v, g_s2
 
 

@@ -125,26 +125,27 @@ def dsi_kernel_1d(X: np.ndarray, alpha: int = 2) -> np.ndarray:
     return -1.0 - beta * x + 2.5 * (1.0 - t1)
 
 
-def kernel_1d(kind: str, Xa: np.ndarray, Xb: np.ndarray) -> np.ndarray:
-    """The univariate kernel of the kind's design/kernel pairing (Cond. 3.1) on fixed-point words."""
+def kernel_1d(kind: str, Xa: np.ndarray, Xb: np.ndarray, alpha: int = 2) -> np.ndarray:
+    """The univariate kernel of the kind's design/kernel pairing (Cond. 3.1) on fixed-point words;
+    alpha is the SI kernel's smoothness (Eq. 2.5); the DSI kernel is the order-2 term of Eq. 2.6."""
     Xa = np.asarray(Xa, dtype=np.uint64)
     Xb = np.asarray(Xb, dtype=np.uint64)
     if kind == "lattice":
         u = ((Xa - Xb) & np.uint64(MASK32)).astype(np.float64) / TWO32
-        return si_kernel_1d(u, 2)
+        return si_kernel_1d(u, alpha)
     if kind == "dnet":
         return dsi_kernel_1d(Xa ^ Xb, 2)
     raise ValueError(kind)
 
 
 def product_kernel(kind: str, Xa: np.ndarray, Xb: np.ndarray, eta: np.ndarray,
-                   gamma: float = 1.0) -> np.ndarray:
+                   gamma: float = 1.0, alpha: int = 2) -> np.ndarray:
     """Eq. 2.4: Q(x, x') = gamma prod_j (1 + eta_j K(x_j, x'_j)); Xa (..., d), Xb (..., d) broadcast."""
     Xa = np.asarray(Xa)
     Xb = np.asarray(Xb)
     out = None
     for j in range(len(eta)):
-        f = 1.0 + eta[j] * kernel_1d(kind, Xa[..., j], Xb[..., j])
+        f = 1.0 + eta[j] * kernel_1d(kind, Xa[..., j], Xb[..., j], alpha)
         out = f if out is None else out * f
     return gamma * out
 

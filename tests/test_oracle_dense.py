@@ -112,3 +112,26 @@ def test_posterior_identities_at_design_points(kind):
     Xr, _, tr = inputs.query_points(20, 2, seed=3, tasks=2)
     _, v2, prior = dense.posterior(kind, X, y, p.eta, p.W, p.v, p.sigma2, Xr, tr)
     assert np.all(v2 >= -1e-12) and np.all(v2 <= prior + 1e-12)
+
+
+@pytest.mark.parametrize("alpha", [1, 3, 4])
+def test_gradient_other_si_smoothness_matches_central_differences(alpha):
+    p = inputs.make_problem("lattice", 2, (4, 3), seed=22, eta=0.7, v=0.2, sigma2=1e-3, s=2)
+    X, y = _setup(p)
+    out, g_eta, g_W, g_v, g_s2 = dense.nll_grad("lattice", X, y, p.eta, p.W, p.v, p.sigma2, alpha)
+
+    def L(eta, W, v, s2):
+        return dense.nll("lattice", X, y, eta, W, v, s2, alpha)["L"]
+
+    h = 1e-6
+    for j in range(p.d):
+        e = np.zeros(p.d)
+        e[j] = h
+        fd = (L(p.eta + e, p.W, p.v, p.sigma2) - L(p.eta - e, p.W, p.v, p.sigma2)) / (2 * h)
+        assert abs(fd - g_eta[j]) < 1e-5 * (1 + abs(g_eta[j]))
+    E = np.zeros_like(p.W)
+    E[1, 0] = h
+    fd = (L(p.eta, p.W + E, p.v, p.sigma2) - L(p.eta, p.W - E, p.v, p.sigma2)) / (2 * h)
+    assert abs(fd - g_W[1, 0]) < 1e-5 * (1 + abs(g_W[1, 0]))
+    # the smoothness changes the kernel: alpha = 2 gives a different loss
+    assert abs(out["L"] - dense.nll("lattice", X, y, p.eta, p.W, p.v, p.sigma2)["L"]) > 1e-6

@@ -70,7 +70,7 @@ def test_dnet_linearity_and_net_property():
 
 # ------------------------------------------------------------------------------- SI kernel
 
-@pytest.mark.parametrize("alpha", [1, 2, 3])
+@pytest.mark.parametrize("alpha", [1, 2, 3, 4])
 def test_si_kernel_fourier_series(alpha):
     # Eq. 2.5 equals sum_{h != 0} e^{2 pi i h u} / |h|^{2 alpha} (Bernoulli polynomial Fourier series)
     u = np.array([0.0, 0.1, 0.25, 0.5, 0.73, 0.999])
