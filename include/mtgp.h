@@ -175,6 +175,14 @@ int mtgp_nll_equal_static(int kind, int d, int T, int m, const uint32_t* gen, in
                           double* tau, int* status, cudaStream_t stream);
 
 /*
+ * mtgp_set_smoothness -- the SI kernel's smoothness alpha in Eq. 2.5 for a lattice handle: 1, 2
+ * (default), 3 or 4, i.e. (-1)^(alpha+1) (2 pi)^(2 alpha) / (2 alpha)! B_(2 alpha)((x - x') mod 1) as
+ * the univariate factor of Eq. 2.4.  Digital-net handles keep the order-2 DSI kernel (other values:
+ * MTGP_ERR_UNSUPPORTED).  Takes effect for the following calls on the handle; synchronous, host only.
+ */
+int mtgp_set_smoothness(mtgp_t* h, int alpha);
+
+/*
  * Multitask Bayesian cubature (Sec. 3.5, multitask cubature theorem) for the task integrals
  * mu_t = int f(t, x) dx under the fitted MTGP at the MLE mean.  The product kernels of Eq. 2.4 with
  * the SI or DSI factors integrate to gamma = 1 in each argument, so

@@ -188,14 +188,14 @@ def nll_grad(kind, X_tasks, y, eta, W, v, sigma2, alpha=2):
     return out, g_eta, g_W, g_v, g_s2
 
 
-def posterior(kind, X_tasks, y, eta, W, v, sigma2, Xq, task_q):
+def posterior(kind, X_tasks, y, eta, W, v, sigma2, Xq, task_q, alpha=2):
     """Posterior mean and variance of f(t, x) at fixed-point queries Xq (nq x d), Eq. 3.2.
 
     tau is the MLE optimal mean (Eq. 3.4), plugged in as the prior mean.
     """
-    out = nll(kind, X_tasks, y, eta, W, v, sigma2)
+    out = nll(kind, X_tasks, y, eta, W, v, sigma2, alpha)
     R = task_covariance(W, v)
-    K = gram(kind, X_tasks, eta, R, sigma2)
+    K = gram(kind, X_tasks, eta, R, sigma2, alpha)
     cf = sla.cho_factor(K, lower=True)
     T = len(X_tasks)
     nq = Xq.shape[0]
@@ -203,13 +203,14 @@ def posterior(kind, X_tasks, y, eta, W, v, sigma2, Xq, task_q):
     off = 0
     Qs = []
     for u in range(T):
-        Qs.append(product_kernel(kind, Xq[:, None, :], X_tasks[u][None, :, :], eta))
+        Qs.append(product_kernel(kind, Xq[:, None, :], X_tasks[u][None, :, :], eta, alpha=alpha))
     for i in range(nq):
         row = np.concatenate([R[task_q[i], u] * Qs[u][i] for u in range(T)])
         kq[i] = row
     mean = out["tau"][task_q] + kq @ out["alpha"]
     Kinv_kq = sla.cho_solve(cf, kq.T)
-    prior = np.array([R[task_q[i], task_q[i]] * product_kernel(kind, Xq[i], Xq[i], eta) for i in range(nq)])
+    prior = np.array([R[task_q[i], task_q[i]] * product_kernel(kind, Xq[i], Xq[i], eta, alpha=alpha)
+                      for i in range(nq)])
     var = prior - np.einsum("ij,ji->i", kq, Kinv_kq)
     return mean, var, prior
 

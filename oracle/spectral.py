@@ -447,6 +447,32 @@ def posterior_mean_equal(kind, gen, shift, m, y, eta, W, v, sigma2, Xq, task_q):
     return mean
 
 
+def posterior_var_equal(kind, gen, shift, m, eta, W, v, sigma2, Xq, task_q):
+    """Posterior variance (Eq. 3.2) for equal sizes, query by query: kappa_u = R_{t u} V^dagger q_u(x)
+    with q_u(x)[i] = Q(x, x_ui), var = R_tt Q(x, x) - sum_f kappa(f)^H Lambda(f)^-1 kappa(f)."""
+    T = len(m)
+    mm = int(m[0])
+    n = 1 << mm
+    X = [design_points(kind, gen, shift[t], n) for t in range(T)]
+    R = task_covariance(W, v)
+    lam = lambda_blocks(kind, X, eta, R, sigma2)
+    Lam = np.zeros((n, T, T), dtype=np.complex128)
+    for t in range(T):
+        for u in range(t, T):
+            Lam[:, t, u] = lam[(t, u)]
+            Lam[:, u, t] = np.conj(lam[(t, u)])
+        Lam[:, t, t] = lam[(t, t)].real
+    var = np.empty(len(task_q))
+    for qi in range(len(task_q)):
+        t = int(task_q[qi])
+        kap = np.stack([R[t, u] * vdag(kind, product_kernel(kind, X[u], Xq[qi][None, :], eta).astype(np.complex128), mm)
+                        for u in range(T)], axis=1)                        # (n, T)
+        sol = np.linalg.solve(Lam, kap[:, :, None])[:, :, 0]
+        prior = R[t, t] * float(product_kernel(kind, Xq[qi], Xq[qi], eta))
+        var[qi] = prior - float(np.sum(np.conj(kap) * sol).real)
+    return var
+
+
 def nll_grad_equal(kind, gen, shift, m, y, eta, W, v, sigma2):
     """Equal sizes: L (Eq. 3.3) and its gradient by per-frequency traces, dL/dtheta = sum_f tr(G(f) dLambda(f)),
     G(f) = Lambda(f)^-1 - alpha(f) alpha(f)^H, every dLambda(f)/dtheta formed explicitly:

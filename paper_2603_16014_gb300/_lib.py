@@ -47,6 +47,7 @@ _SIGS = {
     "mtgp_batch_adam": (_i, [_p, _i, ctypes.c_double, _i, _p, _p]),
     "mtgp_batch_autotune": (_i, [_p, _i, _p, _p]),
     "mtgp_gcv": (_i, [_p, _p, _p, _i, _p, _p, _p, _p, _p]),
+    "mtgp_set_smoothness": (_i, [_p, _i]),
     "mtgp_cubature": (_i, [_p, _p, _p, _i, _p, _p, _p, _p, _p]),
     "mtgp_gcv_grad": (_i, [_p, _p, _p, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p]),
     "mtgp_batch_features": (_i, [_p, _p, _p]),

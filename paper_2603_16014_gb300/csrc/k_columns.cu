@@ -12,6 +12,7 @@ constexpr int kThreads = 256;
 
 struct ColParams {
     ColDesc cols[MTGP_MAX_COLS];
+    int alpha;  // SI smoothness
 };
 
 template <typename S, bool CPLX>
@@ -33,7 +34,7 @@ k_colgen(void* out, ColParams cp, int kind, int d, const uint32_t* __restrict__ 
         for (int j = 0; j < d; ++j) {
             uint32_t z = point_word(kind, (uint32_t)i, j, gen, gen_cols);
             uint32_t X = pair_word(kind, z, s_dt[j], s_du[j]);
-            q *= (S)1 + s_eta[j] * kernel1d<S>(kind, X);
+            q *= (S)1 + s_eta[j] * kernel1d<S>(kind, X, cp.alpha);
         }
         if (CPLX) {
             reinterpret_cast<cx<S>*>(out)[c.off + i] = mk(q, (S)0);
@@ -103,7 +104,7 @@ k_eta_grad(const void* omega, ColParams cp, int ncols, int kind, int d, const ui
         for (int j = 0; j < d; ++j) {
             uint32_t z = point_word(kind, (uint32_t)i, j, gen, gen_cols);
             uint32_t X = pair_word(kind, z, shift[cd.t * d + j], shift[cd.u * d + j]);
-            kv[j] = kernel1d<S>(kind, X);
+            kv[j] = kernel1d<S>(kind, X, cp.alpha);
             pre[j] = p;
             p *= (S)1 + s_eta[j] * kv[j];
         }
@@ -130,6 +131,7 @@ k_eta_grad(const void* omega, ColParams cp, int ncols, int kind, int d, const ui
 ColParams make_params(const Handle* h) {
     ColParams cp;
     for (int c = 0; c < h->ncols; ++c) cp.cols[c] = h->cols[c];
+    cp.alpha = h->smooth;
     return cp;
 }
 

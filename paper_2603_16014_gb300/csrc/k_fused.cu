@@ -25,7 +25,7 @@ __device__ __forceinline__ S el_re(S x) { return x; }
 template <typename S>
 __device__ __forceinline__ S el_re(cx<S> x) { return x.re; }
 struct FusedParams {
-    int kind, d, T, C, gen_cols, m, a, lgL, grad, clamp, store_alpha, mtw, s;
+    int kind, d, T, C, gen_cols, m, a, lgL, grad, clamp, store_alpha, mtw, s, alpha;
     long long n, N;
     int colt[MTGP_MAX_COLS], colu[MTGP_MAX_COLS];
     int colidx[MTGP_TMAX][MTGP_TMAX];
@@ -139,6 +139,31 @@ __device__ void write_outputs(const double* tot, const double* etot, const Fused
     }
 }
 
+// two partial arrays reduced in one pass: warps take the columns of both in turn
+__device__ void reduce_columns2(const double* part1, int nrows1, int ncols1, double* out1, const double* part2,
+                                int nrows2, int ncols2, double* out2) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int qq = warp; qq < ncols1 + ncols2; qq += nw) {
+        const bool first = qq < ncols1;
+        const double* part = first ? part1 : part2;
+        const int nrows = first ? nrows1 : nrows2, ncols = first ? ncols1 : ncols2, q = first ? qq : qq - ncols1;
+        double v = 0.0;
+        for (int b0 = lane; b0 < nrows; b0 += 256) {
+            double t[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int b = b0 + 32 * k;
+                t[k] = b < nrows ? part[(long long)b * ncols + q] : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v += t[k];
+        }
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) (first ? out1 : out2)[q] = v;
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------------- kernel A
 
 // design-point words of the chunk [base, base + 2^a): z(base + lo) = z(base) (+) z(lo) (lattice: +,
@@ -236,7 +261,7 @@ __device__ __forceinline__ void fused_a_body(const FitDesc& f, int blk) {
             for (int j = 0; j < DMAX; ++j) {
                 if (j < d) {
                     uint32_t X = pair_word(p.kind, s_z[(j << p.a) + lo], s_sh[t * d + j], s_sh[u * d + j]);
-                    q *= (S)1 + s_eta[j] * kernel1d<S>(p.kind, X);
+                    q *= (S)1 + s_eta[j] * kernel1d<S>(p.kind, X, p.alpha);
                 }
             }
             if constexpr (CPLX) buf[e] = mk(q, (S)0);
@@ -253,7 +278,7 @@ __device__ __forceinline__ void fused_a_body(const FitDesc& f, int blk) {
                 for (int j = 0; j < DMAX; ++j) {
                     if (j < d) {
                         uint32_t X = pair_word(p.kind, z[j], s_sh[t * d + j], s_sh[u * d + j]);
-                        q *= (S)1 + s_eta[j] * kernel1d<S>(p.kind, X);
+                        q *= (S)1 + s_eta[j] * kernel1d<S>(p.kind, X, p.alpha);
                     }
                 }
                 if constexpr (CPLX) buf[c * HA + lo] = mk(q, (S)0);
@@ -473,7 +498,7 @@ __device__ __forceinline__ void fused_c_body(const FitDesc& f, int blk) {
         for (int j = 0; j < DMAX; ++j) {
             if (j < d) {
                 uint32_t X = pair_word(p.kind, zc[j * zstride], s_sh[t * d + j], s_sh[u * d + j]);
-                kv[j] = kernel1d<S>(p.kind, X);
+                kv[j] = kernel1d<S>(p.kind, X, p.alpha);
                 pre[j] = pr;
                 pr *= (S)1 + s_eta[j] * kv[j];
             }
@@ -521,8 +546,7 @@ __device__ __forceinline__ void fused_c_body(const FitDesc& f, int blk) {
     }
     if (!last_block(counter, f.na)) return;
     const int NQ = 3 + p.T * (p.T + 1) / 2;
-    reduce_columns(partials_b, nb, NQ, s_tot);
-    reduce_columns(partials_c, f.na, d, s_etot);
+    reduce_columns2(partials_b, nb, NQ, s_tot, partials_c, f.na, d, s_etot);
     if (threadIdx.x == 0) {
         write_outputs(s_tot, s_etot, p, th, tau_sorted, f.o);
         *counter = 0u;
@@ -627,6 +651,7 @@ FusedParams make_params(const Handle* h, ThetaPtrs th, bool grad, bool store_alp
     FusedParams p;
     std::memset(&p, 0, sizeof(p));
     p.kind = h->kind;
+    p.alpha = h->smooth;
     p.d = h->d;
     p.T = h->T;
     p.C = h->ncols;

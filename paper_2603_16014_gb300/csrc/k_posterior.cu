@@ -68,7 +68,7 @@ __global__ void k_beta_finish(const double* __restrict__ beta, double* __restric
 }
 
 struct PostParams {
-    int kind, d, T;
+    int kind, d, T, alpha;
     long long n[MTGP_TMAX];
     long long yoff[MTGP_TMAX];
     int order[MTGP_TMAX];
@@ -76,11 +76,11 @@ struct PostParams {
 };
 
 template <typename S>
-__device__ __forceinline__ S qkernel(int kind, const uint32_t* xa, const uint32_t* xb, const S* eta, int d) {
+__device__ __forceinline__ S qkernel(int kind, const uint32_t* xa, const uint32_t* xb, const S* eta, int d, int alpha) {
     S q = (S)1;
     for (int j = 0; j < d; ++j) {
         uint32_t X = (kind == MTGP_LATTICE) ? (xa[j] - xb[j]) : (xa[j] ^ xb[j]);
-        q *= (S)1 + eta[j] * kernel1d<S>(kind, X);
+        q *= (S)1 + eta[j] * kernel1d<S>(kind, X, alpha);
     }
     return q;
 }
@@ -136,7 +136,7 @@ k_post_mean_part(const uint32_t* __restrict__ xqw, const int* __restrict__ task,
         for (int e = threadIdx.x; e < cnt; e += blockDim.x) s_b[e] = beta[p.yoff[u] + i0 + e];
         __syncthreads();
         if (act) {
-            for (int i = 0; i < cnt; ++i) acc += qkernel<double>(p.kind, xq, s_x + i * d, s_eta, d) * s_b[i];
+            for (int i = 0; i < cnt; ++i) acc += qkernel<double>(p.kind, xq, s_x + i * d, s_eta, d, p.alpha) * s_b[i];
         }
     }
     if (act) part[(long long)k * nq + q] = sR[tq * p.T + u] * acc;
@@ -171,7 +171,7 @@ __global__ void k_var_rows(const uint32_t* __restrict__ xqw, const int* __restri
         int b = (int)(bu / p.T);
         int q = q0 + b;
         int tq = p.rank[task[q]];
-        double v = sR[tq * p.T + u] * qkernel<double>(p.kind, xqw + (long long)q * p.d, dw + (p.yoff[u] + i) * p.d, s_eta, p.d);
+        double v = sR[tq * p.T + u] * qkernel<double>(p.kind, xqw + (long long)q * p.d, dw + (p.yoff[u] + i) * p.d, s_eta, p.d, p.alpha);
         if (CPLX) {
             rows[2 * e] = v;
             rows[2 * e + 1] = 0.0;
@@ -300,7 +300,7 @@ k_var_quad(const double* __restrict__ rows, const double* __restrict__ fac, cons
         int q = q0 + b;
         int tq = pp.rank[task[q]];
         const uint32_t* x = xqw + (long long)q * pp.d;
-        double prior = sR[tq * T + tq] * qkernel<double>(pp.kind, x, x, s_eta, pp.d);
+        double prior = sR[tq * T + tq] * qkernel<double>(pp.kind, x, x, s_eta, pp.d, pp.alpha);
         var[q] = prior - s;
     }
 }
@@ -420,6 +420,7 @@ int posterior_run(Handle* h, ThetaPtrs th, int nq, const double* xq, const int* 
                                                        1.0 / sqrt((double)h->n[t]));
     PostParams pp;
     pp.kind = h->kind;
+    pp.alpha = h->smooth;
     pp.d = d;
     pp.T = h->T;
     for (int t = 0; t < MTGP_TMAX; ++t) {

@@ -297,6 +297,7 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
     if (!hs) return fail(MTGP_ERR_CUDA, "host allocation failed");
     Handle* h = &hs->h;
     std::memset(h, 0, sizeof(Handle));
+    h->smooth = 2;
     h->kind = kind;
     h->d = d;
     h->T = T;
@@ -452,6 +453,16 @@ int mtgp_destroy(mtgp_t* hs) {
     posterior_release(&hs->h);
     free_all(&hs->h);
     delete hs;
+    return MTGP_OK;
+}
+
+int mtgp_set_smoothness(mtgp_t* hs, int alpha) {
+    if (!hs) return fail(MTGP_ERR_INVALID_ARG, "NULL handle");
+    Handle* h = &hs->h;
+    if (alpha < 1 || alpha > 4) return fail(MTGP_ERR_INVALID_ARG, "smoothness must be 1, 2, 3 or 4");
+    if (h->kind != MTGP_LATTICE && alpha != 2)
+        return fail(MTGP_ERR_UNSUPPORTED, "digital nets use the order-2 DSI kernel in this build");
+    h->smooth = alpha;
     return MTGP_OK;
 }
 

@@ -120,9 +120,28 @@ __device__ __forceinline__ double dsi2_kernel<double>(uint32_t X) {
     return u64_times_pow2((unsigned long long)(I < 0 ? -I : I), 33, I < 0);
 }
 
+// SI kernel of smoothness alpha = 1, 3, 4 (Eq. 2.5): the Bernoulli polynomial B_{2 alpha}(u) written
+// in w = u (1 - u):  B2 = 1/6 - w,  B6 = -w^3 - w^2 / 2 + 1/42,  B8 = w^4 + 4/3 w^3 + 2/3 w^2 - 1/30.
 template <typename S>
-__device__ __forceinline__ S kernel1d(int kind, uint32_t X) {
-    return kind == MTGP_LATTICE ? si2_kernel<S>(X) : dsi2_kernel<S>(X);
+__device__ __forceinline__ S si_kernel_alpha(uint32_t X, int alpha) {
+    const uint32_t Y = (X > 0x80000000u) ? (0u - X) : X;
+    S w;
+    if constexpr (sizeof(S) == 8) {
+        w = u64_times_pow2((unsigned long long)Y * (0x100000000ull - Y), 64, false);
+    } else {
+        const S u = (S)Y * (S)MTGP_2POW_M32;
+        w = u * ((S)1 - u);
+    }
+    if (alpha == 1) return (S)3.2898681336964529 - (S)19.739208802178717 * w;          // 2 pi^2 (1/6 - w)
+    if (alpha == 3) return (S)2.0346861239688983 - (S)85.456817206693728 * (w * w * ((S)0.5 + w));
+    // alpha = 4: -(2 pi^8 / 315) B8
+    return (S)2.0081547123958887 - (S)60.244641371876660 * (w * w * ((S)2 / (S)3 + w * ((S)4 / (S)3 + w)));
+}
+
+template <typename S>
+__device__ __forceinline__ S kernel1d(int kind, uint32_t X, int alpha = 2) {
+    if (kind == MTGP_LATTICE) return alpha == 2 ? si2_kernel<S>(X) : si_kernel_alpha<S>(X, alpha);
+    return dsi2_kernel<S>(X);
 }
 
 // Point z_i (unshifted) in coordinate j.  Lattice (Def. 2.1): v(i) g mod 1 = bitrev32(i) * g
@@ -281,6 +300,7 @@ struct Handle {
     struct Prof* prof;   // kernel timing log (host side)
     long long ws_bytes;
     bool y_set;
+    int smooth;          // SI kernel smoothness alpha of Eq. 2.5 (lattices; 2 unless set)
 };
 
 __device__ __forceinline__ void set_status(int* st, int bit) { atomicOr(st, bit); }

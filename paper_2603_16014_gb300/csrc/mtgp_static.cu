@@ -98,6 +98,7 @@ extern "C" int mtgp_nll_equal_static(int kind, int d, int T, int m, const uint32
     // ---- a host-side handle whose device pointers all point into the scratch array
     Handle h;
     std::memset(&h, 0, sizeof(h));
+    h.smooth = 2;
     h.kind = kind;
     h.d = d;
     h.T = T;

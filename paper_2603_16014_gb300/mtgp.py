@@ -103,6 +103,10 @@ class MTGP:
                                   _ptr(ge), _ptr(gW), _ptr(gv), _ptr(gs), _stream(stream)), "mtgp_nll_grad")
         return outs
 
+    def set_smoothness(self, alpha: int) -> None:
+        """SI kernel smoothness alpha (1..4) of a lattice handle (Eq. 2.5)."""
+        check(lib().mtgp_set_smoothness(self._h, int(alpha)), "mtgp_set_smoothness")
+
     def gcv(self, eta, W, v, sigma2, stream=None):
         """Returns (out, tau): out = [L_GCV, r^T K~^-2 r, trace K~^-1] (device float64), tau (T,) at
         the GCV mean."""

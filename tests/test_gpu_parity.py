@@ -247,3 +247,108 @@ def test_full_lattice_d16_T5_nested_vs_class_oracle():
     # ... and a tighter check at a step where truncation (h^2) and roundoff (1/h) are both small
     _check_fd(model, p, ge, gW, gv, gs, idx_eta=list(range(16)), idx_W=allW, idx_v=list(range(5)), nll=nll,
               with_sigma2=True, h=1e-4, rtol=1e-6)
+
+
+# ----------------------------------------------------------------------------- full sizes, bench launch shapes
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_full_size_posterior_sampled_outputs(precision):
+    """The d = 8, T = 4, n = 2^16 net fit with the bench's query counts (2^16 means, 2^10 variances);
+    sampled outputs against the per-frequency oracle."""
+    p = inputs.dnet_equal(fp32_transform=(precision == "fp32"))
+    X = _points_oracle(p)
+    y = inputs.synth_y(p, X)
+    model = _model(p, precision)
+    model.set_y(torch.from_numpy(y))
+    Xq, xq, tq = inputs.query_points(1 << 16, p.d, seed=3, tasks=p.T)
+    mean, _ = model.posterior(p.eta, p.W, p.v, p.sigma2, torch.from_numpy(xq), torch.from_numpy(tq), variance=False)
+    Xv, xv, tv = inputs.query_points(1 << 10, p.d, seed=4, tasks=p.T)
+    _, var = model.posterior(p.eta, p.W, p.v, p.sigma2, torch.from_numpy(xv), torch.from_numpy(tv), variance=True)
+    model.sync()
+    mean, var = mean.cpu().numpy(), var.cpu().numpy()
+    pick = np.array([0, 1, 4097, 65535, 31337])
+    ref = spectral.posterior_mean_equal(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2, Xq[pick], tq[pick])
+    R = design.task_covariance(p.W, p.v)
+    prior = np.array([R[t, t] * design.product_kernel(p.kind, Xq[i], Xq[i], p.eta) for i, t in zip(pick, tq[pick])])
+    tol = TOL_NLL[precision]
+    assert np.all(np.abs(mean[pick] - ref) <= tol * prior), np.max(np.abs(mean[pick] - ref) / prior)
+    vpick = np.array([0, 511, 1023])
+    vref = spectral.posterior_var_equal(p.kind, p.gen, p.shift, p.m, p.eta, p.W, p.v, p.sigma2, Xv[vpick], tv[vpick])
+    vprior = np.array([R[t, t] * design.product_kernel(p.kind, Xv[i], Xv[i], p.eta) for i, t in zip(vpick, tv[vpick])])
+    assert np.all(np.abs(var[vpick] - vref) <= tol * vprior), np.max(np.abs(var[vpick] - vref) / vprior)
+
+
+def test_full_size_batch_sampled_fits():
+    """The 512-fit mixed batch of the bench (FP32 transforms): sampled digital-net fits' NLL and
+    gradient against the per-frequency oracle."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    from paper_2603_16014_gb300.mtgp import Batch
+    probs = bench.batch_problems(512)
+    ys = [inputs.synth_y(q, dense.all_points(q.kind, q.gen, q.shift, q.m)) if i in (256, 300, 401, 511) else
+          np.random.default_rng(i).standard_normal(q.N) for i, q in enumerate(probs)]
+    b = Batch(probs, s=2, precision="fp32")
+    b.set_y(torch.from_numpy(np.concatenate(ys)))
+    th = [bench.default_theta(q) for q in probs]
+    b.set_theta(torch.from_numpy(b.pack(th)))
+    nll, g = b.nll_grad()
+    torch.cuda.synchronize()
+    nll, g = nll.cpu().numpy(), g.cpu().numpy()
+    for f in (256, 300, 401, 511):
+        q = probs[f]
+        assert q.kind == "dnet"
+        out, ge, gW, gv, gs = spectral.nll_grad_equal(q.kind, q.gen, q.shift, q.m, ys[f], *th[f])
+        assert abs(nll[f] - out["nll"]) <= 1e-5 * abs(out["nll"]), (f, nll[f], out["nll"])
+        gref = 0.5 * np.concatenate([ge, np.ravel(gW), gv, [gs]])
+        o0, o1 = b.param_offsets[f], b.param_offsets[f + 1]
+        # FP32 transforms of up to 29 columns of 2^16 entries: normwise 1e-3 (the eta entries are sums
+        # over C n terms of FP32-transformed adjoint weights; 1.8e-4 measured at T = 8)
+        err = np.abs(g[o0:o1] - gref).max() / np.abs(gref).max()
+        assert err <= 1e-3, (f, err)
+    b.close()
+
+
+# ----------------------------------------------------------------------------- SI smoothness
+
+@pytest.mark.parametrize("alpha", [1, 3, 4])
+@pytest.mark.parametrize("m", [(6, 6), (6, 4, 3)])
+def test_si_smoothness_nll_grad_posterior_vs_dense(alpha, m):
+    """Lattice handles with the SI kernel of smoothness 1, 3, 4 (Eq. 2.5): equal sizes (fused
+    kernels) and nested sizes (tree solver), against the dense oracle with the same kernel."""
+    p = inputs.make_problem("lattice", 2, m, seed=51, eta=0.6, v=0.2, sigma2=1e-4)
+    X = _points_oracle(p)
+    y = inputs.synth_y(p, X)
+    ref, g_eta, g_W, g_v, g_s2 = dense.nll_grad(p.kind, X, y, p.eta, p.W, p.v, p.sigma2, alpha)
+    model = _model(p, "fp64")
+    model.set_smoothness(alpha)
+    model.set_y(torch.from_numpy(y))
+    out, tau, ge, gW, gv, gs = model.nll_grad(p.eta, p.W, p.v, p.sigma2)
+    model.sync()
+    assert abs(out[0].item() - ref["nll"]) <= 1e-8 * abs(ref["nll"]), (out[0].item(), ref["nll"])
+    gref = 0.5 * np.concatenate([g_eta, g_W.ravel(), g_v, [g_s2]])
+    got = np.concatenate([ge.cpu().numpy(), gW.cpu().numpy().ravel(), gv.cpu().numpy(), gs.cpu().numpy()])
+    assert np.allclose(got, gref, rtol=1e-6, atol=1e-8 * np.abs(gref).max())
+    Xq, xq, tq = inputs.query_points(9, 2, seed=8, tasks=len(m))
+    mean_ref, var_ref, prior = dense.posterior(p.kind, X, y, p.eta, p.W, p.v, p.sigma2, Xq, tq, alpha)
+    equal = len(set(m)) == 1
+    mean, var = model.posterior(p.eta, p.W, p.v, p.sigma2, torch.from_numpy(xq), torch.from_numpy(tq), variance=equal)
+    model.sync()
+    assert np.allclose(mean.cpu().numpy(), mean_ref, rtol=0, atol=1e-8 * prior.max())
+    if equal:
+        assert np.allclose(var.cpu().numpy(), var_ref, rtol=0, atol=1e-8 * prior.max())
+
+
+def test_smoothness_argument_checks():
+    from paper_2603_16014_gb300._lib import MTGPError
+    p = inputs.make_problem("dnet", 2, (5, 5), seed=3)
+    model = _model(p, "fp64")
+    with pytest.raises(MTGPError) as ei:
+        model.set_smoothness(3)
+    assert ei.value.code == 5
+    q = inputs.make_problem("lattice", 2, (5, 5), seed=3)
+    mq = _model(q, "fp64")
+    with pytest.raises(MTGPError) as ei:
+        mq.set_smoothness(7)
+    assert ei.value.code == 1

@@ -75,6 +75,25 @@ def test_mlp_forward_matches_oracle_within_bf16_bound():
     net.close()
 
 
+def test_mlp_forward_bench_shape_within_bf16_bound():
+    """The proposal network's own shape (258-256-256-256-37) at its largest batch (1024 rows)."""
+    from paper_2603_16014_gb300.proposal import MLP, WIDTHS
+    rng = np.random.default_rng(7)
+    widths = list(WIDTHS)
+    Ws, bs = _net(rng, widths)
+    x = _bf(rng.standard_normal((1024, widths[0])))
+    out, acts, pre = omlp.forward(x, Ws, bs)
+    assert min(np.abs(z).min() for z in pre[:-1]) > 0.25
+    net = MLP(widths, max_batch=1024)
+    net.set_params(_pack(Ws, bs))
+    y = net.forward(torch.from_numpy(x.astype(np.float32))).cpu().numpy().astype(np.float64)
+    bound = _fwd_bound(Ws, bs, acts)[-1]
+    pick = np.random.default_rng(8).integers(0, 1024, 64)
+    assert np.all(np.abs(y - out) <= 2 * bound + 1e-7), np.max(np.abs(y - out) / (bound + 1e-7))
+    assert np.all(np.abs(y[pick] - out[pick]) <= 2 * bound[pick] + 1e-7)
+    net.close()
+
+
 def test_mlp_gradients_match_oracle_within_bound():
     from paper_2603_16014_gb300.proposal import MLP
     rng = np.random.default_rng(1)

@@ -198,3 +198,6 @@ def test_posterior_mean_equal_matches_dense(kind):
     mean_ref, _, prior = dense.posterior(p.kind, X, y, p.eta, p.W, p.v, p.sigma2, Xq, tq)
     mean = spectral.posterior_mean_equal(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2, Xq, tq)
     assert np.allclose(mean, mean_ref, rtol=0, atol=1e-9 * prior.max())
+    _, var_ref, _ = dense.posterior(p.kind, X, y, p.eta, p.W, p.v, p.sigma2, Xq, tq)
+    var = spectral.posterior_var_equal(p.kind, p.gen, p.shift, p.m, p.eta, p.W, p.v, p.sigma2, Xq, tq)
+    assert np.allclose(var, var_ref, rtol=0, atol=1e-9 * prior.max())
