@@ -34,7 +34,14 @@ def gram(kind, X_tasks, eta, R, sigma2, alpha=2):
         for u in range(T):
             Q = product_kernel(kind, X_tasks[t][:, None, :], X_tasks[u][None, :, :], eta, alpha=alpha)
             K[off[t]:off[t + 1], off[u]:off[u + 1]] = R[t, u] * Q
-    K[np.diag_indices_from(K)] += sigma2
+    # noise: one variance sigma2, or one per task (xi_t of Eq. 3.1's data model) when given T values
+    sig = np.asarray(sigma2, dtype=np.float64)
+    if sig.ndim == 0:
+        K[np.diag_indices_from(K)] += float(sig)
+    else:
+        for t in range(T):
+            idx = np.arange(off[t], off[t + 1])
+            K[idx, idx] += sig[t]
     return K
 
 
@@ -88,7 +95,7 @@ def gcv(kind, X_tasks, y, eta, W, v, sigma2):
     return dict(L=num / tr ** 2, num=num, trace=tr, tau=tau)
 
 
-def _param_contractions(kind, X_tasks, eta, W, R, K, contract, alpha=2):
+def _param_contractions(kind, X_tasks, eta, W, R, K, contract, alpha=2, sigma2_shape=0.0):
     """contract(dK~/dtheta) for every parameter: eta (d), W (T x s), v (T), sigma2, with the dense
     derivatives of K~ written out (see nll_grad)."""
     T = len(X_tasks)
@@ -133,7 +140,15 @@ def _param_contractions(kind, X_tasks, eta, W, R, K, contract, alpha=2):
         dR = np.zeros((T, T))
         dR[t, t] = 1.0
         g_v[t] = contract(blockwise(dR))
-    g_s2 = contract(np.eye(K.shape[0]))
+    if np.ndim(sigma2_shape) == 0:
+        g_s2 = contract(np.eye(K.shape[0]))
+    else:
+        g_s2 = np.zeros(T)
+        for t in range(T):
+            dK = np.zeros_like(K)
+            idx = np.arange(off[t], off[t + 1])
+            dK[idx, idx] = 1.0
+            g_s2[t] = contract(dK)
     return g_eta, g_W, g_v, g_s2
 
 
@@ -160,7 +175,7 @@ def gcv_grad(kind, X_tasks, y, eta, W, v, sigma2):
     def contract(dK):
         return float(np.sum(G * dK))
 
-    g_eta, g_W, g_v, g_s2 = _param_contractions(kind, X_tasks, eta, W, R, K, contract)
+    g_eta, g_W, g_v, g_s2 = _param_contractions(kind, X_tasks, eta, W, R, K, contract, 2, sigma2)
     return out, g_eta, g_W, g_v, g_s2
 
 
@@ -184,7 +199,7 @@ def nll_grad(kind, X_tasks, y, eta, W, v, sigma2, alpha=2):
     def contract(dK):
         return float(np.sum(Kinv * dK) - a @ dK @ a)
 
-    g_eta, g_W, g_v, g_s2 = _param_contractions(kind, X_tasks, eta, W, R, K, contract, alpha)
+    g_eta, g_W, g_v, g_s2 = _param_contractions(kind, X_tasks, eta, W, R, K, contract, alpha, sigma2)
     return out, g_eta, g_W, g_v, g_s2
 
 

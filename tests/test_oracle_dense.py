@@ -135,3 +135,26 @@ def test_gradient_other_si_smoothness_matches_central_differences(alpha):
     assert abs(fd - g_W[1, 0]) < 1e-5 * (1 + abs(g_W[1, 0]))
     # the smoothness changes the kernel: alpha = 2 gives a different loss
     assert abs(out["L"] - dense.nll("lattice", X, y, p.eta, p.W, p.v, p.sigma2)["L"]) > 1e-6
+
+
+def test_per_task_noise_reduces_to_scalar_and_matches_differences():
+    p = inputs.make_problem("dnet", 2, (4, 3, 3), seed=23, eta=0.7, v=0.2, sigma2=1e-3, s=2)
+    X, y = _setup(p)
+    xi = np.full(p.T, p.sigma2)
+    a = dense.nll_grad("dnet", X, y, p.eta, p.W, p.v, p.sigma2)
+    b = dense.nll_grad("dnet", X, y, p.eta, p.W, p.v, xi)
+    assert b[0]["L"] == pytest.approx(a[0]["L"], rel=1e-13)
+    assert np.sum(b[4]) == pytest.approx(a[4], rel=1e-11)          # per-task traces add up
+    xi = np.array([1e-3, 3e-3, 5e-4])
+    out, ge, gW, gv, gs = dense.nll_grad("dnet", X, y, p.eta, p.W, p.v, xi)
+    for t in range(p.T):
+        h = 1e-4 * xi[t]
+        e = np.zeros(p.T)
+        e[t] = h
+        fd = (dense.nll("dnet", X, y, p.eta, p.W, p.v, xi + e)["L"] - dense.nll("dnet", X, y, p.eta, p.W, p.v, xi - e)["L"]) / (2 * h)
+        assert fd == pytest.approx(gs[t], rel=1e-5)
+    g = dense.gcv_grad("dnet", X, y, p.eta, p.W, p.v, xi)
+    h = 1e-4 * xi[1]
+    e = np.array([0.0, h, 0.0])
+    fd = (dense.gcv("dnet", X, y, p.eta, p.W, p.v, xi + e)["L"] - dense.gcv("dnet", X, y, p.eta, p.W, p.v, xi - e)["L"]) / (2 * h)
+    assert fd == pytest.approx(g[4][1], rel=1e-5)
