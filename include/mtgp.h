@@ -53,6 +53,9 @@ enum {
 
 enum { MTGP_LATTICE = 0, MTGP_DNET = 1 };
 enum { MTGP_FP64 = 0, MTGP_FP32_TRANSFORM = 1 };
+/* OR-ed into mtgp_create's precision: one noise variance per task (xi_t of Sec. 3.1's data model)
+ * instead of a shared sigma2; sigma2 and g_sigma2 then hold T values in caller task order. */
+enum { MTGP_NOISE_PER_TASK = 16 };
 
 /* Limits of this build. */
 #define MTGP_MAX_TASKS 8
@@ -73,7 +76,9 @@ enum { MTGP_FP64 = 0, MTGP_FP32_TRANSFORM = 1 };
  *   shift     host, T x d words (caller task order): lattice shift Delta_t (added mod 2^32) or
  *             digital shift (XOR).
  *   precision MTGP_FP64, or MTGP_FP32_TRANSFORM (kernel columns and their transforms in FP32;
- *             per-frequency factorisations, log-determinants and y transforms stay FP64).
+ *             per-frequency factorisations, log-determinants and y transforms stay FP64), optionally
+ *             OR MTGP_NOISE_PER_TASK (per-task noise variances; such handles use the general kernels,
+ *             not the fused equal-size ones, and are refused by the batch and no-allocation calls).
  * Allocates the handle's device workspace on the current device.
  */
 int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32_t* gen,
@@ -99,7 +104,8 @@ int mtgp_set_y(mtgp_t* h, const double* y, cudaStream_t stream);
  * mtgp_nll -- MLE loss at theta (Eq. 3.3) with tau profiled at its optimum (Eq. 3.4,
  * Theorem "fast MTGP computations" item 4).
  *   eta     d doubles (eta_j >= 0), W T x s doubles row-major (caller task order), 1 <= s <= T,
- *   v       T doubles > 0, sigma2 one double > 0 -- all device pointers.
+ *   v       T doubles > 0, sigma2 one double > 0 (T doubles, caller order, for a handle created
+ *           with MTGP_NOISE_PER_TASK) -- all device pointers.
  *   out     3 doubles: [0] NLL = (L + N log 2 pi) / 2, [1] quad = r^T K~^-1 r, [2] log|K~|.
  *   tau     T doubles (caller order) or NULL: the optimal means.
  */
@@ -108,7 +114,8 @@ int mtgp_nll(mtgp_t* h, const double* eta, const double* W, int s, const double*
 
 /*
  * mtgp_nll_grad -- as mtgp_nll plus the gradient of the NLL (= half the gradient of L) with
- * respect to eta (d), W (T x s), v (T) and sigma2 (1), at the optimal tau (tau minimises L, so
+ * respect to eta (d), W (T x s), v (T) and sigma2 (1, or T with MTGP_NOISE_PER_TASK), at the
+ * optimal tau (tau minimises L, so
  * its own dependence on theta does not enter).  Gradient outputs may not be NULL.
  */
 int mtgp_nll_grad(mtgp_t* h, const double* eta, const double* W, int s, const double* v,

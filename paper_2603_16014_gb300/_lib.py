@@ -20,6 +20,7 @@ ERRORS = {
 }
 LATTICE, DNET = 0, 1
 FP64, FP32_TRANSFORM = 0, 1
+NOISE_PER_TASK = 16
 
 _p = ctypes.c_void_p
 _i = ctypes.c_int

@@ -144,7 +144,9 @@ struct LogAcc {
 template <int T, bool CPLX>
 __device__ __forceinline__ void solve_freq(Vt<CPLX> (&mu)[T][T], const Vt<CPLX> (&rh)[T], const double* sR, double sig,
                                            bool clamp, bool grad, LogAcc& lacc, double* acc, Vt<CPLX> (&w)[T][T],
-                                           Vt<CPLX> (&al)[T], bool want_alpha, int& bad) {
+                                           Vt<CPLX> (&al)[T], bool want_alpha, int& bad,
+                                           const double* sigv = nullptr) {
+    // sigv (optional): per-task noise (sorted order); its gradient traces go to acc[3 + T(T+1)/2 + t]
     using V = Vt<CPLX>;
     double mu0 = creal(mu[0][0]);
     double ind0 = 1.0;
@@ -157,7 +159,7 @@ __device__ __forceinline__ void solve_freq(Vt<CPLX> (&mu)[T][T], const Vt<CPLX> 
     double D[T], iD[T];
 #pragma unroll
     for (int i = 0; i < T; ++i) {
-        D[i] = fma(sR[i * T + i], mu0, sig);
+        D[i] = fma(sR[i * T + i], mu0, sigv ? sigv[i] : sig);
 #pragma unroll
         for (int j = 0; j < i; ++j) S[i][j] = vscale(cconj(mu[j][i]), sR[j * T + i]);
     }
@@ -228,6 +230,7 @@ __device__ __forceinline__ void solve_freq(Vt<CPLX> (&mu)[T][T], const Vt<CPLX> 
             if (uu == t) {
                 double gd = creal(Zl[t][t]) - cabs2(al[t]);
                 acc[2] += gd;
+                if (sigv) acc[3 + T * (T + 1) / 2 + t] += gd;
                 acc[q] = fma(gd, mu0, acc[q]);
                 wdiag = fma(sR[t * T + t], gd, wdiag);
             } else {

@@ -883,6 +883,7 @@ size_t fused_smem(int phase, int T, int C, int m, int a, bool fp32, bool cplx) {
 int fused_threads_ac(int a, int d) { return threads_ac(a, d); }
 
 bool fused_supported(const Handle* h) {
+    if (h->noise_pt) return false;  // the fused solve takes one shared noise variance
     int a, lgL;
     return plan(h, &a, &lgL);
 }

@@ -215,9 +215,9 @@ __global__ void __launch_bounds__(kThreads)
 k_var_factor(const void* spec, PostParams pp, VarParams p, ThetaPtrs th, double* __restrict__ fac) {
     using V = Vt<CPLX>;
     __shared__ double sR[T * T];
-    __shared__ double s_sig;
+    __shared__ double s_sigv[T];
     load_R_post(sR, pp, th);
-    if (threadIdx.x == 0) s_sig = th.sigma2[0];
+    if (threadIdx.x < T) s_sigv[threadIdx.x] = noise_of(th, pp.order, threadIdx.x);
     __syncthreads();
     const long long n = p.n;
     V* facL = reinterpret_cast<V*>(fac + (long long)T * n);
@@ -232,7 +232,7 @@ k_var_factor(const void* spec, PostParams pp, VarParams p, ThetaPtrs th, double*
         V lam[T][T];
 #pragma unroll
         for (int i = 0; i < T; ++i) {
-            lam[i][i] = cfromreal<V>(sR[i * T + i] * mu0 + s_sig);
+            lam[i][i] = cfromreal<V>(sR[i * T + i] * mu0 + s_sigv[i]);
 #pragma unroll
             for (int j = 0; j < i; ++j) lam[i][j] = vscale(cconj(mu[j][i]), sR[j * T + i]);
         }

@@ -27,6 +27,7 @@ __device__ __forceinline__ void store_spec(void* p, long long i, Vt<CPLX> v) { s
 struct SolveParams {
     int T, s, nT;
     int grad, clamp, store_alpha, gcv;  // gcv: 1 loss value, 2 gradient (needs gcv_ab)
+    int pt;                             // per-task noise
     const double* gcv_ab;               // [A, B] of the GCV loss (device), for gcv = 2
     long long n[MTGP_TMAX];
     int order[MTGP_TMAX];
@@ -55,7 +56,8 @@ constexpr int kEqThreads = 128;
 // into adjoint weights exactly as the MLE path does with G = Z - alpha alpha^H.
 template <int T, bool CPLX>
 __device__ void gcv_grad_freq(Vt<CPLX> (&mu)[T][T], const Vt<CPLX> (&rh)[T], const double* sR, double sig, bool clamp,
-                              double c1, double c2, double* acc, Vt<CPLX> (&w)[T][T], int& bad) {
+                              double c1, double c2, double* acc, Vt<CPLX> (&w)[T][T], int& bad,
+                              const double* sigv) {
     using V = Vt<CPLX>;
     double mu0 = creal(mu[0][0]);
     double ind0 = 1.0;
@@ -66,7 +68,7 @@ __device__ void gcv_grad_freq(Vt<CPLX> (&mu)[T][T], const Vt<CPLX> (&rh)[T], con
     V S[T][T], L[T][T];
     double D[T], iD[T];
     for (int i = 0; i < T; ++i) {
-        D[i] = sR[i * T + i] * mu0 + sig;
+        D[i] = sR[i * T + i] * mu0 + (sigv ? sigv[i] : sig);
         for (int j = 0; j < i; ++j) S[i][j] = vscale(cconj(mu[j][i]), sR[j * T + i]);
     }
     for (int k = 0; k < T; ++k) {
@@ -117,6 +119,7 @@ __device__ void gcv_grad_freq(Vt<CPLX> (&mu)[T][T], const Vt<CPLX> (&rh)[T], con
             if (uu == t) {
                 const double gd = creal(g);
                 acc[2] += gd;
+                if (sigv) acc[3 + T * (T + 1) / 2 + t] += gd;
                 acc[q] = fma(gd, mu0, acc[q]);
                 wdiag = fma(sR[t * T + t], gd, wdiag);
             } else {
@@ -135,18 +138,22 @@ k_solve_equal(const void* spec, void* wgt, const double* yhat, SolveParams p, Th
               double* alpha_out, int* status) {
     using V = Vt<CPLX>;
     constexpr int NG = T * (T + 1) / 2;
-    constexpr int NQ = 3 + NG;
+    constexpr int NQX = 3 + NG + T;          // with per-task noise traces
+    const int NQ = 3 + NG + (p.pt ? T : 0);
     __shared__ double sR[T * T];
     __shared__ double s_sig;
-    __shared__ double s_red[kEqThreads / 32][NQ];
+    __shared__ double s_sigv[T];
+    __shared__ double s_red[kEqThreads / 32][NQX];
     load_R(sR, p, th);
     if (threadIdx.x == 0) s_sig = th.sigma2[0];
+    if (threadIdx.x < T) s_sigv[threadIdx.x] = noise_of(th, p.order, threadIdx.x);
     __syncthreads();
     const double sig = s_sig;
+    const double* sigv = p.pt ? s_sigv : nullptr;
     const long long n = p.n[0];
-    double acc[NQ];
+    double acc[NQX];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+    for (int q = 0; q < NQX; ++q) acc[q] = 0.0;
     LogAcc lacc;
     lacc.init();
     int bad = 0;
@@ -160,7 +167,8 @@ k_solve_equal(const void* spec, void* wgt, const double* yhat, SolveParams p, Th
         }
         if (p.gcv == 2) {
             const double A = p.gcv_ab[0], B = p.gcv_ab[1];
-            gcv_grad_freq<T, CPLX>(mu, rh, sR, sig, p.clamp != 0, 1.0 / (B * B), 2.0 * A / (B * B * B), acc, w, bad);
+            gcv_grad_freq<T, CPLX>(mu, rh, sR, sig, p.clamp != 0, 1.0 / (B * B), 2.0 * A / (B * B * B), acc, w, bad,
+                                   sigv);
 #pragma unroll
             for (int t = 0; t < T; ++t)
 #pragma unroll
@@ -171,10 +179,10 @@ k_solve_equal(const void* spec, void* wgt, const double* yhat, SolveParams p, Th
         if (p.gcv) {
             // ||Lambda(f)^-1 rhat(f)||^2 and trace Lambda(f)^-1: the gradient pass yields
             // sum_t G_tt = trace Z - ||alpha||^2 in its third accumulator
-            double scr[NQ];
+            double scr[NQX];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) scr[q] = 0.0;
-            solve_freq<T, CPLX>(mu, rh, sR, sig, p.clamp != 0, true, lacc, scr, w, al, true, bad);
+            for (int q = 0; q < NQX; ++q) scr[q] = 0.0;
+            solve_freq<T, CPLX>(mu, rh, sR, sig, p.clamp != 0, true, lacc, scr, w, al, true, bad, sigv);
             double a2 = 0.0;
 #pragma unroll
             for (int t = 0; t < T; ++t) a2 += cabs2(al[t]);
@@ -183,7 +191,7 @@ k_solve_equal(const void* spec, void* wgt, const double* yhat, SolveParams p, Th
             acc[3] += scr[2] + a2;
             continue;
         }
-        solve_freq<T, CPLX>(mu, rh, sR, sig, p.clamp != 0, p.grad != 0, lacc, acc, w, al, p.store_alpha != 0, bad);
+        solve_freq<T, CPLX>(mu, rh, sR, sig, p.clamp != 0, p.grad != 0, lacc, acc, w, al, p.store_alpha != 0, bad, sigv);
         if (p.store_alpha) {
 #pragma unroll
             for (int k = 0; k < T; ++k) st<CPLX>(alpha_out, p.yoff[k] + f, al[k]);
@@ -200,7 +208,8 @@ k_solve_equal(const void* spec, void* wgt, const double* yhat, SolveParams p, Th
     if (bad) set_status(status, ST_NOT_PD);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
+    for (int q = 0; q < NQX; ++q) {
+        if (q >= NQ) break;
         double v = acc[q];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) s_red[warp][q] = v;
@@ -223,7 +232,7 @@ constexpr int kTreeCW = 8;
 constexpr int kTreeSlots = kTreeThreads / kTreeCW;
 
 struct TreeParams {
-    int T, s, grad, clamp, gcv;
+    int T, s, grad, clamp, gcv, pt;
     double* pi_out;  // when set: Pi = E K~^-1 E^T (sorted order, T x T) from class 0
     long long nT;
     long long n[MTGP_TMAX];
@@ -365,13 +374,13 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
     using V = Vt<CPLX>;
     const int T = p.T;
     const int NG = T * (T + 1) / 2;
-    const int NQ = 3 + NG;
+    const int NQ = 3 + NG + (p.pt ? T : 0);
     __shared__ double sR[MTGP_TMAX * MTGP_TMAX];
-    __shared__ double s_sig;
+    __shared__ double s_sigv[MTGP_TMAX];
     __shared__ double s_tau[MTGP_TMAX];
-    __shared__ double s_red[kTreeWarps][3 + MTGP_MAX_COLS];
+    __shared__ double s_red[kTreeWarps][3 + MTGP_MAX_COLS + MTGP_TMAX];
     load_R_tree(sR, p, th);
-    if (threadIdx.x == 0) s_sig = th.sigma2[0];
+    if (threadIdx.x < T) s_sigv[threadIdx.x] = noise_of(th, p.order, threadIdx.x);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int slot = warp * (32 / kTreeCW) + lane / kTreeCW;
@@ -380,7 +389,7 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
     const long long rho = (long long)blockIdx.x * kTreeCW + cls;
     const bool act = rho < nT;
     __shared__ V s_part[kTreeCW][kTreeSlots][MTGP_TMAX];  // partial sums of split reductions
-    double acc[3 + MTGP_MAX_COLS];
+    double acc[3 + MTGP_MAX_COLS + MTGP_TMAX];
     for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
     int bad = 0;
 
@@ -397,7 +406,7 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
                 if (t == u) {
                     double m0 = creal(mu);
                     if (p.clamp && m0 < 0.0) m0 = 0.0;
-                    val = cfromreal<V>(sR[t * T + t] * m0 + s_sig);
+                    val = cfromreal<V>(sR[t * T + t] * m0 + s_sigv[t]);
                 } else {
                     val = vscale(mu, sc);
                 }
@@ -623,6 +632,7 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
                             ind = 0.0;
                         }
                         acc[2] += gd;
+                        if (p.pt) acc[3 + NG + t] += gd;
                         acc[q] += gd * m0;
                         store_spec<S, CPLX>(wgt, p.po[t][u] + f, cfromreal<V>(sR[t * T + t] * gd * ind));
                     } else {
@@ -650,7 +660,7 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
 // --------------------------------------------------------------------------- finalize
 
 struct FinParams {
-    int T, d, s, equal, cplx, NQ, nsolve, neta, grad, gcv;
+    int T, d, s, equal, cplx, NQ, nsolve, neta, grad, gcv, pt;
     long long N;
     long long n0;
     int order[MTGP_TMAX];
@@ -661,7 +671,7 @@ struct FinParams {
 __global__ void k_finalize(const double* partials, const double* eta_partials, const double* yhat,
                            const double* tau_sorted, FinParams p, ThetaPtrs th, double* out, double* tau,
                            double* g_eta, double* g_W, double* g_v, double* g_s2) {
-    __shared__ double tot[3 + MTGP_MAX_COLS];
+    __shared__ double tot[3 + MTGP_MAX_COLS + MTGP_TMAX];
     __shared__ double etot[MTGP_MAX_DIM];
     for (int q = threadIdx.x; q < p.NQ; q += blockDim.x) {
         double v = 0.0;
@@ -702,7 +712,11 @@ __global__ void k_finalize(const double* partials, const double* eta_partials, c
     const int T = p.T;
     // MLE: gradients of NLL = L / 2; GCV: gradients of the loss itself
     const double sc = (p.gcv == 2) ? 2.0 : 1.0;
-    g_s2[0] = 0.5 * sc * tot[2];
+    if (p.pt) {
+        for (int tc = 0; tc < T; ++tc) g_s2[tc] = 0.5 * sc * tot[3 + T * (T + 1) / 2 + p.rank[tc]];
+    } else {
+        g_s2[0] = 0.5 * sc * tot[2];
+    }
     for (int j = 0; j < p.d; ++j) g_eta[j] = 0.5 * sc * etot[j];
     for (int tc = 0; tc < T; ++tc) {
         int t = p.rank[tc];
@@ -759,6 +773,7 @@ void launch_solve_equal(const Handle* h, ThetaPtrs th, bool grad, double* partia
     sp.grad = (grad && !gcv) ? 1 : 0;
     sp.gcv = gcv;
     sp.gcv_ab = gcv_ab;
+    sp.pt = h->noise_pt ? 1 : 0;
     sp.clamp = h->fp32 ? 1 : 0;
     sp.store_alpha = 1;
     for (int t = 0; t < MTGP_TMAX; ++t) {
@@ -783,6 +798,7 @@ void launch_solve_tree(const Handle* h, ThetaPtrs th, bool grad, double* partial
     tp.s = th.s;
     tp.grad = (grad && !gcv) ? 1 : 0;
     tp.gcv = gcv ? 1 : 0;
+    tp.pt = h->noise_pt ? 1 : 0;
     tp.pi_out = h->pi_buf;
     tp.clamp = h->fp32 ? 1 : 0;
     tp.nT = h->n[h->T - 1];
@@ -813,7 +829,8 @@ void launch_finalize(const Handle* h, ThetaPtrs th, bool grad, const double* par
     fp.s = th.s;
     fp.equal = h->equal ? 1 : 0;
     fp.cplx = h->cplx ? 1 : 0;
-    fp.NQ = 3 + h->T * (h->T + 1) / 2;
+    fp.NQ = solve_nq(h);
+    fp.pt = h->noise_pt ? 1 : 0;
     fp.nsolve = nsolve;
     fp.neta = neta;
     fp.grad = grad ? 1 : 0;

@@ -82,7 +82,8 @@ __global__ void k_check_theta(ThetaPtrs th, int d, int T, int* status) {
         if (!isfinite(th.W[e])) bad = 1;
     for (int t = threadIdx.x; t < T; t += blockDim.x)
         if (!isfinite(th.v[t]) || th.v[t] < 0.0) bad = 1;
-    if (threadIdx.x == 0 && (!isfinite(th.sigma2[0]) || th.sigma2[0] < 0.0)) bad = 1;
+    for (int t = threadIdx.x; t < (th.nsig > 1 ? th.nsig : 1); t += blockDim.x)
+        if (!isfinite(th.sigma2[t]) || th.sigma2[t] < 0.0) bad = 1;
     if (bad) atomicOr(status, ST_NUMERIC);
 }
 
@@ -119,9 +120,9 @@ __global__ void k_cubature(CubParams p, ThetaPtrs th, const void* spec, const do
     if (p.equal) {
         // Lambda(0) in sorted order from the transformed first columns at frequency 0
         double L[MTGP_TMAX][MTGP_TMAX];
-        const double sig = th.sigma2[0];
         for (int t = 0; t < T; ++t)
             for (int u = t; u < T; ++u) {
+                const double sig = noise_of(th, p.order, t);
                 const long long e = p.coloff[p.colidx[t][u]];
                 double mu0;
                 if (p.fp32) mu0 = p.cplx ? (double)((const float*)spec)[2 * e] : (double)((const float*)spec)[e];
@@ -244,7 +245,7 @@ int run_nll(Handle* h, ThetaPtrs th, bool grad, double* out, double* tau, double
         mtgp_prof_end(h, st);
         nsolve = solve_tree_blocks(h);
     }
-    const int NQ = 3 + h->T * (h->T + 1) / 2;
+    const int NQ = solve_nq(h);
     double* eta_part = h->partials + (long long)nsolve * NQ;
     int neta = 0;
     if (grad) {
@@ -284,8 +285,10 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
     if (d < 1 || d > MTGP_MAX_DIM) return fail(MTGP_ERR_INVALID_ARG, "d out of range [1, MTGP_MAX_DIM]");
     if (T < 1 || T > MTGP_MAX_TASKS) return fail(MTGP_ERR_INVALID_ARG, "T out of range [1, MTGP_MAX_TASKS]");
     if (!m || !gen || !shift) return fail(MTGP_ERR_INVALID_ARG, "m, gen and shift must be host arrays");
+    const bool noise_pt = (precision & MTGP_NOISE_PER_TASK) != 0;
+    precision &= ~MTGP_NOISE_PER_TASK;
     if (precision != MTGP_FP64 && precision != MTGP_FP32_TRANSFORM)
-        return fail(MTGP_ERR_INVALID_ARG, "precision must be MTGP_FP64 or MTGP_FP32_TRANSFORM");
+        return fail(MTGP_ERR_INVALID_ARG, "precision must be MTGP_FP64 or MTGP_FP32_TRANSFORM (optionally | MTGP_NOISE_PER_TASK)");
     int mmax = 0;
     for (int t = 0; t < T; ++t) {
         if (m[t] < 0 || m[t] > MTGP_MAX_M) return fail(MTGP_ERR_INVALID_ARG, "m[t] out of range [0, MTGP_MAX_M]");
@@ -298,6 +301,7 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
     Handle* h = &hs->h;
     std::memset(h, 0, sizeof(Handle));
     h->smooth = 2;
+    h->noise_pt = noise_pt;
     h->kind = kind;
     h->d = d;
     h->T = T;
@@ -404,7 +408,7 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
     AL(h->alpha, (size_t)h->N * vs);
     AL(h->tau, (size_t)MTGP_TMAX);
     {
-        const int NQ = 3 + T * (T + 1) / 2;
+        const int NQ = solve_nq(h);
         long long nsolve = h->equal ? solve_equal_blocks(h) : solve_tree_blocks(h);
         h->partials_len = nsolve * NQ + (long long)eta_grad_blocks(h) * d;
         long long fl = fused_partials_len(h);
@@ -493,7 +497,7 @@ int mtgp_nll(mtgp_t* hs, const double* eta, const double* W, int s, const double
     int rc = validate_theta(h, eta, W, s, v, sigma2);
     if (rc) return rc;
     if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
-    ThetaPtrs th{eta, W, s, v, sigma2};
+    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1};
     return run_nll(h, th, false, out, tau, nullptr, nullptr, nullptr, nullptr, st);
 }
 
@@ -506,7 +510,7 @@ int mtgp_nll_grad(mtgp_t* hs, const double* eta, const double* W, int s, const d
     int rc = validate_theta(h, eta, W, s, v, sigma2);
     if (rc) return rc;
     if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
-    ThetaPtrs th{eta, W, s, v, sigma2};
+    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1};
     return run_nll(h, th, true, out, tau, g_eta, g_W, g_v, g_sigma2, st);
 }
 
@@ -559,7 +563,7 @@ int mtgp_cubature(mtgp_t* hs, const double* eta, const double* W, int s, const d
         CK(cudaMalloc(&h->pi_buf, sizeof(double) * MTGP_TMAX * MTGP_TMAX));
         h->ws_bytes += (long long)sizeof(double) * MTGP_TMAX * MTGP_TMAX;
     }
-    ThetaPtrs th{eta, W, s, v, sigma2};
+    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1};
     // the MLE solve leaves alpha, tau (sorted), the transformed spectra (equal sizes) or Pi (nested)
     rc = run_nll(h, th, false, h->out_tmp, nullptr, nullptr, nullptr, nullptr, nullptr, st, true);
     if (rc) return rc;
@@ -594,7 +598,7 @@ static int run_gcv_grad(Handle* h, ThetaPtrs th, double* out, double* tau, doubl
     launch_solve_equal(h, th, true, h->partials, st, 2, out + 1);
     mtgp_prof_end(h, st);
     const int nsolve = solve_equal_blocks(h);
-    const int NQ = 3 + h->T * (h->T + 1) / 2;
+    const int NQ = solve_nq(h);
     double* eta_part = h->partials + (long long)nsolve * NQ;
     mtgp_prof_begin(h, "xform_dif", st);
     for (int g = 0; g < h->ngroups; ++g)
@@ -621,7 +625,7 @@ int mtgp_gcv_grad(mtgp_t* hs, const double* eta, const double* W, int s, const d
     int rc = validate_theta(h, eta, W, s, v, sigma2);
     if (rc) return rc;
     if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
-    ThetaPtrs th{eta, W, s, v, sigma2};
+    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1};
     return run_gcv_grad(h, th, out, tau, g_eta, g_W, g_v, g_sigma2, st);
 }
 
@@ -632,7 +636,7 @@ int mtgp_gcv(mtgp_t* hs, const double* eta, const double* W, int s, const double
     int rc = validate_theta(h, eta, W, s, v, sigma2);
     if (rc) return rc;
     if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
-    ThetaPtrs th{eta, W, s, v, sigma2};
+    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1};
     return run_gcv(h, th, out, tau, st);
 }
 
@@ -646,7 +650,7 @@ int mtgp_posterior(mtgp_t* hs, const double* eta, const double* W, int s, const 
     if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
     if (var && !h->equal) return fail(MTGP_ERR_UNSUPPORTED, "posterior variance needs equal task sizes in this build");
     if (nq == 0) return MTGP_OK;
-    ThetaPtrs th{eta, W, s, v, sigma2};
+    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1};
     // the solve leaves alpha = Lambda^-1 rhat and tau in the workspace
     rc = run_nll(h, th, false, h->out_tmp, nullptr, nullptr, nullptr, nullptr, nullptr, st, true);
     if (rc) return rc;

@@ -448,6 +448,8 @@ int mtgp_batch_create(mtgp_batch_t** out, int nfits, const int* kind, const int*
     if (nfits < 1 || !kind || !d || !T || !m || !gen || !gen_cols || !shift)
         return bfail(MTGP_ERR_INVALID_ARG, "nfits < 1 or NULL host array");
     if (s < 1) return bfail(MTGP_ERR_INVALID_ARG, "s must be >= 1");
+    if (precision & MTGP_NOISE_PER_TASK)
+        return bfail(MTGP_ERR_UNSUPPORTED, "batched fits take one noise variance per fit");
     for (int f = 0; f < nfits; ++f)
         if (T[f] < s) return bfail(MTGP_ERR_INVALID_ARG, "every fit needs T >= s");
     auto* b = new mtgp_batch_s();

@@ -185,7 +185,13 @@ struct ThetaPtrs {
     int s;
     const double* v;
     const double* sigma2;
+    int nsig;  // noise values: 1 (shared sigma2) or T (per task, caller order); 0 reads as 1
 };
+
+// noise variance of sorted task t
+__device__ __forceinline__ double noise_of(const ThetaPtrs& th, const int* order, int t) {
+    return th.nsig > 1 ? th.sigma2[order[t]] : th.sigma2[0];
+}
 
 // k_columns.cu
 void launch_colgen(const Handle* h, const double* eta, void* out, cudaStream_t st);
@@ -301,7 +307,12 @@ struct Handle {
     long long ws_bytes;
     bool y_set;
     int smooth;          // SI kernel smoothness alpha of Eq. 2.5 (lattices; 2 unless set)
+    bool noise_pt;       // one noise variance per task (general path only)
 };
+
+// columns of the per-block partial sums of the general solvers: [log det, quad, trace G, Gamma (T(T+1)/2)]
+// and, with per-task noise, the T per-task traces of G
+inline int solve_nq(const Handle* h) { return 3 + h->T * (h->T + 1) / 2 + (h->noise_pt ? h->T : 0); }
 
 __device__ __forceinline__ void set_status(int* st, int bit) { atomicOr(st, bit); }
 

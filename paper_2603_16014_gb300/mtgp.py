@@ -11,7 +11,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import DNET, FP32_TRANSFORM, FP64, LATTICE, check, lib
+from ._lib import DNET, FP32_TRANSFORM, FP64, LATTICE, NOISE_PER_TASK, check, lib
 
 
 def _ptr(t):
@@ -37,7 +37,7 @@ class MTGP:
     ``shift``: (T, d) words.  ``precision``: "fp64" or "fp32" (FP32 kernel-column transforms).
     """
 
-    def __init__(self, kind: str, d: int, m, gen, shift, precision: str = "fp64"):
+    def __init__(self, kind: str, d: int, m, gen, shift, precision: str = "fp64", noise_per_task: bool = False):
         self.kind = LATTICE if kind == "lattice" else DNET
         self.d = int(d)
         self.m = [int(x) for x in m]
@@ -48,7 +48,8 @@ class MTGP:
         gen_cols = int(gen.shape[1]) if (self.kind == DNET and gen.ndim == 2) else 0
         m_arr = (ctypes.c_int * self.T)(*self.m)
         h = ctypes.c_void_p()
-        prec = FP32_TRANSFORM if precision == "fp32" else FP64
+        prec = (FP32_TRANSFORM if precision == "fp32" else FP64) | (NOISE_PER_TASK if noise_per_task else 0)
+        self.nsig = self.T if noise_per_task else 1
         check(lib().mtgp_create(ctypes.byref(h), self.kind, self.d, self.T, m_arr,
                                 gen.ctypes.data_as(ctypes.c_void_p), gen_cols,
                                 shift.ctypes.data_as(ctypes.c_void_p), prec), "mtgp_create")
@@ -56,9 +57,9 @@ class MTGP:
         self.precision = precision
 
     @classmethod
-    def from_problem(cls, p, precision=None):
+    def from_problem(cls, p, precision=None, noise_per_task: bool = False):
         prec = precision or ("fp32" if p.fp32_transform else "fp64")
-        return cls(p.kind, p.d, p.m, p.gen, p.shift, prec)
+        return cls(p.kind, p.d, p.m, p.gen, p.shift, prec, noise_per_task)
 
     # ------------------------------------------------------------------ calls
     def points(self, stream=None) -> torch.Tensor:
@@ -77,7 +78,7 @@ class MTGP:
         eta = _dev(eta).reshape(-1)
         W = _dev(W).reshape(self.T, -1)
         v = _dev(v).reshape(-1)
-        s2 = _dev(sigma2).reshape(1)
+        s2 = _dev(sigma2).reshape(self.nsig)
         return eta, W, v, s2
 
     def nll(self, eta, W, v, sigma2, stream=None):
@@ -97,7 +98,7 @@ class MTGP:
                     torch.empty(self.T, dtype=torch.float64, device="cuda"),
                     torch.empty(self.d, dtype=torch.float64, device="cuda"),
                     torch.empty_like(W), torch.empty(self.T, dtype=torch.float64, device="cuda"),
-                    torch.empty(1, dtype=torch.float64, device="cuda"))
+                    torch.empty(self.nsig, dtype=torch.float64, device="cuda"))
         out, tau, ge, gW, gv, gs = outs
         check(lib().mtgp_nll_grad(self._h, _ptr(eta), _ptr(W), W.shape[1], _ptr(v), _ptr(s2), _ptr(out), _ptr(tau),
                                   _ptr(ge), _ptr(gW), _ptr(gv), _ptr(gs), _stream(stream)), "mtgp_nll_grad")
@@ -125,7 +126,7 @@ class MTGP:
         ge = torch.empty(self.d, dtype=torch.float64, device="cuda")
         gW = torch.empty_like(W)
         gv = torch.empty(self.T, dtype=torch.float64, device="cuda")
-        gs = torch.empty(1, dtype=torch.float64, device="cuda")
+        gs = torch.empty(self.nsig, dtype=torch.float64, device="cuda")
         check(lib().mtgp_gcv_grad(self._h, _ptr(eta), _ptr(W), W.shape[1], _ptr(v), _ptr(s2), _ptr(out), _ptr(tau),
                                   _ptr(ge), _ptr(gW), _ptr(gv), _ptr(gs), _stream(stream)), "mtgp_gcv_grad")
         return out, tau, ge, gW, gv, gs
