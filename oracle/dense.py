@@ -77,12 +77,12 @@ def nll(kind, X_tasks, y, eta, W, v, sigma2, alpha=2):
                 tau=tau, alpha=a, Pi=Pi)
 
 
-def gcv(kind, X_tasks, y, eta, W, v, sigma2):
+def gcv(kind, X_tasks, y, eta, W, v, sigma2, alpha=2):
     """GCV loss (Eq. 3.3, second form) at the GCV mean (Eq. 3.4, second form), by dense inverses:
     tau solves (E K~^-2 E^T) tau = E K~^-2 y, r = y - E^T tau, L = r^T K~^-2 r / trace(K~^-1)^2.
     Returns dict L, num (r^T K~^-2 r), trace (trace K~^-1), tau."""
     R = task_covariance(W, v)
-    K = gram(kind, X_tasks, eta, R, sigma2)
+    K = gram(kind, X_tasks, eta, R, sigma2, alpha)
     n = [len(X) for X in X_tasks]
     E = summing_matrix(n)
     Kinv = np.linalg.inv(K)
@@ -152,16 +152,11 @@ def _param_contractions(kind, X_tasks, eta, W, R, K, contract, alpha=2, sigma2_s
     return g_eta, g_W, g_v, g_s2
 
 
-def gcv_grad(kind, X_tasks, y, eta, W, v, sigma2):
-    """Analytic gradient of the GCV loss (Eq. 3.3, second form) at the GCV mean (fixed by the envelope
-    theorem: tau_GCV minimises the numerator, the trace does not depend on tau).  With a = K~^-1 r,
-    b = K~^-1 a, A = a^T a, B = trace K~^-1:
-        dL = dA / B^2 - 2 A dB / B^3,  dA = -2 a^T dK~ b,  dB = -trace(K~^-2 dK~),
-    i.e. dL = sum(G * dK~) with G = -(a b^T + b a^T) / B^2 + (2 A / B^3) K~^-2.
-    Returns (gcv dict, g_eta, g_W, g_v, g_sigma2)."""
-    out = gcv(kind, X_tasks, y, eta, W, v, sigma2)
+def _gcv_weights(kind, X_tasks, y, eta, W, v, sigma2, alpha=2):
+    """The GCV loss and the dense matrix G with dL_GCV = sum(G * dK~) (see gcv_grad)."""
+    out = gcv(kind, X_tasks, y, eta, W, v, sigma2, alpha)
     R = task_covariance(W, v)
-    K = gram(kind, X_tasks, eta, R, sigma2)
+    K = gram(kind, X_tasks, eta, R, sigma2, alpha)
     n = [len(X) for X in X_tasks]
     E = summing_matrix(n)
     Kinv = np.linalg.inv(K)
@@ -171,11 +166,22 @@ def gcv_grad(kind, X_tasks, y, eta, W, v, sigma2):
     b = Kinv @ a
     A, B = float(a @ a), float(np.trace(Kinv))
     G = -(np.outer(a, b) + np.outer(b, a)) / B ** 2 + (2.0 * A / B ** 3) * (Kinv @ Kinv)
+    return out, R, K, G
+
+
+def gcv_grad(kind, X_tasks, y, eta, W, v, sigma2, alpha=2):
+    """Analytic gradient of the GCV loss (Eq. 3.3, second form) at the GCV mean (fixed by the envelope
+    theorem: tau_GCV minimises the numerator, the trace does not depend on tau).  With a = K~^-1 r,
+    b = K~^-1 a, A = a^T a, B = trace K~^-1:
+        dL = dA / B^2 - 2 A dB / B^3,  dA = -2 a^T dK~ b,  dB = -trace(K~^-2 dK~),
+    i.e. dL = sum(G * dK~) with G = -(a b^T + b a^T) / B^2 + (2 A / B^3) K~^-2.
+    Returns (gcv dict, g_eta, g_W, g_v, g_sigma2)."""
+    out, R, K, G = _gcv_weights(kind, X_tasks, y, eta, W, v, sigma2, alpha)
 
     def contract(dK):
         return float(np.sum(G * dK))
 
-    g_eta, g_W, g_v, g_s2 = _param_contractions(kind, X_tasks, eta, W, R, K, contract, 2, sigma2)
+    g_eta, g_W, g_v, g_s2 = _param_contractions(kind, X_tasks, eta, W, R, K, contract, alpha, sigma2)
     return out, g_eta, g_W, g_v, g_s2
 
 
@@ -230,12 +236,12 @@ def posterior(kind, X_tasks, y, eta, W, v, sigma2, Xq, task_q, alpha=2):
     return mean, var, prior
 
 
-def cubature(kind, X_tasks, y, eta, W, v, sigma2, gamma=1.0):
+def cubature(kind, X_tasks, y, eta, W, v, sigma2, gamma=1.0, alpha=2):
     """Multitask Bayesian cubature (Sec. 3.5, multitask cubature theorem) for the task integrals
     mu_t = int f(t, x) dx, with int Q(x, x') dx' = gamma: at tau = tau_MLE,
         mu_hat = tau + gamma R E K~^-1 (y - E^T tau),   Sigma = gamma R - gamma^2 R Pi R,
     Pi = E K~^-1 E^T, written out with dense solves.  Returns (mu_hat, Sigma, tau)."""
-    out = nll(kind, X_tasks, y, eta, W, v, sigma2)
+    out = nll(kind, X_tasks, y, eta, W, v, sigma2, alpha)
     R = task_covariance(W, v)
     n = [len(X) for X in X_tasks]
     E = summing_matrix(n)
@@ -243,3 +249,49 @@ def cubature(kind, X_tasks, y, eta, W, v, sigma2, gamma=1.0):
     mu = tau + gamma * R @ (E @ out["alpha"])
     Sigma = gamma * R - gamma ** 2 * R @ out["Pi"] @ R
     return mu, Sigma, tau
+
+
+def dsi_weights_grad(kind, X_tasks, y, eta, W, v, sigma2, b, loss="mle"):
+    """Gradient of L (Eq. 3.3, MLE or GCV form) with respect to the DSI mixture weights b of Eq. 2.6,
+    K(x, x') = sum_a b_a K_a(x XOR x'), with the dense derivative written out:
+      dK~/db_a = R_{tt'} sum_j eta_j K_a(x_j, x'_j) prod_{l != j} (1 + eta_l K(x_l, x'_l)).
+    Returns (loss dict, g_b (4,)) for L (the NLL gradient is half of the MLE one)."""
+    b = np.asarray(b, dtype=np.float64)
+    R = task_covariance(W, v)
+    if loss == "mle":
+        out = nll(kind, X_tasks, y, eta, W, v, sigma2, b)
+        K = gram(kind, X_tasks, eta, R, sigma2, b)
+        Kinv = np.linalg.inv(K)
+        Kinv = 0.5 * (Kinv + Kinv.T)
+        a = out["alpha"]
+
+        def contract(dK):
+            return float(np.sum(Kinv * dK) - a @ dK @ a)
+    elif loss == "gcv":
+        out, R, K, G = _gcv_weights(kind, X_tasks, y, eta, W, v, sigma2, b)
+
+        def contract(dK):
+            return float(np.sum(G * dK))
+    else:
+        raise ValueError(loss)
+    T = len(X_tasks)
+    n = [len(X) for X in X_tasks]
+    off = np.concatenate([[0], np.cumsum(n)])
+    d = len(eta)
+    g_b = np.zeros(4)
+    for a_ in range(1, 5):
+        dK = np.zeros_like(K)
+        for t in range(T):
+            for u in range(T):
+                Xa, Xb = X_tasks[t][:, None, :], X_tasks[u][None, :, :]
+                mix = [kernel_1d(kind, Xa[..., j], Xb[..., j], b) for j in range(d)]
+                blk = np.zeros((n[t], n[u]))
+                for j in range(d):
+                    term = eta[j] * kernel_1d(kind, Xa[..., j], Xb[..., j], a_)
+                    for l in range(d):
+                        if l != j:
+                            term = term * (1.0 + eta[l] * mix[l])
+                    blk += term
+                dK[off[t]:off[t + 1], off[u]:off[u + 1]] = R[t, u] * blk
+        g_b[a_ - 1] = contract(dK)
+    return out, g_b

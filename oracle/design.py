@@ -112,34 +112,64 @@ def dsi_beta_fixed(X: np.ndarray) -> np.ndarray:
 
 
 def dsi_kernel_1d(X: np.ndarray, alpha: int = 2) -> np.ndarray:
-    """Eq. 2.6, order-2 term: K2(x) = -1 - beta(x) x + 5/2 (1 - t_1(x)), t_1 = 2^{-beta}.
+    """Eq. 2.6: the order-alpha term K_alpha(x) of the adaptive-smoothness DSI kernel, alpha = 1..4,
+    with beta(x) = -floor(log2 x), t_nu(x) = 2^{-nu beta(x)} and beta(0) = t_nu(0) = 0:
+      K_1 = 1/6 - t_1 / 2                                  (reading of the garbled printed alpha = 1 form:
+                                                            the order-one Walsh kernel, mean zero)
+      K_2 = -1 - beta x + 5/2 (1 - t_1)
+      K_3 = -1 + beta x^2 - 5 (1 - t_1) x + 43/18 (1 - t_2)
+      K_4 = -1 - 2/3 beta x^3 + 5 (1 - t_1) x^2 - 43/9 (1 - t_2) x + 701/294 (1 - t_3)
+            + beta (1/48 sum_{a >= 1} (1 - 2 x_a) / 2^{3 (a - 1)} - 1/42),   x_a the binary digits of x.
 
-    ``X`` is the fixed-point word of x = x_j XOR x'_j.  With beta(0) = t_1(0) = 0, K2(0) = 3/2.
+    ``X`` is the fixed-point word of x = x_j XOR x'_j, so x has 32 digits and x_a = 0 for a > 32.
     """
-    if alpha != 2:
-        raise NotImplementedError("only the order-2 digitally-shift-invariant kernel")
     X = np.asarray(X, dtype=np.uint64)
+    nz = X > 0
     beta = dsi_beta_fixed(X).astype(np.float64)
     x = X.astype(np.float64) / TWO32
-    t1 = np.where(X > 0, np.exp2(-beta), 0.0)
-    return -1.0 - beta * x + 2.5 * (1.0 - t1)
+    t1 = np.where(nz, np.exp2(-beta), 0.0)
+    t2 = np.where(nz, np.exp2(-2.0 * beta), 0.0)
+    t3 = np.where(nz, np.exp2(-3.0 * beta), 0.0)
+    if alpha == 1:
+        return 1.0 / 6.0 - 0.5 * t1
+    if alpha == 2:
+        return -1.0 - beta * x + 2.5 * (1.0 - t1)
+    if alpha == 3:
+        return -1.0 + beta * x ** 2 - 5.0 * (1.0 - t1) * x + 43.0 / 18.0 * (1.0 - t2)
+    if alpha == 4:
+        digit_sum = np.zeros(X.shape)
+        for a in range(1, 33):
+            x_a = ((X >> np.uint64(32 - a)) & np.uint64(1)).astype(np.float64)
+            digit_sum += (1.0 - 2.0 * x_a) / 8.0 ** (a - 1)
+        digit_sum += 8.0 ** -31 * 8.0 / 7.0            # digits 33, 34, ... are zero
+        return (-1.0 - 2.0 / 3.0 * beta * x ** 3 + 5.0 * (1.0 - t1) * x ** 2 - 43.0 / 9.0 * (1.0 - t2) * x
+                + 701.0 / 294.0 * (1.0 - t3) + beta * (digit_sum / 48.0 - 1.0 / 42.0))
+    raise ValueError("DSI kernel order must be 1, 2, 3 or 4")
 
 
-def kernel_1d(kind: str, Xa: np.ndarray, Xb: np.ndarray, alpha: int = 2) -> np.ndarray:
-    """The univariate kernel of the kind's design/kernel pairing (Cond. 3.1) on fixed-point words;
-    alpha is the SI kernel's smoothness (Eq. 2.5); the DSI kernel is the order-2 term of Eq. 2.6."""
+def dsi_mixture_1d(X: np.ndarray, b) -> np.ndarray:
+    """Eq. 2.6: K(x, x') = sum_{alpha=1}^{4} b_alpha K_alpha(x XOR x'), weights b >= 0."""
+    return sum(float(b[a - 1]) * dsi_kernel_1d(X, a) for a in range(1, 5) if b[a - 1] != 0.0)
+
+
+def kernel_1d(kind: str, Xa: np.ndarray, Xb: np.ndarray, alpha=2) -> np.ndarray:
+    """The univariate kernel of the kind's design/kernel pairing (Cond. 3.1) on fixed-point words.
+    Lattices: alpha is the SI kernel's smoothness (Eq. 2.5).  Digital nets: alpha is either one order
+    1..4 of Eq. 2.6 (weights b = e_alpha) or the four mixture weights b of Eq. 2.6."""
     Xa = np.asarray(Xa, dtype=np.uint64)
     Xb = np.asarray(Xb, dtype=np.uint64)
     if kind == "lattice":
         u = ((Xa - Xb) & np.uint64(MASK32)).astype(np.float64) / TWO32
         return si_kernel_1d(u, alpha)
     if kind == "dnet":
-        return dsi_kernel_1d(Xa ^ Xb, 2)
+        if np.ndim(alpha) == 0:
+            return dsi_kernel_1d(Xa ^ Xb, int(alpha))
+        return dsi_mixture_1d(Xa ^ Xb, alpha)
     raise ValueError(kind)
 
 
 def product_kernel(kind: str, Xa: np.ndarray, Xb: np.ndarray, eta: np.ndarray,
-                   gamma: float = 1.0, alpha: int = 2) -> np.ndarray:
+                   gamma: float = 1.0, alpha=2) -> np.ndarray:
     """Eq. 2.4: Q(x, x') = gamma prod_j (1 + eta_j K(x_j, x'_j)); Xa (..., d), Xb (..., d) broadcast."""
     Xa = np.asarray(Xa)
     Xb = np.asarray(Xb)
