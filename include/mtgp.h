@@ -182,12 +182,38 @@ int mtgp_nll_equal_static(int kind, int d, int T, int m, const uint32_t* gen, in
                           double* tau, int* status, cudaStream_t stream);
 
 /*
- * mtgp_set_smoothness -- the SI kernel's smoothness alpha in Eq. 2.5 for a lattice handle: 1, 2
- * (default), 3 or 4, i.e. (-1)^(alpha+1) (2 pi)^(2 alpha) / (2 alpha)! B_(2 alpha)((x - x') mod 1) as
- * the univariate factor of Eq. 2.4.  Digital-net handles keep the order-2 DSI kernel (other values:
- * MTGP_ERR_UNSUPPORTED).  Takes effect for the following calls on the handle; synchronous, host only.
+ * mtgp_set_smoothness -- the kernel's smoothness alpha, 1, 2 (default), 3 or 4.  Lattice handles:
+ * the SI kernel of Eq. 2.5, (-1)^(alpha+1) (2 pi)^(2 alpha) / (2 alpha)! B_(2 alpha)((x - x') mod 1)
+ * as the univariate factor of Eq. 2.4.  Digital-net handles: the single order K_alpha of the DSI
+ * kernel of Eq. 2.6 (mixture weights b = e_alpha; alpha = 2 clears any weights set by
+ * mtgp_set_dsi_weights).  Takes effect for the following calls on the handle; synchronous (waits
+ * for the device), host only.
  */
 int mtgp_set_smoothness(mtgp_t* h, int alpha);
+
+/*
+ * mtgp_set_dsi_weights -- the adaptive-smoothness DSI kernel of Eq. 2.6 for a digital-net handle:
+ * univariate factor K(x, x') = sum_{a=1}^{4} b_a K_a(x XOR x') in Eq. 2.4, with
+ *   K_1 = 1/6 - t_1/2 (the order-one Walsh kernel; the printed order-1 form is read with mean zero),
+ *   K_2 = -1 - beta x + 5/2 (1 - t_1),  K_3, K_4 as printed in Eq. 2.6,
+ * beta(x) = -floor(log2 x), t_nu = 2^(-nu beta), beta(0) = t_nu(0) = 0.
+ *   b   device, 4 doubles >= 0 (checked by the following evaluations: non-finite or negative
+ *       weights raise MTGP_ERR_NUMERIC at mtgp_sync), copied into the handle in stream order on
+ *       `stream`; NULL returns the handle to the order-2 kernel alone (b = e_2, the default).
+ * With weights set, every evaluation (mtgp_nll, mtgp_nll_grad, mtgp_posterior, mtgp_gcv,
+ * mtgp_gcv_grad, mtgp_cubature) uses the mixture, through the general kernels (the fused
+ * equal-size kernels evaluate the order-2 kernel only), and the gradient calls also form dL/db
+ * (read it with mtgp_dsi_weights_grad).  Lattice handles: MTGP_ERR_UNSUPPORTED.
+ */
+int mtgp_set_dsi_weights(mtgp_t* h, const double* b, cudaStream_t stream);
+
+/*
+ * mtgp_dsi_weights_grad -- copy the gradient with respect to the mixture weights b (4 doubles,
+ * device g_b) left by the last mtgp_nll_grad (gradient of the NLL, as g_eta) or mtgp_gcv_grad
+ * (gradient of the GCV loss) on the handle, in stream order; zeros before the first gradient call
+ * after mtgp_set_dsi_weights.  MTGP_ERR_INVALID_ARG when the handle has no weights set.
+ */
+int mtgp_dsi_weights_grad(mtgp_t* h, double* g_b, cudaStream_t stream);
 
 /*
  * Multitask Bayesian cubature (Sec. 3.5, multitask cubature theorem) for the task integrals

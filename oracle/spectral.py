@@ -473,13 +473,16 @@ def posterior_var_equal(kind, gen, shift, m, eta, W, v, sigma2, Xq, task_q):
     return var
 
 
-def nll_grad_equal(kind, gen, shift, m, y, eta, W, v, sigma2):
+def nll_grad_equal(kind, gen, shift, m, y, eta, W, v, sigma2, alpha=2):
     """Equal sizes: L (Eq. 3.3) and its gradient by per-frequency traces, dL/dtheta = sum_f tr(G(f) dLambda(f)),
     G(f) = Lambda(f)^-1 - alpha(f) alpha(f)^H, every dLambda(f)/dtheta formed explicitly:
       dLambda/d eta_j = R o dM_j(f)  (dM_j = transforms of the columns' eta_j derivatives),
       dLambda/d W_ts  = (e_t W_s^T + W_s e_t^T) o M(f),  dLambda/d v_t = e_t e_t^T o M(f),  dLambda/d sigma2 = I.
-    Returns (out, g_eta, g_W, g_v, g_sigma2) for L (the NLL gradient is half of it)."""
+    Returns (out, g_eta, g_W, g_v, g_sigma2) for L (the NLL gradient is half of it).  With the four DSI
+    mixture weights b of Eq. 2.6 as ``alpha`` (digital nets), also g_b (4,) last, from
+      dLambda/d b_a = R o dB_a(f),  dB_a = transforms of sum_j eta_j K_a(x_j) prod_{l != j} (1 + eta_l K(x_l))."""
     from .design import kernel_1d
+    mix = np.ndim(alpha) > 0
     T = len(m)
     mm = int(m[0])
     n = 1 << mm
@@ -488,9 +491,10 @@ def nll_grad_equal(kind, gen, shift, m, y, eta, W, v, sigma2):
     d = len(eta)
     M = np.zeros((n, T, T), dtype=np.complex128)
     dM = np.zeros((d, n, T, T), dtype=np.complex128)
+    dB = np.zeros((4, n, T, T), dtype=np.complex128)
     for t in range(T):
         for u in range(t, T):
-            K1 = [kernel_1d(kind, X[t][:, j], np.full(n, X[u][0, j], dtype=np.uint64)) for j in range(d)]
+            K1 = [kernel_1d(kind, X[t][:, j], np.full(n, X[u][0, j], dtype=np.uint64), alpha) for j in range(d)]
             fac = [1.0 + eta[j] * K1[j] for j in range(d)]
             col = np.prod(fac, axis=0)
             mu = np.sqrt(n) * vdag(kind, col.astype(np.complex128), mm)
@@ -501,9 +505,20 @@ def nll_grad_equal(kind, gen, shift, m, y, eta, W, v, sigma2):
                 dmu = np.sqrt(n) * vdag(kind, dcol.astype(np.complex128), mm)
                 dM[j, :, t, u] = dmu
                 dM[j, :, u, t] = np.conj(dmu)
+            if mix:
+                for a_ in range(1, 5):
+                    dcol = np.zeros(n)
+                    for j in range(d):
+                        Ka = kernel_1d(kind, X[t][:, j], np.full(n, X[u][0, j], dtype=np.uint64), a_)
+                        dcol += eta[j] * Ka * np.prod([fac[l] for l in range(d) if l != j], axis=0) if d > 1 \
+                            else eta[j] * Ka
+                    dmu = np.sqrt(n) * vdag(kind, dcol.astype(np.complex128), mm)
+                    dB[a_ - 1, :, t, u] = dmu
+                    dB[a_ - 1, :, u, t] = np.conj(dmu)
     for t in range(T):
         M[:, t, t] = M[:, t, t].real
         dM[:, :, t, t] = dM[:, :, t, t].real
+        dB[:, :, t, t] = dB[:, :, t, t].real
     Lam = R[None, :, :] * M + sigma2 * np.eye(T)[None, :, :]
     ys = np.asarray(y, dtype=np.float64).reshape(T, n)
     rhat = vdag(kind, ys.astype(np.complex128), mm).T.copy()     # (n, T)
@@ -532,4 +547,6 @@ def nll_grad_equal(kind, gen, shift, m, y, eta, W, v, sigma2):
     g_s2 = float(np.einsum("faa->", G).real)
     N = T * n
     out = dict(L=quad + logdet, nll=0.5 * (quad + logdet + N * np.log(2 * np.pi)), quad=quad, logdet=logdet, tau=tau)
+    if mix:
+        return out, g_eta, g_W, g_v, g_s2, np.array([tr(R[None] * dB[a_]) for a_ in range(4)])
     return out, g_eta, g_W, g_v, g_s2

@@ -12,7 +12,8 @@ constexpr int kThreads = 256;
 
 struct ColParams {
     ColDesc cols[MTGP_MAX_COLS];
-    int alpha;  // SI smoothness
+    int alpha;           // SI smoothness
+    const double* bmix;  // DSI mixture weights (4), or nullptr
 };
 
 template <typename S, bool CPLX>
@@ -20,6 +21,7 @@ __global__ void __launch_bounds__(kThreads)
 k_colgen(void* out, ColParams cp, int kind, int d, const uint32_t* __restrict__ gen, int gen_cols,
          const uint32_t* __restrict__ shift, const double* __restrict__ eta) {
     __shared__ S s_eta[MTGP_MAX_DIM];
+    __shared__ S s_b[4];
     __shared__ uint32_t s_dt[MTGP_MAX_DIM], s_du[MTGP_MAX_DIM];
     const ColDesc c = cp.cols[blockIdx.y];
     if (threadIdx.x < d) {
@@ -27,6 +29,8 @@ k_colgen(void* out, ColParams cp, int kind, int d, const uint32_t* __restrict__ 
         s_dt[threadIdx.x] = shift[c.t * d + threadIdx.x];
         s_du[threadIdx.x] = shift[c.u * d + threadIdx.x];
     }
+    if (cp.bmix && threadIdx.x < 4) s_b[threadIdx.x] = (S)cp.bmix[threadIdx.x];
+    const S* bw = cp.bmix ? s_b : nullptr;
     __syncthreads();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < c.n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -34,7 +38,7 @@ k_colgen(void* out, ColParams cp, int kind, int d, const uint32_t* __restrict__ 
         for (int j = 0; j < d; ++j) {
             uint32_t z = point_word(kind, (uint32_t)i, j, gen, gen_cols);
             uint32_t X = pair_word(kind, z, s_dt[j], s_du[j]);
-            q *= (S)1 + s_eta[j] * kernel1d<S>(kind, X, cp.alpha);
+            q *= (S)1 + s_eta[j] * kernel1d_b<S>(kind, X, cp.alpha, bw);
         }
         if (CPLX) {
             reinterpret_cast<cx<S>*>(out)[c.off + i] = mk(q, (S)0);
@@ -76,18 +80,24 @@ __global__ void k_scale(double* __restrict__ a, long long n, double s) {
 
 // dL/deta_j = Re sum_c sum_i omega_c[i] dc_c[i]/deta_j, omega = DIF(adjoint weights); the derivative
 // of the product is K_j prod_{l != j} (1 + eta_l K_l), formed with prefix and suffix products
-// (no division: a factor 1 + eta K may vanish).
-template <typename S, bool CPLX>
+// (no division: a factor 1 + eta K may vanish).  With DSI mixture weights (MIX) the same pass also
+// forms dL/db_a = Re sum omega dc/db_a, dc/db_a = sum_j eta_j K_a(x_j) prod_{l != j} (1 + eta_l K_l),
+// written after the d eta entries of each block's partials.
+template <typename S, bool CPLX, bool MIX>
 __global__ void __launch_bounds__(kThreads)
 k_eta_grad(const void* omega, ColParams cp, int ncols, int kind, int d, const uint32_t* __restrict__ gen,
            int gen_cols, const uint32_t* __restrict__ shift, const double* __restrict__ eta,
            double* __restrict__ partials, long long total) {
+    constexpr int NB = MIX ? 4 : 0;
     __shared__ S s_eta[MTGP_MAX_DIM];
-    __shared__ double s_red[kThreads / 32][MTGP_MAX_DIM];
+    __shared__ S s_b[4];
+    __shared__ double s_red[kThreads / 32][MTGP_MAX_DIM + 4];
     if (threadIdx.x < d) s_eta[threadIdx.x] = (S)eta[threadIdx.x];
+    if (MIX && threadIdx.x < 4) s_b[threadIdx.x] = (S)cp.bmix[threadIdx.x];
     __syncthreads();
-    double acc[MTGP_MAX_DIM];
-    for (int j = 0; j < d; ++j) acc[j] = 0.0;
+    const S* bw = MIX ? s_b : nullptr;
+    double acc[MTGP_MAX_DIM + NB];
+    for (int j = 0; j < d + NB; ++j) acc[j] = 0.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
         // locate the column
@@ -100,31 +110,39 @@ k_eta_grad(const void* omega, ColParams cp, int ncols, int kind, int d, const ui
         else w = reinterpret_cast<const S*>(omega)[e];
         S kv[MTGP_MAX_DIM];
         S pre[MTGP_MAX_DIM];
+        uint32_t xw[MIX ? MTGP_MAX_DIM : 1];
         S p = (S)1;
         for (int j = 0; j < d; ++j) {
             uint32_t z = point_word(kind, (uint32_t)i, j, gen, gen_cols);
             uint32_t X = pair_word(kind, z, shift[cd.t * d + j], shift[cd.u * d + j]);
-            kv[j] = kernel1d<S>(kind, X, cp.alpha);
+            if (MIX) xw[j] = X;
+            kv[j] = kernel1d_b<S>(kind, X, cp.alpha, bw);
             pre[j] = p;
             p *= (S)1 + s_eta[j] * kv[j];
         }
         S suf = (S)1;
         for (int j = d - 1; j >= 0; --j) {
             acc[j] += (double)(w * kv[j] * pre[j] * suf);
+            if (MIX) {
+                S ko[4];
+                dsi_orders<S>(xw[j], ko);
+                const S f = w * s_eta[j] * (pre[j] * suf);
+                for (int a = 0; a < 4; ++a) acc[d + a] += (double)(f * ko[a]);
+            }
             suf *= (S)1 + s_eta[j] * kv[j];
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int j = 0; j < d; ++j) {
+    for (int j = 0; j < d + NB; ++j) {
         double v = acc[j];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) s_red[warp][j] = v;
     }
     __syncthreads();
-    if (threadIdx.x < d) {
+    if (threadIdx.x < d + NB) {
         double v = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_red[w][threadIdx.x];
-        partials[(long long)blockIdx.x * d + threadIdx.x] = v;
+        partials[(long long)blockIdx.x * (d + NB) + threadIdx.x] = v;
     }
 }
 
@@ -132,6 +150,7 @@ ColParams make_params(const Handle* h) {
     ColParams cp;
     for (int c = 0; c < h->ncols; ++c) cp.cols[c] = h->cols[c];
     cp.alpha = h->smooth;
+    cp.bmix = h->dsi_mix ? h->bmix : nullptr;
     return cp;
 }
 
@@ -201,11 +220,18 @@ int eta_grad_blocks(const Handle* h) {
 void launch_eta_grad(const Handle* h, const double* eta, const void* omega, double* partials, int nblk,
                      cudaStream_t st) {
     ColParams cp = make_params(h);
-    if (h->fp32) {
-        if (h->cplx) k_eta_grad<float, true><<<nblk, kThreads, 0, st>>>(omega, cp, h->ncols, h->kind, h->d, h->gen, h->gen_cols, h->shift, eta, partials, h->col_elems);
-        else k_eta_grad<float, false><<<nblk, kThreads, 0, st>>>(omega, cp, h->ncols, h->kind, h->d, h->gen, h->gen_cols, h->shift, eta, partials, h->col_elems);
+#define MTGP_ETA_GRAD(S, C, M) \
+    k_eta_grad<S, C, M><<<nblk, kThreads, 0, st>>>(omega, cp, h->ncols, h->kind, h->d, h->gen, h->gen_cols, \
+                                                   h->shift, eta, partials, h->col_elems)
+    if (h->dsi_mix) {
+        if (h->fp32) MTGP_ETA_GRAD(float, false, true);
+        else MTGP_ETA_GRAD(double, false, true);
+    } else if (h->fp32) {
+        if (h->cplx) MTGP_ETA_GRAD(float, true, false);
+        else MTGP_ETA_GRAD(float, false, false);
     } else {
-        if (h->cplx) k_eta_grad<double, true><<<nblk, kThreads, 0, st>>>(omega, cp, h->ncols, h->kind, h->d, h->gen, h->gen_cols, h->shift, eta, partials, h->col_elems);
-        else k_eta_grad<double, false><<<nblk, kThreads, 0, st>>>(omega, cp, h->ncols, h->kind, h->d, h->gen, h->gen_cols, h->shift, eta, partials, h->col_elems);
+        if (h->cplx) MTGP_ETA_GRAD(double, true, false);
+        else MTGP_ETA_GRAD(double, false, false);
     }
+#undef MTGP_ETA_GRAD
 }

@@ -884,6 +884,7 @@ int fused_threads_ac(int a, int d) { return threads_ac(a, d); }
 
 bool fused_supported(const Handle* h) {
     if (h->noise_pt) return false;  // the fused solve takes one shared noise variance
+    if (h->dsi_mix) return false;   // the fused column passes evaluate the order-2 DSI kernel only
     int a, lgL;
     return plan(h, &a, &lgL);
 }

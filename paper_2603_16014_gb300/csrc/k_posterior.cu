@@ -69,6 +69,7 @@ __global__ void k_beta_finish(const double* __restrict__ beta, double* __restric
 
 struct PostParams {
     int kind, d, T, alpha;
+    const double* bmix;  // DSI mixture weights (4), or nullptr
     long long n[MTGP_TMAX];
     long long yoff[MTGP_TMAX];
     int order[MTGP_TMAX];
@@ -76,13 +77,20 @@ struct PostParams {
 };
 
 template <typename S>
-__device__ __forceinline__ S qkernel(int kind, const uint32_t* xa, const uint32_t* xb, const S* eta, int d, int alpha) {
+__device__ __forceinline__ S qkernel(int kind, const uint32_t* xa, const uint32_t* xb, const S* eta, int d, int alpha,
+                                     const S* bmix) {
     S q = (S)1;
     for (int j = 0; j < d; ++j) {
         uint32_t X = (kind == MTGP_LATTICE) ? (xa[j] - xb[j]) : (xa[j] ^ xb[j]);
-        q *= (S)1 + eta[j] * kernel1d<S>(kind, X, alpha);
+        q *= (S)1 + eta[j] * kernel1d_b<S>(kind, X, alpha, bmix);
     }
     return q;
+}
+
+// shared copy of the mixture weights (nullptr when the handle has none)
+__device__ __forceinline__ const double* load_bmix(double* s_bm, const PostParams& p) {
+    if (p.bmix && threadIdx.x < 4) s_bm[threadIdx.x] = p.bmix[threadIdx.x];
+    return p.bmix ? s_bm : nullptr;
 }
 
 __device__ void load_R_post(double* sR, const PostParams& p, const ThetaPtrs& th) {
@@ -111,8 +119,10 @@ k_post_mean_part(const uint32_t* __restrict__ xqw, const int* __restrict__ task,
     __shared__ double s_eta[MTGP_MAX_DIM];
     __shared__ uint32_t s_x[kTile * MTGP_MAX_DIM];
     __shared__ double s_b[kTile];
+    __shared__ double s_bm[4];
     load_R_post(sR, p, th);
     if (threadIdx.x < p.d) s_eta[threadIdx.x] = th.eta[threadIdx.x];
+    const double* bm = load_bmix(s_bm, p);
     const int k = blockIdx.y;
     int u = 0;
     while (u + 1 < p.T && sl.first[u + 1] <= k) ++u;
@@ -136,7 +146,7 @@ k_post_mean_part(const uint32_t* __restrict__ xqw, const int* __restrict__ task,
         for (int e = threadIdx.x; e < cnt; e += blockDim.x) s_b[e] = beta[p.yoff[u] + i0 + e];
         __syncthreads();
         if (act) {
-            for (int i = 0; i < cnt; ++i) acc += qkernel<double>(p.kind, xq, s_x + i * d, s_eta, d, p.alpha) * s_b[i];
+            for (int i = 0; i < cnt; ++i) acc += qkernel<double>(p.kind, xq, s_x + i * d, s_eta, d, p.alpha, bm) * s_b[i];
         }
     }
     if (act) part[(long long)k * nq + q] = sR[tq * p.T + u] * acc;
@@ -158,8 +168,10 @@ __global__ void k_var_rows(const uint32_t* __restrict__ xqw, const int* __restri
                            const uint32_t* __restrict__ dw, PostParams p, ThetaPtrs th, double* __restrict__ rows) {
     __shared__ double sR[MTGP_TMAX * MTGP_TMAX];
     __shared__ double s_eta[MTGP_MAX_DIM];
+    __shared__ double s_bm[4];
     load_R_post(sR, p, th);
     if (threadIdx.x < p.d) s_eta[threadIdx.x] = th.eta[threadIdx.x];
+    const double* bm = load_bmix(s_bm, p);
     __syncthreads();
     const long long n = p.n[0];
     const long long total = (long long)B * p.T * n;
@@ -171,7 +183,7 @@ __global__ void k_var_rows(const uint32_t* __restrict__ xqw, const int* __restri
         int b = (int)(bu / p.T);
         int q = q0 + b;
         int tq = p.rank[task[q]];
-        double v = sR[tq * p.T + u] * qkernel<double>(p.kind, xqw + (long long)q * p.d, dw + (p.yoff[u] + i) * p.d, s_eta, p.d, p.alpha);
+        double v = sR[tq * p.T + u] * qkernel<double>(p.kind, xqw + (long long)q * p.d, dw + (p.yoff[u] + i) * p.d, s_eta, p.d, p.alpha, bm);
         if (CPLX) {
             rows[2 * e] = v;
             rows[2 * e + 1] = 0.0;
@@ -267,8 +279,10 @@ k_var_quad(const double* __restrict__ rows, const double* __restrict__ fac, cons
     __shared__ double sR[T * T];
     __shared__ double s_eta[MTGP_MAX_DIM];
     __shared__ double s_red[kThreads / 32];
+    __shared__ double s_bm[4];
     load_R_post(sR, pp, th);
     if (threadIdx.x < pp.d) s_eta[threadIdx.x] = th.eta[threadIdx.x];
+    const double* bm = load_bmix(s_bm, pp);
     __syncthreads();
     const int b = blockIdx.x;
     const long long n = p.n;
@@ -300,7 +314,7 @@ k_var_quad(const double* __restrict__ rows, const double* __restrict__ fac, cons
         int q = q0 + b;
         int tq = pp.rank[task[q]];
         const uint32_t* x = xqw + (long long)q * pp.d;
-        double prior = sR[tq * T + tq] * qkernel<double>(pp.kind, x, x, s_eta, pp.d, pp.alpha);
+        double prior = sR[tq * T + tq] * qkernel<double>(pp.kind, x, x, s_eta, pp.d, pp.alpha, bm);
         var[q] = prior - s;
     }
 }
@@ -421,6 +435,7 @@ int posterior_run(Handle* h, ThetaPtrs th, int nq, const double* xq, const int* 
     PostParams pp;
     pp.kind = h->kind;
     pp.alpha = h->smooth;
+    pp.bmix = h->dsi_mix ? h->bmix : nullptr;
     pp.d = d;
     pp.T = h->T;
     for (int t = 0; t < MTGP_TMAX; ++t) {

@@ -661,6 +661,7 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
 
 struct FinParams {
     int T, d, s, equal, cplx, NQ, nsolve, neta, grad, gcv, pt;
+    int mix;  // DSI mixture: 4 dL/db entries follow the d eta entries of each eta partial row
     long long N;
     long long n0;
     int order[MTGP_TMAX];
@@ -670,18 +671,19 @@ struct FinParams {
 
 __global__ void k_finalize(const double* partials, const double* eta_partials, const double* yhat,
                            const double* tau_sorted, FinParams p, ThetaPtrs th, double* out, double* tau,
-                           double* g_eta, double* g_W, double* g_v, double* g_s2) {
+                           double* g_eta, double* g_W, double* g_v, double* g_s2, double* g_b) {
     __shared__ double tot[3 + MTGP_MAX_COLS + MTGP_TMAX];
-    __shared__ double etot[MTGP_MAX_DIM];
+    __shared__ double etot[MTGP_MAX_DIM + 4];
     for (int q = threadIdx.x; q < p.NQ; q += blockDim.x) {
         double v = 0.0;
         for (int b = 0; b < p.nsolve; ++b) v += partials[(long long)b * p.NQ + q];
         tot[q] = v;
     }
     if (p.grad) {
-        for (int j = threadIdx.x; j < p.d; j += blockDim.x) {
+        const int pw = p.d + (p.mix ? 4 : 0);
+        for (int j = threadIdx.x; j < pw; j += blockDim.x) {
             double v = 0.0;
-            for (int b = 0; b < p.neta; ++b) v += eta_partials[(long long)b * p.d + j];
+            for (int b = 0; b < p.neta; ++b) v += eta_partials[(long long)b * pw + j];
             etot[j] = v;
         }
     }
@@ -718,6 +720,8 @@ __global__ void k_finalize(const double* partials, const double* eta_partials, c
         g_s2[0] = 0.5 * sc * tot[2];
     }
     for (int j = 0; j < p.d; ++j) g_eta[j] = 0.5 * sc * etot[j];
+    if (p.mix)
+        for (int a = 0; a < 4; ++a) g_b[a] = 0.5 * sc * etot[p.d + a];
     for (int tc = 0; tc < T; ++tc) {
         int t = p.rank[tc];
         for (int k = 0; k < p.s; ++k) {
@@ -831,6 +835,7 @@ void launch_finalize(const Handle* h, ThetaPtrs th, bool grad, const double* par
     fp.cplx = h->cplx ? 1 : 0;
     fp.NQ = solve_nq(h);
     fp.pt = h->noise_pt ? 1 : 0;
+    fp.mix = h->dsi_mix ? 1 : 0;
     fp.nsolve = nsolve;
     fp.neta = neta;
     fp.grad = grad ? 1 : 0;
@@ -841,5 +846,6 @@ void launch_finalize(const Handle* h, ThetaPtrs th, bool grad, const double* par
         fp.rank[t] = t < h->T ? h->rank[t] : 0;
         fp.yoff[t] = t < h->T ? h->yoff[t] : 0;
     }
-    k_finalize<<<1, 64, 0, st>>>(partials, eta_partials, h->yhat, h->tau, fp, th, out, tau, g_eta, g_W, g_v, g_s2);
+    k_finalize<<<1, 64, 0, st>>>(partials, eta_partials, h->yhat, h->tau, fp, th, out, tau, g_eta, g_W, g_v, g_s2,
+                                 h->dsi_mix ? h->bmix + 4 : nullptr);
 }

@@ -84,6 +84,8 @@ __global__ void k_check_theta(ThetaPtrs th, int d, int T, int* status) {
         if (!isfinite(th.v[t]) || th.v[t] < 0.0) bad = 1;
     for (int t = threadIdx.x; t < (th.nsig > 1 ? th.nsig : 1); t += blockDim.x)
         if (!isfinite(th.sigma2[t]) || th.sigma2[t] < 0.0) bad = 1;
+    if (th.bmix && threadIdx.x < 4)
+        if (!isfinite(th.bmix[threadIdx.x]) || th.bmix[threadIdx.x] < 0.0) bad = 1;
     if (bad) atomicOr(status, ST_NUMERIC);
 }
 
@@ -194,7 +196,7 @@ cudaError_t dalloc(Handle* h, T** p, size_t count) {
 void free_all(Handle* h) {
     void* ptrs[] = {h->gen, h->shift, h->cols_dev, h->offs_dev, h->yoffs_dev, h->twid, h->twid32, h->yhat, h->spec,
                     h->wgt, h->S, h->Z, h->r, h->alpha, h->tau, h->partials, h->status, h->out_tmp, h->counters,
-                    h->gcv_h, h->pi_buf};
+                    h->gcv_h, h->pi_buf, h->bmix};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->prof) {
@@ -410,7 +412,7 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
     {
         const int NQ = solve_nq(h);
         long long nsolve = h->equal ? solve_equal_blocks(h) : solve_tree_blocks(h);
-        h->partials_len = nsolve * NQ + (long long)eta_grad_blocks(h) * d;
+        h->partials_len = nsolve * NQ + (long long)eta_grad_blocks(h) * (d + 4);
         long long fl = fused_partials_len(h);
         if (fl > h->partials_len) h->partials_len = fl;
         AL(h->partials, (size_t)h->partials_len);
@@ -418,6 +420,7 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
     AL(h->status, (size_t)1);
     AL(h->out_tmp, (size_t)4);
     AL(h->counters, (size_t)4);
+    AL(h->bmix, (size_t)8);
 #undef AL
     h->prof = new Prof();
     // upload descriptors
@@ -434,6 +437,7 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
                cudaMemcpy(h->yoffs_dev, yoffs.data(), yoffs.size() * sizeof(long long), cudaMemcpyHostToDevice) == cudaSuccess &&
                cudaMemset(h->status, 0, sizeof(int)) == cudaSuccess &&
                cudaMemset(h->counters, 0, 4 * sizeof(unsigned)) == cudaSuccess &&
+               cudaMemset(h->bmix, 0, 8 * sizeof(double)) == cudaSuccess &&
                cudaMemset(h->tau, 0, MTGP_TMAX * sizeof(double)) == cudaSuccess;
     if (!okc) {
         free_all(h);
@@ -464,9 +468,42 @@ int mtgp_set_smoothness(mtgp_t* hs, int alpha) {
     if (!hs) return fail(MTGP_ERR_INVALID_ARG, "NULL handle");
     Handle* h = &hs->h;
     if (alpha < 1 || alpha > 4) return fail(MTGP_ERR_INVALID_ARG, "smoothness must be 1, 2, 3 or 4");
-    if (h->kind != MTGP_LATTICE && alpha != 2)
-        return fail(MTGP_ERR_UNSUPPORTED, "digital nets use the order-2 DSI kernel in this build");
-    h->smooth = alpha;
+    if (h->kind == MTGP_LATTICE) {
+        h->smooth = alpha;
+        return MTGP_OK;
+    }
+    // digital nets: the single order alpha of Eq. 2.6, i.e. mixture weights b = e_alpha
+    if (alpha == 2) {
+        h->dsi_mix = false;
+        return MTGP_OK;
+    }
+    double b[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    b[alpha - 1] = 1.0;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(h->bmix, b, sizeof(b), cudaMemcpyHostToDevice));
+    h->dsi_mix = true;
+    return MTGP_OK;
+}
+
+int mtgp_set_dsi_weights(mtgp_t* hs, const double* b, cudaStream_t st) {
+    if (!hs) return fail(MTGP_ERR_INVALID_ARG, "NULL handle");
+    Handle* h = &hs->h;
+    if (h->kind != MTGP_DNET) return fail(MTGP_ERR_UNSUPPORTED, "mixture weights apply to digital nets (Eq. 2.6)");
+    if (!b) {
+        h->dsi_mix = false;
+        return MTGP_OK;
+    }
+    CK(cudaMemcpyAsync(h->bmix, b, 4 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(h->bmix + 4, 0, 4 * sizeof(double), st));
+    h->dsi_mix = true;
+    return MTGP_OK;
+}
+
+int mtgp_dsi_weights_grad(mtgp_t* hs, double* g_b, cudaStream_t st) {
+    if (!hs || !g_b) return fail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    Handle* h = &hs->h;
+    if (!h->dsi_mix) return fail(MTGP_ERR_INVALID_ARG, "no DSI mixture weights are set on this handle");
+    CK(cudaMemcpyAsync(g_b, h->bmix + 4, 4 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     return MTGP_OK;
 }
 
@@ -497,7 +534,7 @@ int mtgp_nll(mtgp_t* hs, const double* eta, const double* W, int s, const double
     int rc = validate_theta(h, eta, W, s, v, sigma2);
     if (rc) return rc;
     if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
-    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1};
+    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1, h->dsi_mix ? h->bmix : nullptr};
     return run_nll(h, th, false, out, tau, nullptr, nullptr, nullptr, nullptr, st);
 }
 
@@ -510,7 +547,7 @@ int mtgp_nll_grad(mtgp_t* hs, const double* eta, const double* W, int s, const d
     int rc = validate_theta(h, eta, W, s, v, sigma2);
     if (rc) return rc;
     if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
-    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1};
+    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1, h->dsi_mix ? h->bmix : nullptr};
     return run_nll(h, th, true, out, tau, g_eta, g_W, g_v, g_sigma2, st);
 }
 
@@ -563,7 +600,7 @@ int mtgp_cubature(mtgp_t* hs, const double* eta, const double* W, int s, const d
         CK(cudaMalloc(&h->pi_buf, sizeof(double) * MTGP_TMAX * MTGP_TMAX));
         h->ws_bytes += (long long)sizeof(double) * MTGP_TMAX * MTGP_TMAX;
     }
-    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1};
+    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1, h->dsi_mix ? h->bmix : nullptr};
     // the MLE solve leaves alpha, tau (sorted), the transformed spectra (equal sizes) or Pi (nested)
     rc = run_nll(h, th, false, h->out_tmp, nullptr, nullptr, nullptr, nullptr, nullptr, st, true);
     if (rc) return rc;
@@ -625,7 +662,7 @@ int mtgp_gcv_grad(mtgp_t* hs, const double* eta, const double* W, int s, const d
     int rc = validate_theta(h, eta, W, s, v, sigma2);
     if (rc) return rc;
     if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
-    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1};
+    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1, h->dsi_mix ? h->bmix : nullptr};
     return run_gcv_grad(h, th, out, tau, g_eta, g_W, g_v, g_sigma2, st);
 }
 
@@ -636,7 +673,7 @@ int mtgp_gcv(mtgp_t* hs, const double* eta, const double* W, int s, const double
     int rc = validate_theta(h, eta, W, s, v, sigma2);
     if (rc) return rc;
     if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
-    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1};
+    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1, h->dsi_mix ? h->bmix : nullptr};
     return run_gcv(h, th, out, tau, st);
 }
 
@@ -650,7 +687,7 @@ int mtgp_posterior(mtgp_t* hs, const double* eta, const double* W, int s, const 
     if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
     if (var && !h->equal) return fail(MTGP_ERR_UNSUPPORTED, "posterior variance needs equal task sizes in this build");
     if (nq == 0) return MTGP_OK;
-    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1};
+    ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1, h->dsi_mix ? h->bmix : nullptr};
     // the solve leaves alpha = Lambda^-1 rhat and tau in the workspace
     rc = run_nll(h, th, false, h->out_tmp, nullptr, nullptr, nullptr, nullptr, nullptr, st, true);
     if (rc) return rc;

@@ -71,7 +71,7 @@ __device__ __forceinline__ S si2_kernel(uint32_t X) {
 }
 
 template <typename S>
-__device__ __forceinline__ S pow2_neg(int b);  // 2^-b for 0 <= b <= 64
+__device__ __forceinline__ S pow2_neg(int b);  // 2^-b for 0 <= b <= 96
 template <>
 __device__ __forceinline__ float pow2_neg<float>(int b) { return __int_as_float((127 - b) << 23); }
 template <>
@@ -144,6 +144,58 @@ __device__ __forceinline__ S kernel1d(int kind, uint32_t X, int alpha = 2) {
     return dsi2_kernel<S>(X);
 }
 
+// Binary digits x_1..x_21 of x = X / 2^32 spread three bits apart: bit 3 (21 - a) holds x_a, so the
+// word times 2^-60 is sum_{a <= 21} x_a 8^{1-a} (the standard Morton bit-interleave masks).
+__device__ __forceinline__ unsigned long long spread3_top21(uint32_t X) {
+    unsigned long long v = (unsigned long long)(X >> 11);
+    v = (v | (v << 32)) & 0x001F00000000FFFFull;
+    v = (v | (v << 16)) & 0x001F0000FF0000FFull;
+    v = (v | (v << 8)) & 0x100F00F00F00F00Full;
+    v = (v | (v << 4)) & 0x10C30C30C30C30C3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+// The four orders of the adaptive-smoothness DSI kernel (Eq. 2.6) at x = X / 2^32, with
+// beta = clz(X) + 1, t_nu = 2^(-nu beta) and beta(0) = t_nu(0) = 0:
+//   K1 = 1/6 - t1/2   (the order-one Walsh kernel: the printed form is read with mean zero)
+//   K2 = 3/2 - beta x - 5/2 t1
+//   K3 = 25/18 + beta x^2 - 5 x + 5 t1 x - 43/18 t2
+//   K4 = 407/294 - 2/3 beta x^3 + 5 x^2 - 5 t1 x^2 - 43/9 x + 43/9 t2 x - 701/294 t3 + beta (D/48 - 1/42),
+// D = sum_{a >= 1} (1 - 2 x_a) 8^(1-a) = 8/7 - 2 sum_a x_a 8^(1-a); digits past the 21st move D by
+// less than 2^-61 and are dropped.
+template <typename S>
+__device__ __forceinline__ void dsi_orders(uint32_t X, S k[4]) {
+    if (X == 0u) {
+        k[0] = (S)(1.0 / 6.0);
+        k[1] = (S)1.5;
+        k[2] = (S)(25.0 / 18.0);
+        k[3] = (S)(407.0 / 294.0);
+        return;
+    }
+    const int b = __clz(X) + 1;
+    const S bs = (S)b;
+    const S x = (S)X * (S)MTGP_2POW_M32;
+    const S t1 = pow2_neg<S>(b), t2 = pow2_neg<S>(2 * b), t3 = pow2_neg<S>(3 * b);
+    const S x2 = x * x;
+    k[0] = (S)(1.0 / 6.0) - (S)0.5 * t1;
+    k[1] = (S)1.5 - bs * x - (S)2.5 * t1;
+    k[2] = (S)(25.0 / 18.0) + bs * x2 - (S)5 * x + (S)5 * t1 * x - (S)(43.0 / 18.0) * t2;
+    const S D = (S)(8.0 / 7.0) - (S)2 * ((S)spread3_top21(X) * pow2_neg<S>(60));
+    k[3] = (S)(407.0 / 294.0) - (S)(2.0 / 3.0) * bs * x2 * x + (S)5 * x2 * ((S)1 - t1)
+         - (S)(43.0 / 9.0) * x * ((S)1 - t2) - (S)(701.0 / 294.0) * t3 + bs * (D * (S)(1.0 / 48.0) - (S)(1.0 / 42.0));
+}
+
+// Univariate kernel of a handle: the DSI mixture sum_a b_a K_a when weights b are given (digital
+// nets), else the single kernel of kernel1d.
+template <typename S>
+__device__ __forceinline__ S kernel1d_b(int kind, uint32_t X, int alpha, const S* b) {
+    if (b == nullptr) return kernel1d<S>(kind, X, alpha);
+    S k[4];
+    dsi_orders<S>(X, k);
+    return b[0] * k[0] + b[1] * k[1] + b[2] * k[2] + b[3] * k[3];
+}
+
 // Point z_i (unshifted) in coordinate j.  Lattice (Def. 2.1): v(i) g mod 1 = bitrev32(i) * g
 // mod 2^32.  Digital net (Def. 2.2): XOR of generating-matrix columns g_p for the set bits of i.
 __device__ __forceinline__ uint32_t point_word(int kind, uint32_t i, int j, const uint32_t* gen,
@@ -186,6 +238,7 @@ struct ThetaPtrs {
     const double* v;
     const double* sigma2;
     int nsig;  // noise values: 1 (shared sigma2) or T (per task, caller order); 0 reads as 1
+    const double* bmix;  // DSI mixture weights b (4), or nullptr for the order-2 kernel alone
 };
 
 // noise variance of sorted task t
@@ -308,6 +361,8 @@ struct Handle {
     bool y_set;
     int smooth;          // SI kernel smoothness alpha of Eq. 2.5 (lattices; 2 unless set)
     bool noise_pt;       // one noise variance per task (general path only)
+    bool dsi_mix;        // digital nets: DSI mixture weights b set (general path only)
+    double* bmix;        // device: b (4 doubles) then dL/db of the last gradient call (4 doubles)
 };
 
 // columns of the per-block partial sums of the general solvers: [log det, quad, trace G, Gamma (T(T+1)/2)]

@@ -105,8 +105,26 @@ class MTGP:
         return outs
 
     def set_smoothness(self, alpha: int) -> None:
-        """SI kernel smoothness alpha (1..4) of a lattice handle (Eq. 2.5)."""
+        """Kernel smoothness alpha (1..4): the SI kernel of Eq. 2.5 (lattices) or the single order
+        K_alpha of the DSI kernel of Eq. 2.6 (digital nets)."""
         check(lib().mtgp_set_smoothness(self._h, int(alpha)), "mtgp_set_smoothness")
+
+    def set_dsi_weights(self, b, stream=None) -> None:
+        """Mixture weights b (4, >= 0) of the adaptive-smoothness DSI kernel (Eq. 2.6, digital nets);
+        None returns to the order-2 kernel alone."""
+        if b is None:
+            self._b = None
+            check(lib().mtgp_set_dsi_weights(self._h, None, _stream(stream)), "mtgp_set_dsi_weights")
+            return
+        b = _dev(b).reshape(4)
+        self._b = b
+        check(lib().mtgp_set_dsi_weights(self._h, _ptr(b), _stream(stream)), "mtgp_set_dsi_weights")
+
+    def dsi_weights_grad(self, stream=None) -> torch.Tensor:
+        """Gradient with respect to b (4,) from the last nll_grad (of the NLL) or gcv_grad call."""
+        g = torch.empty(4, dtype=torch.float64, device="cuda")
+        check(lib().mtgp_dsi_weights_grad(self._h, _ptr(g), _stream(stream)), "mtgp_dsi_weights_grad")
+        return g
 
     def gcv(self, eta, W, v, sigma2, stream=None):
         """Returns (out, tau): out = [L_GCV, r^T K~^-2 r, trace K~^-1] (device float64), tau (T,) at

@@ -344,9 +344,10 @@ def test_smoothness_argument_checks():
     from paper_2603_16014_gb300._lib import MTGPError
     p = inputs.make_problem("dnet", 2, (5, 5), seed=3)
     model = _model(p, "fp64")
-    with pytest.raises(MTGPError) as ei:
-        model.set_smoothness(3)
-    assert ei.value.code == 5
+    for bad in (0, 5):
+        with pytest.raises(MTGPError) as ei:
+            model.set_smoothness(bad)
+        assert ei.value.code == 1
     q = inputs.make_problem("lattice", 2, (5, 5), seed=3)
     mq = _model(q, "fp64")
     with pytest.raises(MTGPError) as ei:

@@ -123,3 +123,18 @@ def test_mixture_weight_gradient_matches_central_differences(loss):
         assert abs(fd - g_eta[j]) < 1e-5 * (1 + abs(g_eta[j]))
     # homogeneity: scaling b by c and eta by 1/c leaves K unchanged, so b.g_b = eta.g_eta
     assert float(b @ g_b) == pytest.approx(float(p.eta @ g_eta), rel=1e-9, abs=1e-9)
+
+
+def test_spectral_mixture_gradient_matches_dense():
+    from oracle import spectral
+    p = inputs.make_problem("dnet", 3, (5, 5, 5), seed=33, eta=0.6, v=0.2, sigma2=1e-3, s=2)
+    X = dense.all_points(p.kind, p.gen, p.shift, p.m)
+    y = inputs.synth_y(p, X)
+    b = np.array([0.3, 1.0, 0.5, 0.2])
+    out, ge, gW, gv, gs, gb = spectral.nll_grad_equal(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2, b)
+    ref, re, rW, rv, rs = dense.nll_grad(p.kind, X, y, p.eta, p.W, p.v, p.sigma2, b)
+    _, rb = dense.dsi_weights_grad(p.kind, X, y, p.eta, p.W, p.v, p.sigma2, b)
+    assert out["L"] == pytest.approx(ref["L"], rel=1e-11)
+    got = np.concatenate([ge, gW.ravel(), gv, [gs], gb])
+    exp = np.concatenate([re, rW.ravel(), rv, [rs], rb])
+    assert np.allclose(got, exp, rtol=1e-8, atol=1e-9 * np.abs(exp).max())
