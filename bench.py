@@ -267,28 +267,21 @@ def run_ours(args, rank, world, local_rank):
     ms_per_step = total_ms / K
     value = replica_throughput(K, world, total_ms)
 
-    # ---- end to end through the public API: theta from pinned host memory, results back to host.
-    # The parameters travel as one packed buffer and the results come back as one (two copies per
-    # step); the C ABI takes the device views.
-    sizes = [t.numel() for t in th]
-    osizes = [o.numel() for o in outs]
-    h_theta = torch.cat([torch.as_tensor(a, dtype=torch.float64).reshape(-1) for a in (p.eta, p.W, p.v, [p.sigma2])]).pin_memory()
-    d_theta = torch.empty_like(h_theta, device="cuda")
-    th_v = [v.view(t.shape) for v, t in zip(torch.split(d_theta, sizes), th)]
-    d_out = torch.empty(sum(osizes), dtype=torch.float64, device="cuda")
-    outs_v = tuple(v.view(o.shape) for v, o in zip(torch.split(d_out, osizes), outs))
-    h_out = torch.empty(sum(osizes), dtype=torch.float64).pin_memory()
+    # ---- end to end through the public API: theta from pinned host memory, results back to host,
+    # through the C ABI's host-buffer call (copy in, evaluate, copy out, all in stream order).
+    s_cols = p.W.shape[1]
+    h_theta = model.pack_theta(p.eta, p.W, p.v, p.sigma2)
+    h_out = model.host_out(s_cols)
     e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     torch.cuda.synchronize()
     for i in range(K):
         e2e_ev[i][0].record(stream)
-        d_theta.copy_(h_theta, non_blocking=True)
-        model.nll_grad(*th_v, outs=outs_v)
-        h_out.copy_(d_out, non_blocking=True)
+        model.nll_grad_host(h_theta, h_out, s_cols)
         e2e_ev[i][1].record(stream)
         stream.synchronize()
         flush.fill_(float(i))
     torch.cuda.synchronize()
+    model.sync()
     e2e_total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev), dist, "cuda")
     assert abs(h_out[0].item() - outs[0][0].item()) <= 1e-12 * abs(outs[0][0].item())
     h2d = h_theta.numel() * 8

@@ -123,6 +123,22 @@ int mtgp_nll_grad(mtgp_t* h, const double* eta, const double* W, int s, const do
                   double* g_v, double* g_sigma2, cudaStream_t stream);
 
 /*
+ * mtgp_nll_grad_host -- mtgp_nll_grad with HOST buffers: the call copies theta in, evaluates and
+ * copies the results out, all in stream order on `stream` (asynchronous for page-locked host
+ * memory; the caller keeps both buffers alive and calls mtgp_sync before reading `out`).
+ *   theta  host, packed eta (d) | W (T x s, caller task order, row-major) | v (T) | sigma2 (1, or T
+ *          with MTGP_NOISE_PER_TASK): d + T s + T + (1 or T) doubles.
+ *   out    host, packed [NLL, quad, logdet] (3) | tau (T) | g_eta (d) | g_W (T x s) | g_v (T) |
+ *          g_sigma2 (1 or T): 3 + T + (size of theta) doubles.
+ * The device staging buffer belongs to the handle: calls on one handle are ordered by their
+ * stream (two streams on one handle race).  With page-locked buffers and profiling off, the first
+ * call for a given (theta, out, s) and kernel configuration captures the sequence into a CUDA
+ * graph owned by the handle and later calls replay it (one launch); pageable buffers take the
+ * direct launches.  Errors as mtgp_nll_grad.
+ */
+int mtgp_nll_grad_host(mtgp_t* h, const double* theta, int s, double* out, cudaStream_t stream);
+
+/*
  * mtgp_posterior -- posterior mean and variance of f(t, x) (Eq. 3.2) at nq queries, with the
  * prior mean tau at its MLE optimum.
  *   xq     nq x d doubles in [0, 1] (row-major); each is mapped to the fixed-point word

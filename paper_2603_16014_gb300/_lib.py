@@ -50,6 +50,7 @@ _SIGS = {
     "mtgp_gcv": (_i, [_p, _p, _p, _i, _p, _p, _p, _p, _p]),
     "mtgp_set_smoothness": (_i, [_p, _i]),
     "mtgp_set_dsi_weights": (_i, [_p, _p, _p]),
+    "mtgp_nll_grad_host": (_i, [_p, _p, _i, _p, _p]),
     "mtgp_dsi_weights_grad": (_i, [_p, _p, _p]),
     "mtgp_cubature": (_i, [_p, _p, _p, _i, _p, _p, _p, _p, _p]),
     "mtgp_gcv_grad": (_i, [_p, _p, _p, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p]),

@@ -43,12 +43,16 @@ __device__ void load_R_f(double* sR, const FusedParams& p, const ThetaPtrs& th) 
     }
 }
 
-// totals of the ncols columns of an (nrows x ncols) partial array into out[q]: warp w sums columns
-// q = w, w + nwarps, ...; lane l adds rows l, l + 32, ... (fixed order), then a shuffle tree.
-// The loads of 8 rows are issued before their additions (same order, one memory round trip per 8).
-__device__ void reduce_columns(const double* part, int nrows, int ncols, double* out) {
+// Column totals of one or two (nrows x ncols) partial arrays (fixed order): warp w sums columns
+// w, w + nw, ... of the two arrays in turn; column q's lane l adds rows l, l + 32, ... (the loads of
+// 8 rows are issued before their additions: one memory round trip per 8), then a shuffle tree.
+__device__ void reduce_columns2(const double* part1, int nrows1, int ncols1, double* out1, const double* part2,
+                                int nrows2, int ncols2, double* out2) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int q = warp; q < ncols; q += nw) {
+    for (int qq = warp; qq < ncols1 + ncols2; qq += nw) {
+        const bool first = qq < ncols1;
+        const double* part = first ? part1 : part2;
+        const int nrows = first ? nrows1 : nrows2, ncols = first ? ncols1 : ncols2, q = first ? qq : qq - ncols1;
         double v = 0.0;
         for (int b0 = lane; b0 < nrows; b0 += 256) {
             double t[8];
@@ -61,9 +65,13 @@ __device__ void reduce_columns(const double* part, int nrows, int ncols, double*
             for (int k = 0; k < 8; ++k) v += t[k];
         }
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) out[q] = v;
+        if (lane == 0) (first ? out1 : out2)[q] = v;
     }
     __syncthreads();
+}
+
+__device__ void reduce_columns(const double* part, int nrows, int ncols, double* out) {
+    reduce_columns2(part, nrows, ncols, out, nullptr, 0, 0, nullptr);
 }
 
 // last-block election: true in exactly one block, after all blocks have written their partials
@@ -111,57 +119,37 @@ struct FitDesc {
 
 __device__ __forceinline__ int gq(int t, int u, int T) { return t * T - t * (t - 1) / 2 + (u - t); }
 
-// final outputs from the totals (thread 0)
+// Final outputs from the totals, written by all threads of the block (W and the sorted means are
+// read into shared memory first, every output has its own thread).
 __device__ void write_outputs(const double* tot, const double* etot, const FusedParams& p, const ThetaPtrs& th,
                               const double* tau_sorted, OutPtrs o) {
+    __shared__ double s_W[MTGP_TMAX * MTGP_TMAX];
+    const int T = p.T, tid = threadIdx.x;
     const double LOG2PI = 1.8378770664093453;
-    o.out[0] = 0.5 * (tot[0] + tot[1] + (double)p.N * LOG2PI);
-    o.out[1] = tot[1];
-    o.out[2] = tot[0];
-    if (o.tau)
-        for (int t = 0; t < p.T; ++t) o.tau[p.order[t]] = tau_sorted[t];
+    if (p.grad)
+        for (int e = tid; e < T * th.s; e += blockDim.x) s_W[e] = th.W[e];
+    if (tid == 0) {
+        o.out[0] = 0.5 * (tot[0] + tot[1] + (double)p.N * LOG2PI);
+        o.out[1] = tot[1];
+        o.out[2] = tot[0];
+    }
+    if (o.tau && tid < T) o.tau[p.order[tid]] = tau_sorted[tid];
     if (!p.grad) return;
-    const int T = p.T;
-    o.g_s2[0] = 0.5 * tot[2];
-    for (int j = 0; j < p.d; ++j) o.g_eta[j] = 0.5 * etot[j];
-    for (int tc = 0; tc < T; ++tc) {
-        int t = p.rank[tc];
-        for (int k = 0; k < th.s; ++k) {
-            double g = 0.0;
-            for (int uc = 0; uc < T; ++uc) {
-                int u = p.rank[uc];
-                double G = (t <= u) ? tot[3 + gq(t, u, T)] : tot[3 + gq(u, t, T)];
-                g += G * th.W[uc * th.s + k];
-            }
-            o.g_W[tc * th.s + k] = g;
-        }
-        o.g_v[tc] = 0.5 * tot[3 + gq(t, t, T)];
-    }
-}
-
-// two partial arrays reduced in one pass: warps take the columns of both in turn
-__device__ void reduce_columns2(const double* part1, int nrows1, int ncols1, double* out1, const double* part2,
-                                int nrows2, int ncols2, double* out2) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int qq = warp; qq < ncols1 + ncols2; qq += nw) {
-        const bool first = qq < ncols1;
-        const double* part = first ? part1 : part2;
-        const int nrows = first ? nrows1 : nrows2, ncols = first ? ncols1 : ncols2, q = first ? qq : qq - ncols1;
-        double v = 0.0;
-        for (int b0 = lane; b0 < nrows; b0 += 256) {
-            double t[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int b = b0 + 32 * k;
-                t[k] = b < nrows ? part[(long long)b * ncols + q] : 0.0;
-            }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) v += t[k];
-        }
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) (first ? out1 : out2)[q] = v;
-    }
     __syncthreads();
+    if (tid == 0) o.g_s2[0] = 0.5 * tot[2];
+    if (tid < p.d) o.g_eta[tid] = 0.5 * etot[tid];
+    for (int e = tid; e < T * th.s; e += blockDim.x) {
+        const int tc = e / th.s, k = e - tc * th.s;
+        const int t = p.rank[tc];
+        double g = 0.0;
+        for (int uc = 0; uc < T; ++uc) {
+            const int u = p.rank[uc];
+            const double G = (t <= u) ? tot[3 + gq(t, u, T)] : tot[3 + gq(u, t, T)];
+            g += G * s_W[uc * th.s + k];
+        }
+        o.g_W[e] = g;
+    }
+    if (tid < T) o.g_v[tid] = 0.5 * tot[3 + gq(p.rank[tid], p.rank[tid], T)];
 }
 
 // ---------------------------------------------------------------------------------- kernel A
@@ -433,10 +421,8 @@ __device__ __forceinline__ void fused_b_body(const FitDesc& f, int blk) {
     if (p.grad) return;  // kernel C finishes
     if (!last_block(counter, f.nb)) return;
     reduce_columns(partials, f.nb, NQ, s_tot);
-    if (threadIdx.x == 0) {
-        write_outputs(s_tot, nullptr, p, th, tau_sorted, f.o);
-        *counter = 0u;
-    }
+    write_outputs(s_tot, nullptr, p, th, tau_sorted, f.o);
+    if (threadIdx.x == 0) *counter = 0u;
 }
 
 // ---------------------------------------------------------------------------------- kernel C
@@ -547,10 +533,8 @@ __device__ __forceinline__ void fused_c_body(const FitDesc& f, int blk) {
     if (!last_block(counter, f.na)) return;
     const int NQ = 3 + p.T * (p.T + 1) / 2;
     reduce_columns2(partials_b, nb, NQ, s_tot, partials_c, f.na, d, s_etot);
-    if (threadIdx.x == 0) {
-        write_outputs(s_tot, s_etot, p, th, tau_sorted, f.o);
-        *counter = 0u;
-    }
+    write_outputs(s_tot, s_etot, p, th, tau_sorted, f.o);
+    if (threadIdx.x == 0) *counter = 0u;
 }
 
 // ---------------------------------------------------------------------------------- kernels

@@ -196,9 +196,13 @@ cudaError_t dalloc(Handle* h, T** p, size_t count) {
 void free_all(Handle* h) {
     void* ptrs[] = {h->gen, h->shift, h->cols_dev, h->offs_dev, h->yoffs_dev, h->twid, h->twid32, h->yhat, h->spec,
                     h->wgt, h->S, h->Z, h->r, h->alpha, h->tau, h->partials, h->status, h->out_tmp, h->counters,
-                    h->gcv_h, h->pi_buf, h->bmix};
+                    h->gcv_h, h->pi_buf, h->bmix, h->hio};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (h->hio_exec) cudaGraphExecDestroy(h->hio_exec);
+    h->hio_exec = nullptr;
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
     if (h->prof) {
         for (auto& r : h->prof->recs) {
             cudaEventDestroy(r.a);
@@ -421,6 +425,7 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
     AL(h->out_tmp, (size_t)4);
     AL(h->counters, (size_t)4);
     AL(h->bmix, (size_t)8);
+    AL(h->hio, (size_t)(2 * (d + T * T + 2 * T) + 3 + T));
 #undef AL
     h->prof = new Prof();
     // upload descriptors
@@ -468,6 +473,7 @@ int mtgp_set_smoothness(mtgp_t* hs, int alpha) {
     if (!hs) return fail(MTGP_ERR_INVALID_ARG, "NULL handle");
     Handle* h = &hs->h;
     if (alpha < 1 || alpha > 4) return fail(MTGP_ERR_INVALID_ARG, "smoothness must be 1, 2, 3 or 4");
+    ++h->cfg_gen;
     if (h->kind == MTGP_LATTICE) {
         h->smooth = alpha;
         return MTGP_OK;
@@ -489,6 +495,7 @@ int mtgp_set_dsi_weights(mtgp_t* hs, const double* b, cudaStream_t st) {
     if (!hs) return fail(MTGP_ERR_INVALID_ARG, "NULL handle");
     Handle* h = &hs->h;
     if (h->kind != MTGP_DNET) return fail(MTGP_ERR_UNSUPPORTED, "mixture weights apply to digital nets (Eq. 2.6)");
+    ++h->cfg_gen;
     if (!b) {
         h->dsi_mix = false;
         return MTGP_OK;
@@ -549,6 +556,86 @@ int mtgp_nll_grad(mtgp_t* hs, const double* eta, const double* W, int s, const d
     if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
     ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1, h->dsi_mix ? h->bmix : nullptr};
     return run_nll(h, th, true, out, tau, g_eta, g_W, g_v, g_sigma2, st);
+}
+
+// copy in, evaluate, copy out on stream st (the direct launches of the host-buffer entry point)
+static int enqueue_nll_grad_host(Handle* h, const double* theta, int s, double* out, cudaStream_t st) {
+    const int d = h->d, T = h->T, nsig = h->noise_pt ? T : 1;
+    const size_t nth = (size_t)d + (size_t)T * s + T + nsig;
+    const size_t nout = 3 + (size_t)T + nth;
+    double* dth = h->hio;
+    double* dout = h->hio + nth;
+    CK(cudaMemcpyAsync(dth, theta, nth * sizeof(double), cudaMemcpyHostToDevice, st));
+    ThetaPtrs th{dth, dth + d, s, dth + d + (size_t)T * s, dth + d + (size_t)T * s + T, nsig,
+                 h->dsi_mix ? h->bmix : nullptr};
+    double* g = dout + 3 + T;
+    int rc = run_nll(h, th, true, dout, dout + 3, g, g + d, g + d + (size_t)T * s, g + d + (size_t)T * s + T, st);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(out, dout, nout * sizeof(double), cudaMemcpyDeviceToHost, st));
+    return MTGP_OK;
+}
+
+static void drop_hio_graph(Handle* h) {
+    if (h->hio_exec) cudaGraphExecDestroy(h->hio_exec);
+    h->hio_exec = nullptr;
+}
+
+// capture the copy-in / kernels / copy-out sequence into h->hio_exec; false if the capture fails
+static bool capture_hio_graph(Handle* h, const double* theta, int s, double* out) {
+    drop_hio_graph(h);
+    if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        h->cap_stream = nullptr;
+        return false;
+    }
+    if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    const int rc = enqueue_nll_grad_host(h, theta, s, out, h->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
+    bool ok = rc == MTGP_OK && ec == cudaSuccess && graph != nullptr;
+    if (ok) ok = cudaGraphInstantiate(&h->hio_exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        h->hio_exec = nullptr;
+        cudaGetLastError();  // the failed capture's error is not the caller's
+    }
+    return ok;
+}
+
+// page-locked (or registered) host memory: the only kind a captured copy may use
+static bool host_pinned(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+int mtgp_nll_grad_host(mtgp_t* hs, const double* theta, int s, double* out, cudaStream_t st) {
+    if (!hs || !theta || !out) return fail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    Handle* h = &hs->h;
+    if (s < 1 || s > h->T) return fail(MTGP_ERR_INVALID_ARG, "s must satisfy 1 <= s <= T");
+    if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
+    const bool profiling = h->prof && h->prof->on;
+    if (!profiling && !h->hio_nograph) {
+        const bool same = h->hio_key_valid && h->hio_key_th == theta && h->hio_key_out == out &&
+                          h->hio_key_s == s && h->hio_key_gen == h->cfg_gen;
+        if (!same) {
+            drop_hio_graph(h);
+            h->hio_key_valid = true;
+            h->hio_key_th = theta;
+            h->hio_key_out = out;
+            h->hio_key_s = s;
+            h->hio_key_gen = h->cfg_gen;
+            // pageable buffers take the direct launches; a failed capture disables graphs for the handle
+            if (host_pinned(theta) && host_pinned(out) && !capture_hio_graph(h, theta, s, out)) h->hio_nograph = true;
+        }
+        if (h->hio_exec) {
+            CK(cudaGraphLaunch(h->hio_exec, st));
+            return MTGP_OK;
+        }
+    }
+    return enqueue_nll_grad_host(h, theta, s, out, st);
 }
 
 // GCV loss at the GCV mean: generic path (column generation, transforms, per-frequency or tree

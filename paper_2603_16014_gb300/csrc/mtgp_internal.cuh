@@ -363,6 +363,18 @@ struct Handle {
     bool noise_pt;       // one noise variance per task (general path only)
     bool dsi_mix;        // digital nets: DSI mixture weights b set (general path only)
     double* bmix;        // device: b (4 doubles) then dL/db of the last gradient call (4 doubles)
+    double* hio;         // device staging of the host-buffer entry point: packed theta, then outputs
+    // the host-buffer entry point replays one CUDA graph (copy in, kernels, copy out) per
+    // (theta, out, s, configuration); any call that changes which kernels run bumps cfg_gen
+    unsigned cfg_gen;
+    cudaStream_t cap_stream;
+    cudaGraphExec_t hio_exec;
+    const void* hio_key_th;
+    void* hio_key_out;
+    int hio_key_s;
+    unsigned hio_key_gen;
+    bool hio_key_valid;
+    bool hio_nograph;    // capture failed once: the direct launches are used from then on
 };
 
 // columns of the per-block partial sums of the general solvers: [log det, quad, trace G, Gamma (T(T+1)/2)]

@@ -158,6 +158,35 @@ class MTGP:
                                   _stream(stream)), "mtgp_cubature")
         return mu, Sigma
 
+    # ------------------------------------------------------------ host-buffer entry point
+    def pack_theta(self, eta, W, v, sigma2, pin=True) -> torch.Tensor:
+        """Packed host theta of mtgp_nll_grad_host: eta | W (T x s) | v | sigma2 (1 or T)."""
+        parts = [np.asarray(eta, dtype=np.float64).reshape(-1), np.asarray(W, dtype=np.float64).reshape(-1),
+                 np.asarray(v, dtype=np.float64).reshape(-1), np.asarray(sigma2, dtype=np.float64).reshape(self.nsig)]
+        t = torch.from_numpy(np.concatenate(parts))
+        return t.pin_memory() if pin else t
+
+    def host_out(self, s, pin=True) -> torch.Tensor:
+        """Host output buffer of mtgp_nll_grad_host for W with s columns."""
+        n = 3 + self.T + self.d + self.T * s + self.T + self.nsig
+        t = torch.empty(n, dtype=torch.float64)
+        return t.pin_memory() if pin else t
+
+    def unpack_out(self, out, s):
+        """(out3, tau, g_eta, g_W, g_v, g_sigma2) views of a filled host output buffer."""
+        T, d = self.T, self.d
+        sizes = [3, T, d, T * s, T, self.nsig]
+        o = torch.split(out, sizes)
+        return o[0], o[1], o[2], o[3].view(T, s), o[4], o[5]
+
+    def nll_grad_host(self, theta, out, s, stream=None) -> None:
+        """NLL and gradient with host buffers (theta packed as pack_theta, out as host_out): copy in,
+        evaluate, copy out, all in stream order; call sync() before reading ``out``."""
+        assert theta.device.type == "cpu" and out.device.type == "cpu"
+        assert theta.dtype == torch.float64 and out.dtype == torch.float64
+        check(lib().mtgp_nll_grad_host(self._h, ctypes.c_void_p(theta.data_ptr()), int(s),
+                                       ctypes.c_void_p(out.data_ptr()), _stream(stream)), "mtgp_nll_grad_host")
+
     def posterior(self, eta, W, v, sigma2, xq, task, variance=True, stream=None):
         eta, W, v, s2 = self._theta(eta, W, v, sigma2)
         xq = _dev(xq).reshape(-1, self.d)

@@ -353,3 +353,53 @@ def test_smoothness_argument_checks():
     with pytest.raises(MTGPError) as ei:
         mq.set_smoothness(7)
     assert ei.value.code == 1
+
+
+@pytest.mark.parametrize("kind,d,m,pt", [("dnet", 3, (6, 6, 6), False), ("lattice", 2, (6, 4, 3), False),
+                                         ("dnet", 2, (5, 5), True)])
+def test_host_buffer_entry_point_matches_device_call(kind, d, m, pt):
+    # mtgp_nll_grad_host: packed host theta in, packed host results out, same values as the device call
+    from paper_2603_16014_gb300.mtgp import MTGP
+    p = inputs.make_problem(kind, d, m, seed=81, eta=0.6, v=0.2, sigma2=1e-4, s=2)
+    X = _points_oracle(p)
+    y = inputs.synth_y(p, X)
+    model = MTGP.from_problem(p, "fp64", noise_per_task=pt)
+    model.set_y(torch.from_numpy(y))
+    s2 = np.array([1e-4, 3e-4, 2e-4][:p.T]) if pt else p.sigma2
+    ref = [t.cpu().numpy() for t in model.nll_grad(p.eta, p.W, p.v, s2)]
+    h_th = model.pack_theta(p.eta, p.W, p.v, s2)
+    h_out = model.host_out(p.W.shape[1])
+    h_out.fill_(np.nan)
+    model.nll_grad_host(h_th, h_out, p.W.shape[1])
+    model.sync()
+    got = [t.numpy() for t in model.unpack_out(h_out, p.W.shape[1])]
+    for a, b in zip(got, ref):
+        assert np.array_equal(a.reshape(-1), b.reshape(-1))
+    dref, ge, gW, gv, gs = dense.nll_grad(p.kind, X, y, p.eta, p.W, p.v, s2)
+    assert abs(got[0][0] - dref["nll"]) <= 1e-8 * abs(dref["nll"])
+    # later calls replay the captured sequence and read the host buffer's current contents
+    v2 = p.v * 1.5
+    h_th.copy_(model.pack_theta(p.eta, p.W, v2, s2, pin=False))
+    model.nll_grad_host(h_th, h_out, p.W.shape[1])
+    model.sync()
+    ref2 = [t.cpu().numpy() for t in model.nll_grad(p.eta, p.W, v2, s2)]
+    for a, b in zip(model.unpack_out(h_out, p.W.shape[1]), ref2):
+        assert np.array_equal(a.numpy().reshape(-1), b.reshape(-1))
+    # a kernel-configuration change takes effect (digital nets: order 3 of Eq. 2.6)
+    if kind == "dnet":
+        model.set_smoothness(3)
+        model.nll_grad_host(h_th, h_out, p.W.shape[1])
+        model.sync()
+        ref3 = [t.cpu().numpy() for t in model.nll_grad(p.eta, p.W, v2, s2)]
+        for a, b in zip(model.unpack_out(h_out, p.W.shape[1]), ref3):
+            assert np.array_equal(a.numpy().reshape(-1), b.reshape(-1))
+        assert abs(ref3[0][0] - ref2[0][0]) > 1e-6 * abs(ref2[0][0])
+    # pageable host buffers take the direct launches
+    p_th = model.pack_theta(p.eta, p.W, v2, s2, pin=False)
+    p_out = model.host_out(p.W.shape[1], pin=False)
+    model.nll_grad_host(p_th, p_out, p.W.shape[1])
+    model.sync()
+    assert np.array_equal(p_out.numpy(), h_out.numpy())
+    with pytest.raises(Exception):
+        model.nll_grad_host(h_th, h_out, p.T + 1)    # s out of range: refused before any device work
+    model.close()
