@@ -33,7 +33,7 @@ WORKLOAD = "dnet_d8_T4_n2^16_nll_grad"
 FP64_PEAK_TFLOPS = 1.25       # GB300 dense FP64, nominal
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_fused_b launch on this workload, from one ncu
 # capture (caches flushed by ncu between passes); valid while the kernel is unchanged
-FUSED_B_DRAM_BYTES = 3998208
+FUSED_B_DRAM_BYTES = 3992320
 L2_FLUSH_BYTES = 256 << 20
 
 

@@ -131,10 +131,12 @@ int mtgp_nll_grad(mtgp_t* h, const double* eta, const double* W, int s, const do
  *   out    host, packed [NLL, quad, logdet] (3) | tau (T) | g_eta (d) | g_W (T x s) | g_v (T) |
  *          g_sigma2 (1 or T): 3 + T + (size of theta) doubles.
  * The device staging buffer belongs to the handle: calls on one handle are ordered by their
- * stream (two streams on one handle race).  With page-locked buffers and profiling off, the first
- * call for a given (theta, out, s) and kernel configuration captures the sequence into a CUDA
- * graph owned by the handle and later calls replay it (one launch); pageable buffers take the
- * direct launches.  Errors as mtgp_nll_grad.
+ * stream (two streams on one handle race).  Page-locked buffers are reached by the kernels
+ * themselves (theta read by a one-block staging kernel, the results written by the kernels that
+ * produce them, no DMA copies); with profiling off, the first call for a given (theta, out, s) and
+ * kernel configuration captures the launches into a CUDA graph owned by the handle and later calls
+ * replay it (one launch).  Pageable buffers go through cudaMemcpyAsync, without a graph.  Errors
+ * as mtgp_nll_grad.
  */
 int mtgp_nll_grad_host(mtgp_t* h, const double* theta, int s, double* out, cudaStream_t stream);
 

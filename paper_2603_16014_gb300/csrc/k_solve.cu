@@ -669,72 +669,85 @@ struct FinParams {
     long long yoff[MTGP_TMAX];
 };
 
+// Column sums of a (nrows x ncols) partial array into out[q], by the whole block in a fixed order:
+// warp w takes columns w, w + nw, ...; lane l adds rows l, l + 32, ... (the loads of 8 rows are in
+// flight together), then a shuffle tree.
+__device__ void block_column_sums(const double* part, int nrows, int ncols, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = warp; q < ncols; q += nw) {
+        double v = 0.0;
+        for (int b0 = lane; b0 < nrows; b0 += 256) {
+            double t[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int b = b0 + 32 * k;
+                t[k] = b < nrows ? part[(long long)b * ncols + q] : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v += t[k];
+        }
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) out[q] = v;
+    }
+}
+
+// one block: totals of the solver and eta partials, then every output by its own thread
 __global__ void k_finalize(const double* partials, const double* eta_partials, const double* yhat,
                            const double* tau_sorted, FinParams p, ThetaPtrs th, double* out, double* tau,
                            double* g_eta, double* g_W, double* g_v, double* g_s2, double* g_b) {
     __shared__ double tot[3 + MTGP_MAX_COLS + MTGP_TMAX];
     __shared__ double etot[MTGP_MAX_DIM + 4];
-    for (int q = threadIdx.x; q < p.NQ; q += blockDim.x) {
-        double v = 0.0;
-        for (int b = 0; b < p.nsolve; ++b) v += partials[(long long)b * p.NQ + q];
-        tot[q] = v;
-    }
+    __shared__ double s_W[MTGP_TMAX * MTGP_TMAX];
+    const int tid = threadIdx.x, T = p.T;
+    block_column_sums(partials, p.nsolve, p.NQ, tot);
     if (p.grad) {
-        const int pw = p.d + (p.mix ? 4 : 0);
-        for (int j = threadIdx.x; j < pw; j += blockDim.x) {
-            double v = 0.0;
-            for (int b = 0; b < p.neta; ++b) v += eta_partials[(long long)b * pw + j];
-            etot[j] = v;
-        }
+        block_column_sums(eta_partials, p.neta, p.d + (p.mix ? 4 : 0), etot);
+        for (int e = tid; e < T * p.s; e += blockDim.x) s_W[e] = th.W[e];
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
     const double LOG2PI = 1.8378770664093453;
-    if (p.gcv == 2) {
-        // GCV gradient pass: the loss was written by the value pass
-    } else if (p.gcv) {
-        // GCV loss ||Lambda~^-1 rhat||^2 / trace(Lambda~^-1)^2, its numerator and the trace
-        out[0] = tot[2] / (tot[3] * tot[3]);
-        out[1] = tot[2];
-        out[2] = tot[3];
-    } else {
-        out[0] = 0.5 * (tot[0] + tot[1] + (double)p.N * LOG2PI);
-        out[1] = tot[1];
-        out[2] = tot[0];
-    }
-    if (tau) {
-        for (int t = 0; t < p.T; ++t) {
-            double tv;
-            if (p.equal) tv = yhat[(p.cplx ? 2 : 1) * p.yoff[t]] / sqrt((double)p.n0);
-            else tv = tau_sorted[t];
-            tau[p.order[t]] = tv;
+    if (tid == 0) {
+        if (p.gcv == 2) {
+            // GCV gradient pass: the loss was written by the value pass
+        } else if (p.gcv) {
+            // GCV loss ||Lambda~^-1 rhat||^2 / trace(Lambda~^-1)^2, its numerator and the trace
+            out[0] = tot[2] / (tot[3] * tot[3]);
+            out[1] = tot[2];
+            out[2] = tot[3];
+        } else {
+            out[0] = 0.5 * (tot[0] + tot[1] + (double)p.N * LOG2PI);
+            out[1] = tot[1];
+            out[2] = tot[0];
         }
     }
+    if (tau && tid < T) {
+        double tv;
+        if (p.equal) tv = yhat[(p.cplx ? 2 : 1) * p.yoff[tid]] / sqrt((double)p.n0);
+        else tv = tau_sorted[tid];
+        tau[p.order[tid]] = tv;
+    }
     if (!p.grad) return;
-    const int T = p.T;
     // MLE: gradients of NLL = L / 2; GCV: gradients of the loss itself
     const double sc = (p.gcv == 2) ? 2.0 : 1.0;
     if (p.pt) {
-        for (int tc = 0; tc < T; ++tc) g_s2[tc] = 0.5 * sc * tot[3 + T * (T + 1) / 2 + p.rank[tc]];
-    } else {
+        if (tid < T) g_s2[tid] = 0.5 * sc * tot[3 + T * (T + 1) / 2 + p.rank[tid]];
+    } else if (tid == 0) {
         g_s2[0] = 0.5 * sc * tot[2];
     }
-    for (int j = 0; j < p.d; ++j) g_eta[j] = 0.5 * sc * etot[j];
-    if (p.mix)
-        for (int a = 0; a < 4; ++a) g_b[a] = 0.5 * sc * etot[p.d + a];
-    for (int tc = 0; tc < T; ++tc) {
-        int t = p.rank[tc];
-        for (int k = 0; k < p.s; ++k) {
-            double g = 0.0;
-            for (int uc = 0; uc < T; ++uc) {
-                int u = p.rank[uc];
-                double G = (t <= u) ? tot[3 + gidx(t, u, T)] : tot[3 + gidx(u, t, T)];
-                g += G * th.W[uc * p.s + k];
-            }
-            g_W[tc * p.s + k] = sc * g;
+    if (tid < p.d) g_eta[tid] = 0.5 * sc * etot[tid];
+    if (p.mix && tid < 4) g_b[tid] = 0.5 * sc * etot[p.d + tid];
+    for (int e = tid; e < T * p.s; e += blockDim.x) {
+        const int tc = e / p.s, k = e - tc * p.s;
+        const int t = p.rank[tc];
+        double g = 0.0;
+        for (int uc = 0; uc < T; ++uc) {
+            const int u = p.rank[uc];
+            const double G = (t <= u) ? tot[3 + gidx(t, u, T)] : tot[3 + gidx(u, t, T)];
+            g += G * s_W[uc * p.s + k];
         }
-        g_v[tc] = 0.5 * sc * tot[3 + gidx(t, t, T)];
+        g_W[e] = sc * g;
     }
+    if (tid < T) g_v[tid] = 0.5 * sc * tot[3 + gidx(p.rank[tid], p.rank[tid], T)];
 }
 
 int eq_blocks(const Handle* h) {
@@ -846,6 +859,6 @@ void launch_finalize(const Handle* h, ThetaPtrs th, bool grad, const double* par
         fp.rank[t] = t < h->T ? h->rank[t] : 0;
         fp.yoff[t] = t < h->T ? h->yoff[t] : 0;
     }
-    k_finalize<<<1, 64, 0, st>>>(partials, eta_partials, h->yhat, h->tau, fp, th, out, tau, g_eta, g_W, g_v, g_s2,
+    k_finalize<<<1, 256, 0, st>>>(partials, eta_partials, h->yhat, h->tau, fp, th, out, tau, g_eta, g_W, g_v, g_s2,
                                  h->dsi_mix ? h->bmix + 4 : nullptr);
 }

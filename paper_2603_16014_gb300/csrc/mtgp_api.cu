@@ -558,20 +558,45 @@ int mtgp_nll_grad(mtgp_t* hs, const double* eta, const double* W, int s, const d
     return run_nll(h, th, true, out, tau, g_eta, g_W, g_v, g_sigma2, st);
 }
 
-// copy in, evaluate, copy out on stream st (the direct launches of the host-buffer entry point)
-static int enqueue_nll_grad_host(Handle* h, const double* theta, int s, double* out, cudaStream_t st) {
+// theta from page-locked host memory into the handle's staging buffer (one small block; the fused
+// kernels wait for it through their programmatic-launch wait)
+__global__ void k_stage_in(const double* __restrict__ src, double* __restrict__ dst, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// device address of page-locked host memory, or nullptr if it has none (pageable memory)
+static void* mapped_ptr(const void* host) {
+    void* dp = nullptr;
+    if (cudaHostGetDevicePointer(&dp, const_cast<void*>(host), 0) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return dp;
+}
+
+// copy in, evaluate, copy out on stream st (the launches of the host-buffer entry point).  With
+// page-locked buffers the kernels read theta through k_stage_in and write the results straight into
+// the host buffer (no DMA copies); pageable buffers go through cudaMemcpyAsync.
+static int enqueue_nll_grad_host(Handle* h, const double* theta, int s, double* out, const double* th_map,
+                                 double* out_map, cudaStream_t st) {
     const int d = h->d, T = h->T, nsig = h->noise_pt ? T : 1;
     const size_t nth = (size_t)d + (size_t)T * s + T + nsig;
     const size_t nout = 3 + (size_t)T + nth;
     double* dth = h->hio;
-    double* dout = h->hio + nth;
-    CK(cudaMemcpyAsync(dth, theta, nth * sizeof(double), cudaMemcpyHostToDevice, st));
+    const bool zero_copy = th_map && out_map;
+    double* dout = zero_copy ? out_map : h->hio + nth;
+    if (zero_copy) {
+        k_stage_in<<<1, 64, 0, st>>>(th_map, dth, (int)nth);
+        CK(cudaGetLastError());
+    } else {
+        CK(cudaMemcpyAsync(dth, theta, nth * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
     ThetaPtrs th{dth, dth + d, s, dth + d + (size_t)T * s, dth + d + (size_t)T * s + T, nsig,
                  h->dsi_mix ? h->bmix : nullptr};
     double* g = dout + 3 + T;
     int rc = run_nll(h, th, true, dout, dout + 3, g, g + d, g + d + (size_t)T * s, g + d + (size_t)T * s + T, st);
     if (rc) return rc;
-    CK(cudaMemcpyAsync(out, dout, nout * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (!zero_copy) CK(cudaMemcpyAsync(out, dout, nout * sizeof(double), cudaMemcpyDeviceToHost, st));
     return MTGP_OK;
 }
 
@@ -581,14 +606,15 @@ static void drop_hio_graph(Handle* h) {
 }
 
 // capture the copy-in / kernels / copy-out sequence into h->hio_exec; false if the capture fails
-static bool capture_hio_graph(Handle* h, const double* theta, int s, double* out) {
+static bool capture_hio_graph(Handle* h, const double* theta, int s, double* out, const double* th_map,
+                              double* out_map) {
     drop_hio_graph(h);
     if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         h->cap_stream = nullptr;
         return false;
     }
     if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
-    const int rc = enqueue_nll_grad_host(h, theta, s, out, h->cap_stream);
+    const int rc = enqueue_nll_grad_host(h, theta, s, out, th_map, out_map, h->cap_stream);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
     bool ok = rc == MTGP_OK && ec == cudaSuccess && graph != nullptr;
@@ -601,41 +627,31 @@ static bool capture_hio_graph(Handle* h, const double* theta, int s, double* out
     return ok;
 }
 
-// page-locked (or registered) host memory: the only kind a captured copy may use
-static bool host_pinned(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeHost;
-}
-
 int mtgp_nll_grad_host(mtgp_t* hs, const double* theta, int s, double* out, cudaStream_t st) {
     if (!hs || !theta || !out) return fail(MTGP_ERR_INVALID_ARG, "NULL argument");
     Handle* h = &hs->h;
     if (s < 1 || s > h->T) return fail(MTGP_ERR_INVALID_ARG, "s must satisfy 1 <= s <= T");
     if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
+    // looked up on every call: a buffer that is no longer page-locked must not reach a kernel
+    const double* th_map = static_cast<const double*>(mapped_ptr(theta));
+    double* out_map = static_cast<double*>(mapped_ptr(out));
     const bool profiling = h->prof && h->prof->on;
-    if (!profiling && !h->hio_nograph) {
-        const bool same = h->hio_key_valid && h->hio_key_th == theta && h->hio_key_out == out &&
+    if (th_map && out_map && !profiling && !h->hio_nograph) {
+        const bool same = h->hio_exec && h->hio_key_th == th_map && h->hio_key_out == out_map &&
                           h->hio_key_s == s && h->hio_key_gen == h->cfg_gen;
         if (!same) {
-            drop_hio_graph(h);
-            h->hio_key_valid = true;
-            h->hio_key_th = theta;
-            h->hio_key_out = out;
+            h->hio_key_th = th_map;
+            h->hio_key_out = out_map;
             h->hio_key_s = s;
             h->hio_key_gen = h->cfg_gen;
-            // pageable buffers take the direct launches; a failed capture disables graphs for the handle
-            if (host_pinned(theta) && host_pinned(out) && !capture_hio_graph(h, theta, s, out)) h->hio_nograph = true;
+            if (!capture_hio_graph(h, theta, s, out, th_map, out_map)) h->hio_nograph = true;  // direct from now on
         }
         if (h->hio_exec) {
             CK(cudaGraphLaunch(h->hio_exec, st));
             return MTGP_OK;
         }
     }
-    return enqueue_nll_grad_host(h, theta, s, out, st);
+    return enqueue_nll_grad_host(h, theta, s, out, th_map, out_map, st);
 }
 
 // GCV loss at the GCV mean: generic path (column generation, transforms, per-frequency or tree

@@ -364,8 +364,8 @@ struct Handle {
     bool dsi_mix;        // digital nets: DSI mixture weights b set (general path only)
     double* bmix;        // device: b (4 doubles) then dL/db of the last gradient call (4 doubles)
     double* hio;         // device staging of the host-buffer entry point: packed theta, then outputs
-    // the host-buffer entry point replays one CUDA graph (copy in, kernels, copy out) per
-    // (theta, out, s, configuration); any call that changes which kernels run bumps cfg_gen
+    // the host-buffer entry point replays one CUDA graph (staging, kernels) per (device addresses of
+    // the page-locked theta and out, s, configuration); a call that changes which kernels run bumps cfg_gen
     unsigned cfg_gen;
     cudaStream_t cap_stream;
     cudaGraphExec_t hio_exec;
@@ -373,7 +373,6 @@ struct Handle {
     void* hio_key_out;
     int hio_key_s;
     unsigned hio_key_gen;
-    bool hio_key_valid;
     bool hio_nograph;    // capture failed once: the direct launches are used from then on
 };
 
