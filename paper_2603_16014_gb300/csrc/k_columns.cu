@@ -12,9 +12,19 @@ constexpr int kThreads = 256;
 
 struct ColParams {
     ColDesc cols[MTGP_MAX_COLS];
+    long long tile0[MTGP_MAX_COLS + 1];  // first 256-element tile of each column (prefix sums)
     int alpha;           // SI smoothness
     const double* bmix;  // DSI mixture weights (4), or nullptr
 };
+
+// Points of a tile of 256 consecutive indices t0 + lo (t0 a multiple of 256): the index bits of t0
+// and lo are disjoint, and both constructions are linear in them (lattice: bitrev(t0 | lo) g =
+// bitrev(t0) g + bitrev(lo) g mod 2^32; digital net: XOR of the generator columns of the set bits),
+// so z(t0 + lo) = z(t0) (+) z(lo).  Each thread keeps z(lo) of its own lo in shared memory; z(t0) is
+// formed once per tile by d threads.
+__device__ __forceinline__ uint32_t combine_word(int kind, uint32_t zhi, uint32_t zlo) {
+    return kind == MTGP_LATTICE ? zhi + zlo : (zhi ^ zlo);
+}
 
 template <typename S, bool CPLX>
 __global__ void __launch_bounds__(kThreads)
@@ -22,28 +32,35 @@ k_colgen(void* out, ColParams cp, int kind, int d, const uint32_t* __restrict__ 
          const uint32_t* __restrict__ shift, const double* __restrict__ eta) {
     __shared__ S s_eta[MTGP_MAX_DIM];
     __shared__ S s_b[4];
-    __shared__ uint32_t s_dt[MTGP_MAX_DIM], s_du[MTGP_MAX_DIM];
+    __shared__ uint32_t s_dt[MTGP_MAX_DIM], s_du[MTGP_MAX_DIM], s_zhi[MTGP_MAX_DIM];
+    __shared__ uint32_t s_zlo[MTGP_MAX_DIM * kThreads];
     const ColDesc c = cp.cols[blockIdx.y];
-    if (threadIdx.x < d) {
-        s_eta[threadIdx.x] = (S)eta[threadIdx.x];
-        s_dt[threadIdx.x] = shift[c.t * d + threadIdx.x];
-        s_du[threadIdx.x] = shift[c.u * d + threadIdx.x];
+    const int tid = threadIdx.x;
+    if (tid < d) {
+        s_eta[tid] = (S)eta[tid];
+        s_dt[tid] = shift[c.t * d + tid];
+        s_du[tid] = shift[c.u * d + tid];
     }
-    if (cp.bmix && threadIdx.x < 4) s_b[threadIdx.x] = (S)cp.bmix[threadIdx.x];
+    if (cp.bmix && tid < 4) s_b[tid] = (S)cp.bmix[tid];
     const S* bw = cp.bmix ? s_b : nullptr;
-    __syncthreads();
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < c.n;
-         i += (long long)gridDim.x * blockDim.x) {
-        S q = (S)1;
-        for (int j = 0; j < d; ++j) {
-            uint32_t z = point_word(kind, (uint32_t)i, j, gen, gen_cols);
-            uint32_t X = pair_word(kind, z, s_dt[j], s_du[j]);
-            q *= (S)1 + s_eta[j] * kernel1d_b<S>(kind, X, cp.alpha, bw);
-        }
-        if (CPLX) {
-            reinterpret_cast<cx<S>*>(out)[c.off + i] = mk(q, (S)0);
-        } else {
-            reinterpret_cast<S*>(out)[c.off + i] = q;
+    for (int j = 0; j < d; ++j) s_zlo[j * kThreads + tid] = point_word(kind, (uint32_t)tid, j, gen, gen_cols);
+    for (long long t0 = (long long)blockIdx.x * kThreads; t0 < c.n; t0 += (long long)gridDim.x * kThreads) {
+        __syncthreads();  // the previous tile's reads of s_zhi are done
+        if (tid < d) s_zhi[tid] = point_word(kind, (uint32_t)t0, tid, gen, gen_cols);
+        __syncthreads();
+        const long long i = t0 + tid;
+        if (i < c.n) {
+            S q = (S)1;
+            for (int j = 0; j < d; ++j) {
+                const uint32_t z = combine_word(kind, s_zhi[j], s_zlo[j * kThreads + tid]);
+                const uint32_t X = pair_word(kind, z, s_dt[j], s_du[j]);
+                q *= (S)1 + s_eta[j] * kernel1d_b<S>(kind, X, cp.alpha, bw);
+            }
+            if (CPLX) {
+                reinterpret_cast<cx<S>*>(out)[c.off + i] = mk(q, (S)0);
+            } else {
+                reinterpret_cast<S*>(out)[c.off + i] = q;
+            }
         }
     }
 }
@@ -92,19 +109,34 @@ k_eta_grad(const void* omega, ColParams cp, int ncols, int kind, int d, const ui
     __shared__ S s_eta[MTGP_MAX_DIM];
     __shared__ S s_b[4];
     __shared__ double s_red[kThreads / 32][MTGP_MAX_DIM + 4];
-    if (threadIdx.x < d) s_eta[threadIdx.x] = (S)eta[threadIdx.x];
-    if (MIX && threadIdx.x < 4) s_b[threadIdx.x] = (S)cp.bmix[threadIdx.x];
-    __syncthreads();
+    __shared__ uint32_t s_dt[MTGP_MAX_DIM], s_du[MTGP_MAX_DIM], s_zhi[MTGP_MAX_DIM];
+    __shared__ uint32_t s_zlo[MTGP_MAX_DIM * kThreads];
+    const int tid = threadIdx.x;
+    if (tid < d) s_eta[tid] = (S)eta[tid];
+    if (MIX && tid < 4) s_b[tid] = (S)cp.bmix[tid];
+    for (int j = 0; j < d; ++j) s_zlo[j * kThreads + tid] = point_word(kind, (uint32_t)tid, j, gen, gen_cols);
     const S* bw = MIX ? s_b : nullptr;
-    double acc[MTGP_MAX_DIM + NB];
-    for (int j = 0; j < d + NB; ++j) acc[j] = 0.0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        // locate the column
+    // per-thread sums in the transform precision (FP32 additions keep the FP64 pipe free; a thread
+    // adds a few hundred terms), FP64 from the warp sums on
+    S acc[MTGP_MAX_DIM + NB];
+    for (int j = 0; j < d + NB; ++j) acc[j] = (S)0;
+    // 256-element tiles of the columns, tile g of all columns (column c owns tiles tile0[c] ..)
+    const long long ntiles = cp.tile0[ncols];
+    for (long long g = blockIdx.x; g < ntiles; g += gridDim.x) {
         int c = 0;
-        while (c + 1 < ncols && e >= cp.cols[c + 1].off) ++c;
+        while (c + 1 < ncols && g >= cp.tile0[c + 1]) ++c;
         const ColDesc cd = cp.cols[c];
-        long long i = e - cd.off;
+        const long long t0 = (g - cp.tile0[c]) * kThreads;
+        __syncthreads();  // the previous tile's reads of the shared words are done
+        if (tid < d) {
+            s_zhi[tid] = point_word(kind, (uint32_t)t0, tid, gen, gen_cols);
+            s_dt[tid] = shift[cd.t * d + tid];
+            s_du[tid] = shift[cd.u * d + tid];
+        }
+        __syncthreads();
+        const long long i = t0 + tid;
+        if (i >= cd.n) continue;
+        const long long e = cd.off + i;
         S w;
         if (CPLX) w = reinterpret_cast<const cx<S>*>(omega)[e].re;
         else w = reinterpret_cast<const S*>(omega)[e];
@@ -113,8 +145,8 @@ k_eta_grad(const void* omega, ColParams cp, int ncols, int kind, int d, const ui
         uint32_t xw[MIX ? MTGP_MAX_DIM : 1];
         S p = (S)1;
         for (int j = 0; j < d; ++j) {
-            uint32_t z = point_word(kind, (uint32_t)i, j, gen, gen_cols);
-            uint32_t X = pair_word(kind, z, shift[cd.t * d + j], shift[cd.u * d + j]);
+            const uint32_t z = combine_word(kind, s_zhi[j], s_zlo[j * kThreads + tid]);
+            const uint32_t X = pair_word(kind, z, s_dt[j], s_du[j]);
             if (MIX) xw[j] = X;
             kv[j] = kernel1d_b<S>(kind, X, cp.alpha, bw);
             pre[j] = p;
@@ -122,19 +154,19 @@ k_eta_grad(const void* omega, ColParams cp, int ncols, int kind, int d, const ui
         }
         S suf = (S)1;
         for (int j = d - 1; j >= 0; --j) {
-            acc[j] += (double)(w * kv[j] * pre[j] * suf);
+            acc[j] += w * kv[j] * pre[j] * suf;
             if (MIX) {
                 S ko[4];
                 dsi_orders<S>(xw[j], ko);
                 const S f = w * s_eta[j] * (pre[j] * suf);
-                for (int a = 0; a < 4; ++a) acc[d + a] += (double)(f * ko[a]);
+                for (int a = 0; a < 4; ++a) acc[d + a] += f * ko[a];
             }
             suf *= (S)1 + s_eta[j] * kv[j];
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int j = 0; j < d + NB; ++j) {
-        double v = acc[j];
+        double v = (double)acc[j];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) s_red[warp][j] = v;
     }
@@ -151,6 +183,8 @@ ColParams make_params(const Handle* h) {
     for (int c = 0; c < h->ncols; ++c) cp.cols[c] = h->cols[c];
     cp.alpha = h->smooth;
     cp.bmix = h->dsi_mix ? h->bmix : nullptr;
+    cp.tile0[0] = 0;
+    for (int c = 0; c < h->ncols; ++c) cp.tile0[c + 1] = cp.tile0[c] + (h->cols[c].n + kThreads - 1) / kThreads;
     return cp;
 }
 
