@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the torch-composition comparison arm")
+    ap.add_argument("--ncu-no-tune", action="store_true", help="--ncu with batch512: default transform splits")
     ap.add_argument("--ncu", action="store_true",
                     help="only warm-up + K steps of the workload, no extras (for ncu captures)")
     ap.add_argument("--workload", default="nllgrad", choices=["nllgrad", "batch512", "proposal", "nested", "posterior", "sweep", "gcv"],
@@ -354,11 +355,51 @@ def run_ours(args, rank, world, local_rank):
 
 
 def run_ncu_case(args):
-    """W warm-up then K steps, nothing else: 3 kernels per step (fused A, B, C)."""
+    """W warm-up then K steps of the workload, nothing else (for ncu captures): nllgrad 3 kernels
+    per step (fused A, B, C); nested the general path (columns, transforms, tree solve, adjoint,
+    finalize); posterior one mean call over --queries queries; batch512 one batched NLL + gradient
+    of every fit (transform splits autotuned first)."""
+    import numpy as np
     import torch
 
-    p, model, y = make_workload()
+    from paper_2603_16014_gb300 import inputs
+    from paper_2603_16014_gb300.mtgp import MTGP, Batch
+
+    if args.workload == "batch512":
+        probs = batch_problems(args.fits)
+        ys = []
+        for p in probs:
+            m = MTGP.from_problem(p, "fp32")
+            X = m.points().cpu().numpy().view(np.uint32)
+            ys.append(inputs.synth_y(p, [X[i * p.n[0]:(i + 1) * p.n[0]] for i in range(p.T)]))
+            m.close()
+        b = Batch(probs, s=2, precision="fp32")
+        b.set_y(torch.from_numpy(np.concatenate(ys)))
+        b.set_theta(torch.from_numpy(b.pack([default_theta(p) for p in probs])))
+        if not args.ncu_no_tune:
+            b.autotune(reps=2)
+        for _ in range(args.warmup + args.steps):
+            nll, _ = b.nll_grad()
+        torch.cuda.synchronize()
+        print(json.dumps({"fits": len(probs), "nll0": nll[0].item(), "steps": args.steps, "warmup": args.warmup}))
+        return
+    if args.workload == "nested":
+        p = inputs.lattice_nested()
+        model = MTGP.from_problem(p, "fp64")
+        X = model.points().cpu().numpy().view(np.uint32)
+        offs = np.concatenate([[0], np.cumsum(p.n)])
+        model.set_y(torch.from_numpy(inputs.synth_y(p, [X[offs[t]:offs[t + 1]] for t in range(p.T)])))
+    else:
+        p, model, y = make_workload()
     th = [torch.as_tensor(a, dtype=torch.float64).cuda().contiguous() for a in (p.eta, p.W, p.v, [p.sigma2])]
+    if args.workload == "posterior":
+        _, xq, task = inputs.query_points(args.queries, p.d, seed=3, tasks=p.T)
+        xq_d, task_d = torch.from_numpy(xq).cuda(), torch.from_numpy(task).cuda()
+        for _ in range(args.warmup + args.steps):
+            mean, _ = model.posterior(*th, xq_d, task_d, variance=False)
+        model.sync()
+        print(json.dumps({"mean0": mean[0].item(), "queries": args.queries, "steps": args.steps}))
+        return
     outs = model.nll_grad(*th)
     for _ in range(args.warmup + args.steps):
         model.nll_grad(*th, outs=outs)
