@@ -142,6 +142,7 @@ k_eta_grad(const void* omega, ColParams cp, int ncols, int kind, int d, const ui
         else w = reinterpret_cast<const S*>(omega)[e];
         S kv[MTGP_MAX_DIM];
         S pre[MTGP_MAX_DIM];
+        S fac[MTGP_MAX_DIM];
         uint32_t xw[MIX ? MTGP_MAX_DIM : 1];
         S p = (S)1;
         for (int j = 0; j < d; ++j) {
@@ -149,19 +150,22 @@ k_eta_grad(const void* omega, ColParams cp, int ncols, int kind, int d, const ui
             const uint32_t X = pair_word(kind, z, s_dt[j], s_du[j]);
             if (MIX) xw[j] = X;
             kv[j] = kernel1d_b<S>(kind, X, cp.alpha, bw);
+            fac[j] = fma(s_eta[j], kv[j], (S)1);
             pre[j] = p;
-            p *= (S)1 + s_eta[j] * kv[j];
+            p *= fac[j];
         }
-        S suf = (S)1;
+        // the adjoint weight rides in the suffix product: suf = w prod_{l > j} (1 + eta_l K_l)
+        S suf = w;
         for (int j = d - 1; j >= 0; --j) {
-            acc[j] += w * kv[j] * pre[j] * suf;
+            const S ps = pre[j] * suf;
+            acc[j] = fma(kv[j], ps, acc[j]);
             if (MIX) {
                 S ko[4];
                 dsi_orders<S>(xw[j], ko);
-                const S f = w * s_eta[j] * (pre[j] * suf);
-                for (int a = 0; a < 4; ++a) acc[d + a] += f * ko[a];
+                const S f = s_eta[j] * ps;
+                for (int a = 0; a < 4; ++a) acc[d + a] = fma(f, ko[a], acc[d + a]);
             }
-            suf *= (S)1 + s_eta[j] * kv[j];
+            suf *= fac[j];
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
