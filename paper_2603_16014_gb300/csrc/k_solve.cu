@@ -420,15 +420,21 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
     // diagonal slot is replaced by 1 / D once its log is taken; for each target node (a, g) the
     // factors L = conj(S_{ta}) / D of the rr nodes above it are formed once and applied to every
     // a2 >= a.
+    // pivots multiplied into a mantissa / exponent accumulator: one log per thread at the end
+    LogAcc lacc;
+    lacc.init();
     for (int t = 0; t < T; ++t) {
         const long long mt = p.n[t] / nT;
         if (act) {
             for (long long k = slot; k < mt; k += kTreeSlots) {
                 long long f = rho + k * nT;
                 double D = creal(ld<CPLX>(Sb, p.po[t][t] + f));
-                if (!(D > 0.0) || !isfinite(D)) bad = 1;
-                else acc[0] += log(D);
-                st<CPLX>(Sb, p.po[t][t] + f, cfromreal<V>(1.0 / D));
+                if (!pos_finite(D)) {
+                    bad = 1;
+                    D = 1.0;
+                }
+                lacc.mul(D);
+                st<CPLX>(Sb, p.po[t][t] + f, cfromreal<V>(fast_rcp(D)));
             }
         }
         __syncthreads();
@@ -644,6 +650,7 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
         }
     }
     if (bad) set_status(status, ST_NOT_PD);
+    acc[0] = lacc.log_value();
     for (int q = 0; q < NQ; ++q) {
         double v = acc[q];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
