@@ -319,7 +319,7 @@ __device__ void tree_forward(const TreeParams& p, const double* Sb, double* rb, 
 // Z is stored like S: Z_{ta'}[f] = Z[(t, f), (a', f mod n_a')].  The diagonal slot of S holds 1 / D.
 template <bool CPLX>
 __device__ void tree_backward(const TreeParams& p, const double* Sb, double* Zb, const double* rb, double* ab,
-                              long long rho, bool act, int slot, bool wantZ) {
+                              long long rho, bool act, int slot, bool wantZ, bool mir = false) {
     using V = Vt<CPLX>;
     const long long nT = p.nT;
     for (int t = p.T - 1; t >= 0; --t) {
@@ -337,6 +337,8 @@ __device__ void tree_backward(const TreeParams& p, const double* Sb, double* Zb,
                 for (int a2 = 0; a2 < MTGP_TMAX; ++a2)
                     if (a2 > t && a2 < p.T) a = vsub(a, vmul(l[a2], ld<CPLX>(ab, p.yoff[a2] + (f & (p.n[a2] - 1)))));
                 st<CPLX>(ab, p.yoff[t] + f, a);
+                // the conjugate class holds the conjugate solution at the mirrored frequencies
+                if (mir) st<CPLX>(ab, p.yoff[t] + ((p.n[t] - f) & (p.n[t] - 1)), cconj(a));
                 if (wantZ) {
                     double zd = invD;
 #pragma unroll
@@ -387,7 +389,12 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
     const long long nT = p.nT;
     const int cls = lane % kTreeCW;
     const long long rho = (long long)blockIdx.x * kTreeCW + cls;
-    const bool act = rho < nT;
+    // lattices (complex spectra of real data): class nT - rho is the conjugate of class rho, so only
+    // rho = 0 .. nT/2 are solved; a class with a distinct conjugate counts twice and writes the
+    // conjugate solution and weights at the mirrored frequencies
+    const long long ncls = (CPLX && nT >= 2) ? nT / 2 + 1 : nT;
+    const bool act = rho < ncls;
+    const bool mir = CPLX && act && rho != 0 && 2 * rho != nT;
     __shared__ V s_part[kTreeCW][kTreeSlots][MTGP_TMAX];  // partial sums of split reductions
     double acc[3 + MTGP_MAX_COLS + MTGP_TMAX];
     for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
@@ -603,7 +610,7 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
     }
     __syncthreads();
     tree_forward<CPLX>(p, Sb, rb, rho, act, slot, acc[1], s_part);
-    tree_backward<CPLX>(p, Sb, Zb, rb, ab, rho, act, slot, p.grad != 0 || p.gcv != 0);
+    tree_backward<CPLX>(p, Sb, Zb, rb, ab, rho, act, slot, p.grad != 0 || p.gcv != 0, mir);
 
     if (p.gcv && act) {
         // ||Lambda~^-1 rhat||^2 and trace Lambda~^-1 over this class's nodes
@@ -640,10 +647,14 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
                         acc[2] += gd;
                         if (p.pt) acc[3 + NG + t] += gd;
                         acc[q] += gd * m0;
-                        store_spec<S, CPLX>(wgt, p.po[t][u] + f, cfromreal<V>(sR[t * T + t] * gd * ind));
+                        const V wv = cfromreal<V>(sR[t * T + t] * gd * ind);
+                        store_spec<S, CPLX>(wgt, p.po[t][u] + f, wv);
+                        if (mir) store_spec<S, CPLX>(wgt, p.po[t][u] + ((p.n[t] - f) & (p.n[t] - 1)), wv);
                     } else {
                         acc[q] += sc * creal(vmul(g, mu));
-                        store_spec<S, CPLX>(wgt, p.po[t][u] + f, vscale(g, 2.0 * sR[t * T + u] * sc));
+                        const V wv = vscale(g, 2.0 * sR[t * T + u] * sc);
+                        store_spec<S, CPLX>(wgt, p.po[t][u] + f, wv);
+                        if (mir) store_spec<S, CPLX>(wgt, p.po[t][u] + ((p.n[t] - f) & (p.n[t] - 1)), cconj(wv));
                     }
                 }
             }
@@ -651,6 +662,8 @@ k_solve_tree(const void* spec, void* wgt, const double* yhat, double* Sb, double
     }
     if (bad) set_status(status, ST_NOT_PD);
     acc[0] = lacc.log_value();
+    if (mir)
+        for (int q = 0; q < NQ; ++q) acc[q] *= 2.0;
     for (int q = 0; q < NQ; ++q) {
         double v = acc[q];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -766,7 +779,11 @@ int eq_blocks(const Handle* h) {
 }  // namespace
 
 int solve_equal_blocks(const Handle* h) { return eq_blocks(h); }
-int solve_tree_blocks(const Handle* h) { return (int)((h->n[h->T - 1] + kTreeCW - 1) / kTreeCW); }
+int solve_tree_blocks(const Handle* h) {
+    const long long nT = h->n[h->T - 1];
+    const long long ncls = (h->cplx && nT >= 2) ? nT / 2 + 1 : nT;  // conjugate classes (lattices)
+    return (int)((ncls + kTreeCW - 1) / kTreeCW);
+}
 
 template <int T, bool CPLX, typename S>
 static void run_eq(const Handle* h, ThetaPtrs th, SolveParams sp, double* partials, cudaStream_t st) {
