@@ -57,7 +57,11 @@ k_colgen(void* out, ColParams cp, int kind, int d, const uint32_t* __restrict__ 
                 q *= (S)1 + s_eta[j] * kernel1d_b<S>(kind, X, cp.alpha, bw);
             }
             if (CPLX) {
-                reinterpret_cast<cx<S>*>(out)[c.off + i] = mk(q, (S)0);
+                // a pair's lead writes the real part, its partner the imaginary part of the lead's element
+                S* o = reinterpret_cast<S*>(out);
+                if (c.role == 0) reinterpret_cast<cx<S>*>(out)[c.off + i] = mk(q, (S)0);
+                else if (c.role == 1) o[2 * (c.off + i)] = q;
+                else o[2 * (c.src + i) + 1] = q;
             } else {
                 reinterpret_cast<S*>(out)[c.off + i] = q;
             }
@@ -136,10 +140,14 @@ k_eta_grad(const void* omega, ColParams cp, int ncols, int kind, int d, const ui
         __syncthreads();
         const long long i = t0 + tid;
         if (i >= cd.n) continue;
-        const long long e = cd.off + i;
         S w;
-        if (CPLX) w = reinterpret_cast<const cx<S>*>(omega)[e].re;
-        else w = reinterpret_cast<const S*>(omega)[e];
+        if (CPLX) {
+            // a partner's transformed weights are the imaginary part of its lead's array
+            const cx<S> o = reinterpret_cast<const cx<S>*>(omega)[(cd.role == 2 ? cd.src : cd.off) + i];
+            w = cd.role == 2 ? o.im : o.re;
+        } else {
+            w = reinterpret_cast<const S*>(omega)[cd.off + i];
+        }
         S kv[MTGP_MAX_DIM];
         S pre[MTGP_MAX_DIM];
         S fac[MTGP_MAX_DIM];
@@ -179,6 +187,41 @@ k_eta_grad(const void* omega, ColParams cp, int ncols, int kind, int d, const ui
         double v = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_red[w][threadIdx.x];
         partials[(long long)blockIdx.x * (d + NB) + threadIdx.x] = v;
+    }
+}
+
+// F(a), F(b) from Z = F(a + i b) for real a, b (Hermitian spectra): F(a)[f] = (Z[f] + conj Z[-f]) / 2,
+// F(b)[f] = -i (Z[f] - conj Z[-f]) / 2, -f = (n - f) mod n.  One thread takes f and -f together, so
+// the lead's array is overwritten in place.
+template <typename S>
+__global__ void k_pair_split(cx<S>* __restrict__ spec, const long long* __restrict__ pairs, int npairs) {
+    const int pr = blockIdx.y;
+    if (pr >= npairs) return;
+    const long long offa = pairs[3 * pr], offb = pairs[3 * pr + 1], n = pairs[3 * pr + 2];
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f <= n / 2;
+         f += (long long)gridDim.x * blockDim.x) {
+        const long long g = (n - f) & (n - 1);
+        const cx<S> zf = spec[offa + f], zg = spec[offa + g];
+        const S h = (S)0.5;
+        spec[offa + f] = mk(h * (zf.re + zg.re), h * (zf.im - zg.im));
+        spec[offb + f] = mk(h * (zf.im + zg.im), h * (zg.re - zf.re));
+        if (g != f) {
+            spec[offa + g] = mk(h * (zg.re + zf.re), h * (zg.im - zf.im));
+            spec[offb + g] = mk(h * (zg.im + zf.im), h * (zf.re - zg.re));
+        }
+    }
+}
+
+// the lead's weights become w_a + i w_b (the adjoint transform is linear; both transformed weight
+// arrays are real up to rounding, the eta adjoint reads the real part for a and the imaginary for b)
+template <typename S>
+__global__ void k_pair_pack(cx<S>* __restrict__ wgt, const long long* __restrict__ pairs, int npairs) {
+    const int pr = blockIdx.y;
+    if (pr >= npairs) return;
+    const long long offa = pairs[3 * pr], offb = pairs[3 * pr + 1], n = pairs[3 * pr + 2];
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < n; f += (long long)gridDim.x * blockDim.x) {
+        const cx<S> wa = wgt[offa + f], wb = wgt[offb + f];
+        wgt[offa + f] = mk(wa.re - wb.im, wa.im + wb.re);
     }
 }
 
@@ -272,4 +315,24 @@ void launch_eta_grad(const Handle* h, const double* eta, const void* omega, doub
         else MTGP_ETA_GRAD(double, false, false);
     }
 #undef MTGP_ETA_GRAD
+}
+
+static dim3 pair_grid(const Handle* h) {
+    long long maxn = 0;
+    for (int c = 0; c < h->ncols; ++c) maxn = maxn > h->cols[c].n ? maxn : h->cols[c].n;
+    long long bx = (maxn + kThreads - 1) / kThreads;
+    if (bx > 2048) bx = 2048;
+    return dim3((unsigned)bx, (unsigned)h->npairs);
+}
+
+void launch_pair_split(const Handle* h, void* spec, cudaStream_t st) {
+    if (h->npairs == 0) return;
+    if (h->fp32) k_pair_split<float><<<pair_grid(h), kThreads, 0, st>>>(reinterpret_cast<cx<float>*>(spec), h->pairs_dev, h->npairs);
+    else k_pair_split<double><<<pair_grid(h), kThreads, 0, st>>>(reinterpret_cast<cx<double>*>(spec), h->pairs_dev, h->npairs);
+}
+
+void launch_pair_pack(const Handle* h, void* wgt, cudaStream_t st) {
+    if (h->npairs == 0) return;
+    if (h->fp32) k_pair_pack<float><<<pair_grid(h), kThreads, 0, st>>>(reinterpret_cast<cx<float>*>(wgt), h->pairs_dev, h->npairs);
+    else k_pair_pack<double><<<pair_grid(h), kThreads, 0, st>>>(reinterpret_cast<cx<double>*>(wgt), h->pairs_dev, h->npairs);
 }

@@ -196,7 +196,7 @@ cudaError_t dalloc(Handle* h, T** p, size_t count) {
 void free_all(Handle* h) {
     void* ptrs[] = {h->gen, h->shift, h->cols_dev, h->offs_dev, h->yoffs_dev, h->twid, h->twid32, h->yhat, h->spec,
                     h->wgt, h->S, h->Z, h->r, h->alpha, h->tau, h->partials, h->status, h->out_tmp, h->counters,
-                    h->gcv_h, h->pi_buf, h->bmix, h->hio};
+                    h->gcv_h, h->pi_buf, h->bmix, h->hio, h->lead_offs_dev, h->pairs_dev};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->hio_exec) cudaGraphExecDestroy(h->hio_exec);
@@ -220,6 +220,30 @@ int validate_theta(const Handle* h, const double* eta, const double* W, int s, c
     return MTGP_OK;
 }
 
+// First-column spectra of the general path: columns, forward transforms (paired columns of a
+// lattice share one complex transform), split of the pairs.
+static void forward_columns(Handle* h, const double* eta, cudaStream_t st) {
+    mtgp_prof_begin(h, "colgen", st);
+    launch_colgen(h, eta, h->spec, st);
+    mtgp_prof_end(h, st);
+    mtgp_prof_begin(h, "xform_dit", st);
+    for (int g = 0; g < h->ngroups; ++g)
+        launch_transform(h, h->spec, h->fp32, h->cplx, h->group_m[g], h->lead_offs_dev + h->group_lfirst[g],
+                         h->group_lcount[g], false, st);
+    launch_pair_split(h, h->spec, st);
+    mtgp_prof_end(h, st);
+}
+
+// Adjoint transforms of the gradient weights (paired columns packed as w_a + i w_b first).
+static void adjoint_columns(Handle* h, cudaStream_t st) {
+    mtgp_prof_begin(h, "xform_dif", st);
+    launch_pair_pack(h, h->wgt, st);
+    for (int g = 0; g < h->ngroups; ++g)
+        launch_transform(h, h->wgt, h->fp32, h->cplx, h->group_m[g], h->lead_offs_dev + h->group_lfirst[g],
+                         h->group_lcount[g], true, st);
+    mtgp_prof_end(h, st);
+}
+
 // NLL (and gradient) at theta; leaves alpha = Lambda^-1 rhat in h->alpha and tau in h->tau.
 int run_nll(Handle* h, ThetaPtrs th, bool grad, double* out, double* tau, double* g_eta, double* g_W, double* g_v,
             double* g_s2, cudaStream_t st, bool store_alpha = false) {
@@ -231,14 +255,7 @@ int run_nll(Handle* h, ThetaPtrs th, bool grad, double* out, double* tau, double
         return MTGP_OK;
     }
     k_check_theta<<<1, 64, 0, st>>>(th, h->d, h->T, h->status);
-    mtgp_prof_begin(h, "colgen", st);
-    launch_colgen(h, th.eta, h->spec, st);
-    mtgp_prof_end(h, st);
-    mtgp_prof_begin(h, "xform_dit", st);
-    for (int g = 0; g < h->ngroups; ++g)
-        launch_transform(h, h->spec, h->fp32, h->cplx, h->group_m[g], h->offs_dev + h->group_first[g],
-                         h->group_count[g], false, st);
-    mtgp_prof_end(h, st);
+    forward_columns(h, th.eta, st);
     int nsolve;
     if (h->equal) {
         mtgp_prof_begin(h, "solve_equal", st);
@@ -255,11 +272,7 @@ int run_nll(Handle* h, ThetaPtrs th, bool grad, double* out, double* tau, double
     double* eta_part = h->partials + (long long)nsolve * NQ;
     int neta = 0;
     if (grad) {
-        mtgp_prof_begin(h, "xform_dif", st);
-        for (int g = 0; g < h->ngroups; ++g)
-            launch_transform(h, h->wgt, h->fp32, h->cplx, h->group_m[g], h->offs_dev + h->group_first[g],
-                             h->group_count[g], true, st);
-        mtgp_prof_end(h, st);
+        adjoint_columns(h, st);
         neta = eta_grad_blocks(h);
         mtgp_prof_begin(h, "eta_grad", st);
         launch_eta_grad(h, th.eta, h->wgt, eta_part, neta, st);
@@ -373,6 +386,35 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
         h->group_m[g] = mm;
         i = j;
     }
+    // lattices: pair the columns of each group (two real columns per complex transform)
+    std::vector<long long> lead_offs, pair_tab;
+    h->npairs = 0;
+    for (int g = 0; g < h->ngroups; ++g) {
+        h->group_lfirst[g] = (int)lead_offs.size();
+        const int c0 = h->group_first[g], cnt = h->group_count[g];
+        for (int k = 0; k < cnt; ++k) {
+            ColDesc& cd = h->cols[c0 + k];
+            cd.src = cd.off;
+            cd.role = 0;
+        }
+        for (int k = 0; k < cnt; k += 2) {
+            ColDesc& a = h->cols[c0 + k];
+            lead_offs.push_back(a.off);
+            if (h->cplx && k + 1 < cnt) {
+                ColDesc& b = h->cols[c0 + k + 1];
+                a.role = 1;
+                b.role = 2;
+                b.src = a.off;
+                pair_tab.push_back(a.off);
+                pair_tab.push_back(b.off);
+                pair_tab.push_back(a.n);
+                ++h->npairs;
+            } else if (k + 1 < cnt) {
+                lead_offs.push_back(h->cols[c0 + k + 1].off);  // real data: every column alone
+            }
+        }
+        h->group_lcount[g] = (int)lead_offs.size() - h->group_lfirst[g];
+    }
     const size_t es = (h->fp32 ? 4 : 8) * (h->cplx ? 2 : 1);
     const size_t vs = h->cplx ? 2 : 1;  // doubles per FP64 value
     cudaError_t e;
@@ -387,6 +429,8 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
     AL(h->shift, (size_t)T * d);
     AL(h->cols_dev, (size_t)h->ncols);
     AL(h->offs_dev, (size_t)h->ncols);
+    AL(h->lead_offs_dev, lead_offs.size());
+    AL(h->pairs_dev, pair_tab.size());
     AL(h->yoffs_dev, (size_t)T);
     {
         size_t half = mmax >= 1 ? ((size_t)1 << (mmax - 1)) : 1;
@@ -439,6 +483,10 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
                cudaMemcpy(h->shift, shift_sorted.data(), shift_sorted.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) == cudaSuccess &&
                cudaMemcpy(h->cols_dev, h->cols, (size_t)h->ncols * sizeof(ColDesc), cudaMemcpyHostToDevice) == cudaSuccess &&
                cudaMemcpy(h->offs_dev, offs.data(), offs.size() * sizeof(long long), cudaMemcpyHostToDevice) == cudaSuccess &&
+               cudaMemcpy(h->lead_offs_dev, lead_offs.data(), lead_offs.size() * sizeof(long long),
+                          cudaMemcpyHostToDevice) == cudaSuccess &&
+               (pair_tab.empty() || cudaMemcpy(h->pairs_dev, pair_tab.data(), pair_tab.size() * sizeof(long long),
+                                               cudaMemcpyHostToDevice) == cudaSuccess) &&
                cudaMemcpy(h->yoffs_dev, yoffs.data(), yoffs.size() * sizeof(long long), cudaMemcpyHostToDevice) == cudaSuccess &&
                cudaMemset(h->status, 0, sizeof(int)) == cudaSuccess &&
                cudaMemset(h->counters, 0, 4 * sizeof(unsigned)) == cudaSuccess &&
@@ -665,14 +713,7 @@ static int run_gcv(Handle* h, ThetaPtrs th, double* out, double* tau, cudaStream
         h->ws_bytes += (long long)bytes;
     }
     k_check_theta<<<1, 64, 0, st>>>(th, h->d, h->T, h->status);
-    mtgp_prof_begin(h, "colgen", st);
-    launch_colgen(h, th.eta, h->spec, st);
-    mtgp_prof_end(h, st);
-    mtgp_prof_begin(h, "xform_dit", st);
-    for (int g = 0; g < h->ngroups; ++g)
-        launch_transform(h, h->spec, h->fp32, h->cplx, h->group_m[g], h->offs_dev + h->group_first[g],
-                         h->group_count[g], false, st);
-    mtgp_prof_end(h, st);
+    forward_columns(h, th.eta, st);
     int nsolve;
     if (h->equal) {
         mtgp_prof_begin(h, "solve_equal_gcv", st);
@@ -740,11 +781,7 @@ static int run_gcv_grad(Handle* h, ThetaPtrs th, double* out, double* tau, doubl
     const int nsolve = solve_equal_blocks(h);
     const int NQ = solve_nq(h);
     double* eta_part = h->partials + (long long)nsolve * NQ;
-    mtgp_prof_begin(h, "xform_dif", st);
-    for (int g = 0; g < h->ngroups; ++g)
-        launch_transform(h, h->wgt, h->fp32, h->cplx, h->group_m[g], h->offs_dev + h->group_first[g],
-                         h->group_count[g], true, st);
-    mtgp_prof_end(h, st);
+    adjoint_columns(h, st);
     const int neta = eta_grad_blocks(h);
     mtgp_prof_begin(h, "eta_grad", st);
     launch_eta_grad(h, th.eta, h->wgt, eta_part, neta, st);

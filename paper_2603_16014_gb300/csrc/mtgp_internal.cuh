@@ -225,6 +225,11 @@ struct ColDesc {
     long long off;  // element offset in the column buffers
     int n;          // length n_t
     int t, u;       // sorted task pair (t <= u)
+    // complex (lattice) columns are real, so two of equal length share one complex transform: the
+    // lead (role 1) in the real part, its partner (role 2) in the imaginary part of the lead's array
+    // (src); role 0 is a column transformed alone
+    long long src;
+    int role;
 };
 
 struct Handle;
@@ -250,6 +255,11 @@ __device__ __forceinline__ double noise_of(const ThetaPtrs& th, const int* order
 void launch_colgen(const Handle* h, const double* eta, void* out, cudaStream_t st);
 void launch_points(const Handle* h, uint32_t* x, cudaStream_t st);
 void launch_y_load(const Handle* h, const double* y, cudaStream_t st);
+// paired columns: after the forward transform, Z = F(a + i b) -> F(a) = (Z + conj(Z(-f))) / 2 and
+// F(b) = (Z - conj(Z(-f))) / (2i) into the lead's and the partner's arrays; before the adjoint
+// transform, the lead's weights w_a + i w_b
+void launch_pair_split(const Handle* h, void* spec, cudaStream_t st);
+void launch_pair_pack(const Handle* h, void* wgt, cudaStream_t st);
 void launch_eta_grad(const Handle* h, const double* eta, const void* omega, double* partials,
                      int nblk_max, cudaStream_t st);
 int eta_grad_blocks(const Handle* h);
@@ -337,6 +347,12 @@ struct Handle {
     int group_m[MTGP_TMAX];
     int group_first[MTGP_TMAX];
     int group_count[MTGP_TMAX];
+    // the arrays the general path transforms (leads and lone columns), per group, and the pairs
+    long long* lead_offs_dev;
+    int group_lfirst[MTGP_TMAX];
+    int group_lcount[MTGP_TMAX];
+    int npairs;
+    long long* pairs_dev;  // (lead offset, partner offset, length) per pair
     long long* yoffs_dev;  // per sorted task offset (for y transforms)
 
     void* twid;          // twiddle table e^{-2 pi i k / 2^mmax}, k < 2^{mmax-1}, double2 and float2
