@@ -108,7 +108,7 @@ template <typename S, bool CPLX, bool MIX>
 __global__ void __launch_bounds__(kThreads)
 k_eta_grad(const void* omega, ColParams cp, int ncols, int kind, int d, const uint32_t* __restrict__ gen,
            int gen_cols, const uint32_t* __restrict__ shift, const double* __restrict__ eta,
-           double* __restrict__ partials, long long total) {
+           double* __restrict__ partials) {
     constexpr int NB = MIX ? 4 : 0;
     __shared__ S s_eta[MTGP_MAX_DIM];
     __shared__ S s_b[4];
@@ -303,7 +303,7 @@ void launch_eta_grad(const Handle* h, const double* eta, const void* omega, doub
     ColParams cp = make_params(h);
 #define MTGP_ETA_GRAD(S, C, M) \
     k_eta_grad<S, C, M><<<nblk, kThreads, 0, st>>>(omega, cp, h->ncols, h->kind, h->d, h->gen, h->gen_cols, \
-                                                   h->shift, eta, partials, h->col_elems)
+                                                   h->shift, eta, partials)
     if (h->dsi_mix) {
         if (h->fp32) MTGP_ETA_GRAD(float, false, true);
         else MTGP_ETA_GRAD(double, false, true);

@@ -194,7 +194,7 @@ cudaError_t dalloc(Handle* h, T** p, size_t count) {
 }
 
 void free_all(Handle* h) {
-    void* ptrs[] = {h->gen, h->shift, h->cols_dev, h->offs_dev, h->yoffs_dev, h->twid, h->twid32, h->yhat, h->spec,
+    void* ptrs[] = {h->gen, h->shift, h->cols_dev, h->yoffs_dev, h->twid, h->twid32, h->yhat, h->spec,
                     h->wgt, h->S, h->Z, h->r, h->alpha, h->tau, h->partials, h->status, h->out_tmp, h->counters,
                     h->gcv_h, h->pi_buf, h->bmix, h->hio, h->lead_offs_dev, h->pairs_dev};
     for (void* p : ptrs)
@@ -428,7 +428,6 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
     AL(h->gen, (size_t)d * h->gen_cols);
     AL(h->shift, (size_t)T * d);
     AL(h->cols_dev, (size_t)h->ncols);
-    AL(h->offs_dev, (size_t)h->ncols);
     AL(h->lead_offs_dev, lead_offs.size());
     AL(h->pairs_dev, pair_tab.size());
     AL(h->yoffs_dev, (size_t)T);
@@ -476,13 +475,11 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
     std::vector<uint32_t> shift_sorted((size_t)T * d);
     for (int t = 0; t < T; ++t)
         for (int j = 0; j < d; ++j) shift_sorted[(size_t)t * d + j] = shift[(size_t)h->order[t] * d + j];
-    std::vector<long long> offs(h->ncols), yoffs(T);
-    for (int i = 0; i < h->ncols; ++i) offs[i] = h->cols[i].off;
+    std::vector<long long> yoffs(T);
     for (int t = 0; t < T; ++t) yoffs[t] = h->yoff[t];
     bool okc = cudaMemcpy(h->gen, gen, (size_t)d * h->gen_cols * sizeof(uint32_t), cudaMemcpyHostToDevice) == cudaSuccess &&
                cudaMemcpy(h->shift, shift_sorted.data(), shift_sorted.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) == cudaSuccess &&
                cudaMemcpy(h->cols_dev, h->cols, (size_t)h->ncols * sizeof(ColDesc), cudaMemcpyHostToDevice) == cudaSuccess &&
-               cudaMemcpy(h->offs_dev, offs.data(), offs.size() * sizeof(long long), cudaMemcpyHostToDevice) == cudaSuccess &&
                cudaMemcpy(h->lead_offs_dev, lead_offs.data(), lead_offs.size() * sizeof(long long),
                           cudaMemcpyHostToDevice) == cudaSuccess &&
                (pair_tab.empty() || cudaMemcpy(h->pairs_dev, pair_tab.data(), pair_tab.size() * sizeof(long long),

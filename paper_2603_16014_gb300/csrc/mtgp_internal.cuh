@@ -342,7 +342,6 @@ struct Handle {
     uint32_t* gen;       // lattice: d words; dnet: d * gen_cols
     uint32_t* shift;     // sorted T x d
     ColDesc* cols_dev;
-    long long* offs_dev;  // per column offset, grouped by length (see group_*)
     int ngroups;
     int group_m[MTGP_TMAX];
     int group_first[MTGP_TMAX];
