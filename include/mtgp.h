@@ -147,7 +147,8 @@ int mtgp_nll_grad_host(mtgp_t* h, const double* theta, int s, double* out, cudaS
  *          floor(x 2^32), 1.0 mapping to the largest word below 1 (Sec. 2.2.1 boundary rule).
  *   task   nq ints, caller task index of each query.
  *   mean   nq doubles (required); var nq doubles or NULL (NULL skips the variance).
- * Variance needs equal task sizes in this build (MTGP_ERR_UNSUPPORTED otherwise).
+ * Variance: equal sizes through per-frequency T x T factors; unequal nested sizes through the tree
+ * solver's factor, class by class (queries in batches of the rows that fit in 64 M doubles).
  */
 int mtgp_posterior(mtgp_t* h, const double* eta, const double* W, int s, const double* v,
                    const double* sigma2, int nq, const double* xq, const int* task,

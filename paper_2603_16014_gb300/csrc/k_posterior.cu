@@ -330,6 +330,61 @@ void run_var(bool factor, int B, const double* rows, const void* spec, double* f
     }
 }
 
+// rows of the variance batch, unequal sizes: rows[b * N + yoff[u] + i] = R_{t_b u} Q(x_b, x_{u,i}) / sqrt(n_u)
+// (the 1 / sqrt(n_u) of V^dagger folded in), tasks in the sorted observation layout
+template <bool CPLX>
+__global__ void k_var_rows_all(const uint32_t* __restrict__ xqw, const int* __restrict__ task, int q0, int B,
+                               const uint32_t* __restrict__ dw, PostParams p, ThetaPtrs th, long long N,
+                               double* __restrict__ rows) {
+    __shared__ double sR[MTGP_TMAX * MTGP_TMAX];
+    __shared__ double s_eta[MTGP_MAX_DIM];
+    __shared__ double s_bm[4];
+    load_R_post(sR, p, th);
+    if (threadIdx.x < p.d) s_eta[threadIdx.x] = th.eta[threadIdx.x];
+    const double* bm = load_bmix(s_bm, p);
+    __syncthreads();
+    if (threadIdx.x < p.T * p.T) sR[threadIdx.x] *= 1.0 / sqrt((double)p.n[threadIdx.x % p.T]);
+    __syncthreads();
+    const long long total = (long long)B * N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long idx = e % N;
+        const int b = (int)(e / N);
+        int u = 0;
+        while (u + 1 < p.T && idx >= p.yoff[u + 1]) ++u;
+        const int q = q0 + b;
+        const int tq = p.rank[task[q]];
+        const double v = sR[tq * p.T + u] * qkernel<double>(p.kind, xqw + (long long)q * p.d, dw + idx * p.d, s_eta,
+                                                             p.d, p.alpha, bm);
+        if (CPLX) {
+            rows[2 * e] = v;
+            rows[2 * e + 1] = 0.0;
+        } else {
+            rows[e] = v;
+        }
+    }
+}
+
+// var[q0 + b] = R_{tt} Q(x_b, x_b) - sum of the per-class-block quadratic forms (in block order)
+__global__ void k_var_tree_sum(const double* __restrict__ part, int nblk, int B, int q0, const int* __restrict__ task,
+                               const uint32_t* __restrict__ xqw, PostParams p, ThetaPtrs th, double* __restrict__ var) {
+    __shared__ double sR[MTGP_TMAX * MTGP_TMAX];
+    __shared__ double s_eta[MTGP_MAX_DIM];
+    __shared__ double s_bm[4];
+    load_R_post(sR, p, th);
+    if (threadIdx.x < p.d) s_eta[threadIdx.x] = th.eta[threadIdx.x];
+    const double* bm = load_bmix(s_bm, p);
+    __syncthreads();
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double s = 0.0;
+    for (int k = 0; k < nblk; ++k) s += part[(long long)b * nblk + k];
+    const int q = q0 + b;
+    const int tq = p.rank[task[q]];
+    const uint32_t* x = xqw + (long long)q * p.d;
+    var[q] = sR[tq * p.T + tq] * qkernel<double>(p.kind, x, x, s_eta, p.d, p.alpha, bm) - s;
+}
+
 // factor = true: per-frequency factors into fac; false: the quadratic forms of B queries
 template <bool CPLX, typename S>
 void dispatch_var(bool factor, int T, int B, const double* rows, const void* spec, double* fac, const int* task,
@@ -373,10 +428,14 @@ struct PostScratch {
     long long rows_cap = 0;
     long long* offs = nullptr;   // row offsets of the variance batch (multiples of n)
     int offs_cap = 0;
+    int offs_kind = -1;          // 0: equal sizes (i n), 1: unequal sizes (b N + yoff[u], u-major)
+    int offs_B = 0;
     double* fac = nullptr;       // per-frequency L D L^H factors of Lambda (variance)
     long long fac_cap = 0;
     double* part = nullptr;      // mean partial sums, slices x nq
     long long part_cap = 0;
+    double* vpart = nullptr;     // variance, unequal sizes: per (query, class block) sums
+    long long vpart_cap = 0;
 };
 std::map<const Handle*, PostScratch> g_post;
 std::mutex g_post_mu;
@@ -394,6 +453,7 @@ void posterior_release(const Handle* h) {
     cudaFree(it->second.offs);
     cudaFree(it->second.fac);
     cudaFree(it->second.part);
+    cudaFree(it->second.vpart);
     g_post.erase(it);
 }
 
@@ -477,7 +537,57 @@ int posterior_run(Handle* h, ThetaPtrs th, int nq, const double* xq, const int* 
         mtgp_prof_end(h, st);
     }
     if (!var) return MTGP_OK;
-    if (!h->equal) return MTGP_ERR_UNSUPPORTED;
+    if (!h->equal) {
+        // unequal sizes: rows of a batch of queries, their transforms per task, then the quadratic
+        // forms through the tree solver's factor class by class
+        const long long per_q = N * es;
+        int B = (int)((64LL << 20) / per_q);
+        if (B < 1) B = 1;
+        if (B > 1024) B = 1024;
+        if (B > nq) B = nq;
+        if ((long long)B * per_q > ps->rows_cap) {
+            cudaFree(ps->rows);
+            ps->rows_cap = (long long)B * per_q;
+            if (cudaMalloc(&ps->rows, (size_t)ps->rows_cap * sizeof(double)) != cudaSuccess) return MTGP_ERR_CUDA;
+        }
+        const int T = h->T;
+        if (B * T > ps->offs_cap || ps->offs_kind != 1 || ps->offs_B != B) {
+            // offsets of query b's task-u row: b N + yoff[u], grouped by task (u-major)
+            cudaFree(ps->offs);
+            ps->offs_cap = B * T;
+            if (cudaMalloc(&ps->offs, (size_t)ps->offs_cap * sizeof(long long)) != cudaSuccess) return MTGP_ERR_CUDA;
+            long long* tmp = new long long[ps->offs_cap];
+            for (int u = 0; u < T; ++u)
+                for (int b = 0; b < B; ++b) tmp[u * B + b] = (long long)b * N + h->yoff[u];
+            cudaMemcpyAsync(ps->offs, tmp, (size_t)ps->offs_cap * sizeof(long long), cudaMemcpyHostToDevice, st);
+            cudaStreamSynchronize(st);
+            delete[] tmp;
+            ps->offs_kind = 1;
+            ps->offs_B = B;
+        }
+        const int nblk = solve_tree_blocks(h);
+        if ((long long)B * nblk > ps->vpart_cap) {
+            cudaFree(ps->vpart);
+            ps->vpart_cap = (long long)B * nblk;
+            if (cudaMalloc(&ps->vpart, (size_t)ps->vpart_cap * sizeof(double)) != cudaSuccess) return MTGP_ERR_CUDA;
+        }
+        for (int q0 = 0; q0 < nq; q0 += B) {
+            const int Bb = (nq - q0) < B ? (nq - q0) : B;
+            mtgp_prof_begin(h, "var_rows", st);
+            if (h->cplx) k_var_rows_all<true><<<grid_for((long long)Bb * N), 256, 0, st>>>(ps->xq, task, q0, Bb, ps->design, pp, th, N, ps->rows);
+            else k_var_rows_all<false><<<grid_for((long long)Bb * N), 256, 0, st>>>(ps->xq, task, q0, Bb, ps->design, pp, th, N, ps->rows);
+            mtgp_prof_end(h, st);
+            mtgp_prof_begin(h, "var_xform", st);
+            for (int u = 0; u < T; ++u)
+                launch_transform(h, ps->rows, false, h->cplx, h->m[u], ps->offs + (long long)u * B, Bb, false, st);
+            mtgp_prof_end(h, st);
+            mtgp_prof_begin(h, "var_quad", st);
+            launch_var_tree(h, ps->rows, Bb, ps->vpart, st);
+            k_var_tree_sum<<<(Bb + 127) / 128, 128, 0, st>>>(ps->vpart, nblk, Bb, q0, task, ps->xq, pp, th, var);
+            mtgp_prof_end(h, st);
+        }
+        return MTGP_OK;
+    }
     const long long n = h->n[0];
     // batch so the rows stay within ~512 MB
     long long per_q = (long long)h->T * n * es;
@@ -491,8 +601,9 @@ int posterior_run(Handle* h, ThetaPtrs th, int nq, const double* xq, const int* 
         if (cudaMalloc(&ps->rows, (size_t)ps->rows_cap * sizeof(double)) != cudaSuccess) return MTGP_ERR_CUDA;
     }
     // offsets of the B*T rows for the batched transform
-    if (B * h->T > ps->offs_cap) {
+    if (B * h->T > ps->offs_cap || ps->offs_kind != 0) {
         cudaFree(ps->offs);
+        ps->offs_kind = 0;
         ps->offs_cap = B * h->T;
         if (cudaMalloc(&ps->offs, (size_t)ps->offs_cap * sizeof(long long)) != cudaSuccess) return MTGP_ERR_CUDA;
         long long* tmp = new long long[ps->offs_cap];

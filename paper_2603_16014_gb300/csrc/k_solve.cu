@@ -770,6 +770,39 @@ __global__ void k_finalize(const double* partials, const double* eta_partials, c
     if (tid < T) g_v[tid] = 0.5 * sc * tot[3 + gidx(p.rank[tid], p.rank[tid], T)];
 }
 
+// Posterior variance, unequal sizes: for B queries the quadratic forms kappa^H Lambda~^-1 kappa of the
+// transformed rows (one N-vector per query in the observation layout), class by class through the
+// factor the tree solver left in S: forward elimination u = L^-1 kappa with sum_j |u_j|^2 / D_j.
+// Lattices: classes 0 .. nT/2 only, a class with a distinct conjugate counted twice (the rows are
+// transforms of real vectors).  part[b * gridDim.x + blockIdx.x] = the sum of this CTA's classes.
+template <bool CPLX>
+__global__ void __launch_bounds__(kTreeThreads)
+k_var_tree(const double* Sb, double* rows, long long N, TreeParams p, double* part) {
+    using V = Vt<CPLX>;
+    __shared__ V s_part[kTreeCW][kTreeSlots][MTGP_TMAX];
+    __shared__ double s_red[kTreeWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int slot = warp * (32 / kTreeCW) + lane / kTreeCW;
+    const int cls = lane % kTreeCW;
+    const long long nT = p.nT;
+    const long long rho = (long long)blockIdx.x * kTreeCW + cls;
+    const long long ncls = (CPLX && nT >= 2) ? nT / 2 + 1 : nT;
+    const bool act = rho < ncls;
+    const bool mir = CPLX && act && rho != 0 && 2 * rho != nT;
+    double* rb = rows + (long long)blockIdx.y * N * (CPLX ? 2 : 1);
+    double quad = 0.0;
+    tree_forward<CPLX>(p, Sb, rb, rho, act, slot, quad, s_part);
+    if (mir) quad *= 2.0;
+    for (int o = 16; o > 0; o >>= 1) quad += __shfl_down_sync(0xffffffffu, quad, o);
+    if (lane == 0) s_red[warp] = quad;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < kTreeWarps; ++w) v += s_red[w];
+        part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = v;
+    }
+}
+
 int eq_blocks(const Handle* h) {
     long long b = (h->n[0] + kEqThreads - 1) / kEqThreads;
     if (b > 152 * 8) b = 152 * 8;
@@ -833,10 +866,10 @@ void launch_solve_equal(const Handle* h, ThetaPtrs th, bool grad, double* partia
     }
 }
 
-void launch_solve_tree(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st, bool gcv) {
+static TreeParams tree_params(const Handle* h, int s, bool grad, bool gcv) {
     TreeParams tp;
     tp.T = h->T;
-    tp.s = th.s;
+    tp.s = s;
     tp.grad = (grad && !gcv) ? 1 : 0;
     tp.gcv = gcv ? 1 : 0;
     tp.pt = h->noise_pt ? 1 : 0;
@@ -850,6 +883,18 @@ void launch_solve_tree(const Handle* h, ThetaPtrs th, bool grad, double* partial
         for (int u = 0; u < MTGP_TMAX; ++u)
             tp.po[t][u] = (t < h->T && u < h->T && t <= u) ? h->cols[h->col_of[t][u]].off : 0;
     }
+    return tp;
+}
+
+void launch_var_tree(const Handle* h, double* rows, int B, double* part, cudaStream_t st) {
+    const TreeParams tp = tree_params(h, 1, false, false);
+    dim3 grid((unsigned)solve_tree_blocks(h), (unsigned)B);
+    if (h->cplx) k_var_tree<true><<<grid, kTreeThreads, 0, st>>>(h->S, rows, h->N, tp, part);
+    else k_var_tree<false><<<grid, kTreeThreads, 0, st>>>(h->S, rows, h->N, tp, part);
+}
+
+void launch_solve_tree(const Handle* h, ThetaPtrs th, bool grad, double* partials, cudaStream_t st, bool gcv) {
+    const TreeParams tp = tree_params(h, th.s, grad, gcv);
     int blocks = solve_tree_blocks(h);
     if (h->fp32) {
         if (h->cplx) k_solve_tree<true, float><<<blocks, kTreeThreads, 0, st>>>(h->spec, h->wgt, h->yhat, h->S, h->Z, h->r, h->alpha, h->tau, tp, th, partials, h->status, h->gcv_h);

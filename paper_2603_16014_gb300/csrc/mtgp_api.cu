@@ -822,7 +822,6 @@ int mtgp_posterior(mtgp_t* hs, const double* eta, const double* W, int s, const 
     int rc = validate_theta(h, eta, W, s, v, sigma2);
     if (rc) return rc;
     if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
-    if (var && !h->equal) return fail(MTGP_ERR_UNSUPPORTED, "posterior variance needs equal task sizes in this build");
     if (nq == 0) return MTGP_OK;
     ThetaPtrs th{eta, W, s, v, sigma2, h->noise_pt ? h->T : 1, h->dsi_mix ? h->bmix : nullptr};
     // the solve leaves alpha = Lambda^-1 rhat and tau in the workspace

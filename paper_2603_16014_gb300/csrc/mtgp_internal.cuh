@@ -259,6 +259,9 @@ void launch_y_load(const Handle* h, const double* y, cudaStream_t st);
 // F(b) = (Z - conj(Z(-f))) / (2i) into the lead's and the partner's arrays; before the adjoint
 // transform, the lead's weights w_a + i w_b
 void launch_pair_split(const Handle* h, void* spec, cudaStream_t st);
+// posterior variance, unequal sizes: per (class block, query) sums of kappa^H Lambda~^-1 kappa over the
+// transformed rows of B queries (N doubles / complex values per query), from the tree solver's factor
+void launch_var_tree(const Handle* h, double* rows, int B, double* part, cudaStream_t st);
 void launch_pair_pack(const Handle* h, void* wgt, cudaStream_t st);
 void launch_eta_grad(const Handle* h, const double* eta, const void* omega, double* partials,
                      int nblk_max, cudaStream_t st);

@@ -93,13 +93,11 @@ def test_posterior_vs_dense_oracle(kind, d, m, precision):
     mean_ref, var_ref, prior = dense.posterior(kind, X, y, p.eta, p.W, p.v, p.sigma2, Xq, tq)
     model = _model(p, precision)
     model.set_y(torch.from_numpy(y))
-    equal = len(set(m)) == 1
-    mean, var = model.posterior(p.eta, p.W, p.v, p.sigma2, torch.from_numpy(xq), torch.from_numpy(tq), variance=equal)
+    mean, var = model.posterior(p.eta, p.W, p.v, p.sigma2, torch.from_numpy(xq), torch.from_numpy(tq), variance=True)
     model.sync()
     tol = TOL_NLL[precision]
     assert np.allclose(mean.cpu().numpy(), mean_ref, rtol=0, atol=tol * prior.max())
-    if equal:
-        assert np.allclose(var.cpu().numpy(), var_ref, rtol=0, atol=tol * prior.max())
+    assert np.allclose(var.cpu().numpy(), var_ref, rtol=0, atol=tol * prior.max())
 
 
 @pytest.mark.parametrize("nq", [1, 2, 257, 4099])
@@ -146,13 +144,6 @@ def test_errors_surface_through_status():
     out, _ = model.nll(p.eta, p.W, p.v, p.sigma2)  # and the handle stays usable
     model.sync()
     assert np.isfinite(out[0].item())
-    # unequal sizes: variance not supported in this build, mean is
-    q = inputs.make_problem("dnet", 2, (5, 3), seed=3)
-    mq = _model(q, "fp64")
-    mq.set_y(torch.zeros(q.N, dtype=torch.float64))
-    with pytest.raises(MTGPError) as ei:
-        mq.posterior(q.eta, q.W, q.v, q.sigma2, torch.zeros(4, 2, dtype=torch.float64), torch.zeros(4, dtype=torch.int32))
-    assert ei.value.code == 5
 
 
 # ----------------------------------------------------------------------------- full sizes
@@ -403,3 +394,28 @@ def test_host_buffer_entry_point_matches_device_call(kind, d, m, pt):
     with pytest.raises(Exception):
         model.nll_grad_host(h_th, h_out, p.T + 1)    # s out of range: refused before any device work
     model.close()
+
+
+@pytest.mark.parametrize("nq", [1, 3, 130])
+def test_nested_posterior_variance_batches_and_medium_size(nq):
+    """Unequal sizes: the variance through the tree solver's factor (rows of a query batch, per-task
+    transforms, class-by-class forward elimination), at a size with 256 residue classes, against
+    the per-class dense oracle; query counts below, at and above the batch edges."""
+    p = inputs.make_problem("lattice", 4, (12, 10, 8), seed=49, eta=0.6, v=0.1, sigma2=1e-4)
+    model = _model(p, "fp64")
+    X = model.points().cpu().numpy().view(np.uint32)
+    offs = np.concatenate([[0], np.cumsum(p.n)])
+    y = inputs.synth_y(p, [X[offs[t]:offs[t + 1]] for t in range(p.T)])
+    model.set_y(torch.from_numpy(y))
+    Xq, xq, tq = inputs.query_points(nq, 4, seed=7, tasks=3)
+    mean, var = model.posterior(p.eta, p.W, p.v, p.sigma2, torch.from_numpy(xq), torch.from_numpy(tq), variance=True)
+    model.sync()
+    k = min(nq, 3)
+    mean_ref, var_ref = spectral.posterior_by_class(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2,
+                                                    Xq[:k], tq[:k])
+    R = dense.task_covariance(p.W, p.v)
+    scale = np.abs(R).max() * (1 + 0.6 * np.pi ** 4 / 45) ** 4     # prior bound: R_tt prod_j (1 + eta_j K(0))
+    assert np.allclose(var.cpu().numpy()[:k], var_ref, rtol=0, atol=1e-8 * scale)
+    assert np.allclose(mean.cpu().numpy()[:k], mean_ref, rtol=0, atol=1e-8 * scale)
+    v = var.cpu().numpy()
+    assert np.all(v > -1e-9 * scale)
