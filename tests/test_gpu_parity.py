@@ -4,7 +4,7 @@ Tolerances: NLL within 1e-8 relative in FP64 mode and 1e-5 in FP32-transform mod
 within 1e-7 (FP64) / 1e-4 (FP32) of the gradient's max-norm scale.  Posterior: |delta mean| and
 |delta var| within 1e-8 (FP64) / 1e-5 (FP32) of the largest prior variance R_tt Q(x, x).
 FP32-transform mode is exercised on digital nets, the designs it is specified for: the SI lattice
-spectrum decays like f^-4 and falls below FP32 transform noise (precision modes).
+spectrum decays like f^-4, so its small eigenvalues fall below the FP32 transform noise.
 """
 import numpy as np
 import pytest
