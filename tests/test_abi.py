@@ -50,3 +50,28 @@ def test_oracle_not_imported_by_product_modules():
         if f.endswith(".py"):
             src = open(os.path.join(here, f)).read()
             assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_host_buffer_layout_round_trip():
+    # packed layouts of mtgp_nll_grad_host (host logic only): theta = eta | W (T x s) | v | sigma2,
+    # out = [NLL, quad, logdet] | tau | g_eta | g_W | g_v | g_sigma2
+    import numpy as np
+    from paper_2603_16014_gb300.mtgp import MTGP
+    m = MTGP.__new__(MTGP)
+    m.T, m.d = 3, 4
+    for nsig in (1, 3):
+        m.nsig = nsig
+        eta = np.arange(4.0) + 1
+        W = np.arange(6.0).reshape(3, 2) + 10
+        v = np.array([0.1, 0.2, 0.3])
+        s2 = np.full(nsig, 1e-4) * (1 + np.arange(nsig))
+        th = m.pack_theta(eta, W, v, s2, pin=False)
+        assert th.numel() == 4 + 6 + 3 + nsig
+        assert np.array_equal(th.numpy(), np.concatenate([eta, W.ravel(), v, s2]))
+        out = m.host_out(2, pin=False)
+        assert out.numel() == 3 + 3 + 4 + 6 + 3 + nsig
+        out.copy_(__import__("torch").arange(out.numel(), dtype=out.dtype))
+        o3, tau, ge, gW, gv, gs = m.unpack_out(out, 2)
+        assert o3.tolist() == [0, 1, 2] and tau.tolist() == [3, 4, 5] and ge.tolist() == [6, 7, 8, 9]
+        assert gW.shape == (3, 2) and gW[0, 0].item() == 10 and gW[2, 1].item() == 15
+        assert gv.tolist() == [16, 17, 18] and gs.numel() == nsig and gs[0].item() == 19
