@@ -550,3 +550,99 @@ def nll_grad_equal(kind, gen, shift, m, y, eta, W, v, sigma2, alpha=2):
     if mix:
         return out, g_eta, g_W, g_v, g_s2, np.array([tr(R[None] * dB[a_]) for a_ in range(4)])
     return out, g_eta, g_W, g_v, g_s2
+
+
+def grad_by_class(kind, gen, shift, m, y, eta, W, v, sigma2, loss="mle"):
+    """Gradient of L (Eq. 3.3, MLE or GCV form) through the residue classes mod n_T (unequal nested
+    sizes; any sizes), tau held at the loss's own optimum.  With M_rho the class matrix and every
+    dM_rho/dtheta assembled from the transformed first columns of the derivative kernels exactly as
+    M_rho is assembled from the kernel's (theorem item 3):
+      MLE: dL = sum_rho Re tr(G_rho dM_rho),  G = M^-1 - a a^H,  a = M^-1 rhat;
+      GCV: G = -(a b^H + b a^H) / B^2 + (2 A / B^3) M^-2,  b = M^-1 a,
+           A = sum_rho ||a||^2, B = sum_rho tr M^-1.
+    One shared sigma2.  Returns (L, g_eta, g_W, g_v, g_sigma2), W and v in user task order."""
+    from .design import kernel_1d
+    order = sorted_order(m)
+    n_user = [1 << int(x) for x in m]
+    offs = np.concatenate([[0], np.cumsum(n_user)])
+    X = [design_points(kind, gen, shift[t], n_user[t]) for t in order]
+    ys = [np.asarray(y[offs[t]:offs[t + 1]], dtype=np.float64) for t in order]
+    Ru = task_covariance(W, v)
+    R = Ru[np.ix_(order, order)]
+    n = [n_user[t] for t in order]
+    T, d = len(n), len(eta)
+    if np.ndim(sigma2) != 0:
+        raise NotImplementedError("one shared noise variance (per-task noise: the dense oracle)")
+    sig = np.full(T, float(sigma2))
+    ref = (nll_by_class if loss == "mle" else gcv_by_class)(kind, gen, shift, m, y, eta, W, v, float(sigma2))
+    tau_s = np.asarray(ref["tau"])[order]
+    mt = [int(np.log2(x)) for x in n]
+    yhat = [vdag(kind, ys[t].astype(np.complex128), mt[t]) for t in range(T)]
+    rhat = [yh.copy() for yh in yhat]
+    for t in range(T):
+        rhat[t][0] -= np.sqrt(n[t]) * tau_s[t]
+    # transformed first columns of Q and of its eta derivatives (sorted pairs t <= u)
+    lamQ, dlamQ = {}, {}
+    for t in range(T):
+        for u in range(t, T):
+            K1 = [kernel_1d(kind, X[t][:, j], np.full(n[t], X[u][0, j], dtype=np.uint64)) for j in range(d)]
+            fac = [1.0 + eta[j] * K1[j] for j in range(d)]
+            sc = np.sqrt(n[u])
+            lamQ[(t, u)] = sc * vdag(kind, np.prod(fac, axis=0).astype(np.complex128), mt[t])
+            dlamQ[(t, u)] = [sc * vdag(kind, (K1[j] * np.prod([fac[l] for l in range(d) if l != j], axis=0)
+                                              if d > 1 else K1[j]).astype(np.complex128), mt[t]) for j in range(d)]
+
+    def blocks(dR=None, eta_j=None, noise=None):
+        out = {}
+        for t in range(T):
+            for u in range(t, T):
+                if eta_j is not None:
+                    val = R[t, u] * dlamQ[(t, u)][eta_j]
+                elif dR is not None:
+                    val = dR[t, u] * lamQ[(t, u)]
+                else:
+                    val = np.zeros(n[t], dtype=np.complex128)
+                if noise is not None and t == u:
+                    val = val + noise[t]
+                out[(t, u)] = val
+        return out
+
+    lam = blocks(dR=R, noise=sig)
+    classes = []
+    A = Bt = 0.0
+    for rho in range(n[-1]):
+        nodes, M = class_matrix(lam, n, rho)
+        Minv = np.linalg.inv(M)
+        a = Minv @ np.array([rhat[t][f] for (t, f) in nodes])
+        classes.append((rho, Minv, a))
+        A += float(np.vdot(a, a).real)
+        Bt += float(np.trace(Minv).real)
+
+    def contract(blk):
+        tot = 0.0
+        for rho, Minv, a in classes:
+            _, dM = class_matrix(blk, n, rho)
+            if loss == "mle":
+                G = Minv - np.outer(a, a.conj())
+            else:
+                b = Minv @ a
+                G = -(np.outer(a, b.conj()) + np.outer(b, a.conj())) / Bt ** 2 + (2.0 * A / Bt ** 3) * (Minv @ Minv)
+            tot += float(np.sum(G * dM.T).real)           # tr(G dM)
+        return tot
+
+    g_eta = np.array([contract(blocks(eta_j=j)) for j in range(d)])
+    s = W.shape[1]
+    g_W = np.zeros_like(W)
+    for tc in range(T):
+        for k in range(s):
+            e = np.zeros(T)
+            e[tc] = 1.0
+            dRu = np.outer(e, W[:, k]) + np.outer(W[:, k], e)
+            g_W[tc, k] = contract(blocks(dR=dRu[np.ix_(order, order)]))
+    g_v = np.zeros(T)
+    for tc in range(T):
+        dRu = np.zeros((T, T))
+        dRu[tc, tc] = 1.0
+        g_v[tc] = contract(blocks(dR=dRu[np.ix_(order, order)]))
+    g_s2 = contract(blocks(noise=np.ones(T)))
+    return ref["L"], g_eta, g_W, g_v, g_s2

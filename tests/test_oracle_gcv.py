@@ -99,3 +99,20 @@ def test_gcv_gradient_matches_central_differences(kind, m):
     hs = h * p.sigma2
     fd = (L(p.eta, p.W, p.v, p.sigma2 + hs) - L(p.eta, p.W, p.v, p.sigma2 - hs)) / (2 * hs)
     assert fd == pytest.approx(gs, rel=1e-5, abs=1e-9 * out["L"])
+
+
+@pytest.mark.parametrize("kind,m", [("lattice", (5, 3, 2)), ("dnet", (4, 4, 2)), ("lattice", (3, 5))])
+@pytest.mark.parametrize("loss", ["mle", "gcv"])
+def test_per_class_gradient_matches_dense(kind, m, loss):
+    # the residue-class gradient (any sizes) against the dense analytic gradient, itself pinned by
+    # central differences: same loss, same gradient for eta, W, v, sigma2
+    p = inputs.make_problem(kind, 2, m, seed=91, eta=0.6, v=0.2, sigma2=1e-3, s=2)
+    X = dense.all_points(p.kind, p.gen, p.shift, p.m)
+    y = inputs.synth_y(p, X)
+    L, ge, gW, gv, gs = spectral.grad_by_class(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2, loss)
+    f = dense.nll_grad if loss == "mle" else dense.gcv_grad
+    out, re, rW, rv, rs = f(p.kind, X, y, p.eta, p.W, p.v, p.sigma2)
+    assert L == pytest.approx(out["L"], rel=1e-11)
+    got = np.concatenate([ge, gW.ravel(), gv, [gs]])
+    exp = np.concatenate([re, rW.ravel(), rv, [rs]])
+    assert np.abs(got - exp).max() <= 1e-9 * np.abs(exp).max()
