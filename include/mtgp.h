@@ -281,10 +281,13 @@ int mtgp_gcv_grad(mtgp_t* h, const double* eta, const double* W, int s, const do
  * beta1 = 0.9, beta2 = 0.999, eps = 1e-8; gradients returned by mtgp_batch_nll_grad are with respect
  * to the packed (natural) parameters.
  *
- * mtgp_batch_create -- host arrays of length nfits: kind, d, T, m, gen_cols; gen and shift are the
- *   fits' generator / shift arrays (as mtgp_create) concatenated; s is W's column count for every
- *   fit (1 <= s <= T).  precision as mtgp_create.  MTGP_ERR_UNSUPPORTED if a fit's size is outside
- *   the fused kernels (m >= 4, per-CTA tiles <= 96 KB).
+ * mtgp_batch_create -- host arrays of length nfits: kind, d, T, m, gen_cols, precision; gen and shift
+ *   are the fits' generator / shift arrays (as mtgp_create) concatenated; s is W's column count for
+ *   every fit (1 <= s <= T).  precision[f] is MTGP_FP64 or MTGP_FP32_TRANSFORM for fit f (as
+ *   mtgp_create, without MTGP_NOISE_PER_TASK): FP32 transforms meet the 1e-5 relative NLL tolerance on
+ *   digital nets, while the SI spectrum of a lattice decays below FP32 transform noise, so lattice fits
+ *   should take MTGP_FP64.  Fits of both precisions run in one batch (separate kernel classes).
+ *   MTGP_ERR_UNSUPPORTED if a fit's size is outside the fused kernels (m >= 4, per-CTA tiles <= 96 KB).
  * mtgp_batch_layout -- host arrays of nfits + 1 offsets into the packed parameters and observations.
  * mtgp_batch_set_y -- device, all fits' observations concatenated (each fit as mtgp_set_y).
  * mtgp_batch_set_theta / mtgp_batch_get_theta -- device packed parameters (natural scale); set
@@ -297,10 +300,17 @@ int mtgp_gcv_grad(mtgp_t* h, const double* eta, const double* W, int s, const do
  *   dimension bucket) on one representative fit (reps timed runs each), keeps the fastest for all
  *   fits of that key and rebuilds the launch tables; chosen (host, nfits, or NULL) receives the
  *   splits.  Needs observations and parameters set; synchronises the device.
+ * mtgp_batch_fit -- fit every model of the batch by `steps` Adam steps on its MLE loss (Sec. 4.1's
+ *   optimisation loop, run for all fits at once): theta0 (device, packed natural parameters) starts
+ *   the run and resets the Adam moments (as mtgp_batch_set_theta); NULL continues from the current
+ *   parameters and optimiser state (e.g. those mtgp_propose set).  lr > 0 is the step size and
+ *   use_graph, trace as mtgp_batch_adam.  theta_out (device, packed, or NULL) receives the final
+ *   parameters and nll_out (device, nfits, or NULL) the NLL at them (one more batched evaluation).
+ *   Needs mtgp_batch_set_y first; asynchronous on `stream` (a graph run needs a non-default stream).
  */
 typedef struct mtgp_batch_s mtgp_batch_t;
 int mtgp_batch_create(mtgp_batch_t** out, int nfits, const int* kind, const int* d, const int* T, const int* m,
-                      const uint32_t* gen, const int* gen_cols, const uint32_t* shift, int s, int precision);
+                      const uint32_t* gen, const int* gen_cols, const uint32_t* shift, int s, const int* precision);
 int mtgp_batch_destroy(mtgp_batch_t* b);
 int mtgp_batch_layout(const mtgp_batch_t* b, long long* param_offsets, long long* y_offsets);
 int mtgp_batch_set_y(mtgp_batch_t* b, const double* y, cudaStream_t stream);
@@ -309,6 +319,8 @@ int mtgp_batch_get_theta(mtgp_batch_t* b, double* theta, cudaStream_t stream);
 int mtgp_batch_nll_grad(mtgp_batch_t* b, double* nll, double* grad, cudaStream_t stream);
 int mtgp_batch_adam(mtgp_batch_t* b, int steps, double lr, int use_graph, double* trace, cudaStream_t stream);
 int mtgp_batch_autotune(mtgp_batch_t* b, int reps, int* chosen, cudaStream_t stream);
+int mtgp_batch_fit(mtgp_batch_t* b, const double* theta0, int steps, double lr, int use_graph, double* theta_out,
+                   double* nll_out, double* trace, cudaStream_t stream);
 
 /*
  * Learned proposal of starting hyper-parameters.  The paper has no counterpart: it starts every fit's
@@ -369,6 +381,20 @@ int mtgp_mlp_gradients(mtgp_mlp_t* m, int B, const float* x, const float* target
                        const int* rows, float* grads, float* loss, cudaStream_t stream);
 int mtgp_mlp_train_step(mtgp_mlp_t* m, int B, const float* x, const float* target, const float* mask,
                         const int* rows, float lr, float* loss, cudaStream_t stream);
+
+/*
+ * mtgp_propose -- the learned starting point of every fit in the batch, in one call: the spectral
+ * features of mtgp_batch_features, the network's forward pass (in chunks of its max_batch rows) and
+ * mtgp_batch_set_theta_proposal on the prediction.  A following mtgp_batch_fit with theta0 = NULL
+ * starts the optimiser there.  No counterpart in the paper (it starts each fit from a fixed point).
+ *   net   a network mapping 258 features to 37 outputs (mtgp_mlp_create widths 258, ..., 37), with
+ *         its parameters and input scaling set; otherwise MTGP_ERR_INVALID_ARG.
+ *   pred  device, nfits x 37 FP32, or NULL: receives the prediction (layout of mtgp_batch_targets).
+ * Needs mtgp_batch_set_y first, s = 2 and d <= 12 for every fit (else MTGP_ERR_UNSUPPORTED).  The
+ * first call allocates the batch's feature and prediction buffers (synchronously); later calls are
+ * asynchronous on `stream`.  The network's buffers are used: order calls on one network on one stream.
+ */
+int mtgp_propose(mtgp_batch_t* b, mtgp_mlp_t* net, float* pred, cudaStream_t stream);
 
 /* mtgp_workspace_bytes -- device bytes the handle holds (for capacity planning). */
 long long mtgp_workspace_bytes(const mtgp_t* h);

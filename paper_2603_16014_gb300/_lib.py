@@ -38,7 +38,7 @@ _SIGS = {
     "mtgp_profile": (_i, [_p, _i]),
     "mtgp_profile_read": (_i, [_p, _i, _p, _p, _p, _p]),
     "mtgp_nll_equal_static": (_i, [_i, _i, _i, _i, _p, _i, _p, _i, _p, _p, _p, _i, _p, _p, _p, _p, _p, _p]),
-    "mtgp_batch_create": (_i, [ctypes.POINTER(_p), _i, _p, _p, _p, _p, _p, _p, _p, _i, _i]),
+    "mtgp_batch_create": (_i, [ctypes.POINTER(_p), _i, _p, _p, _p, _p, _p, _p, _p, _i, _p]),
     "mtgp_batch_destroy": (_i, [_p]),
     "mtgp_batch_layout": (_i, [_p, _p, _p]),
     "mtgp_batch_set_y": (_i, [_p, _p, _p]),
@@ -47,6 +47,8 @@ _SIGS = {
     "mtgp_batch_nll_grad": (_i, [_p, _p, _p, _p]),
     "mtgp_batch_adam": (_i, [_p, _i, ctypes.c_double, _i, _p, _p]),
     "mtgp_batch_autotune": (_i, [_p, _i, _p, _p]),
+    "mtgp_batch_fit": (_i, [_p, _p, _i, ctypes.c_double, _i, _p, _p, _p, _p]),
+    "mtgp_propose": (_i, [_p, _p, _p, _p]),
     "mtgp_gcv": (_i, [_p, _p, _p, _i, _p, _p, _p, _p, _p]),
     "mtgp_set_smoothness": (_i, [_p, _i]),
     "mtgp_set_dsi_weights": (_i, [_p, _p, _p]),

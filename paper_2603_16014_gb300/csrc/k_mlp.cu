@@ -317,6 +317,13 @@ void backward(mtgp_mlp_s* m, int B, const float* tgt, const float* mask, const i
 
 }  // namespace
 
+// input width, output width and largest batch of a network (for callers inside the library)
+void mlp_shape(const mtgp_mlp_t* m, int* in_width, int* out_width, int* max_batch) {
+    *in_width = m->w[0];
+    *out_width = m->w[m->L];
+    *max_batch = m->maxB;
+}
+
 extern "C" {
 
 int mtgp_mlp_create(mtgp_mlp_t** out, int nlayers, const int* widths, int max_batch) {

@@ -25,6 +25,7 @@ constexpr int kSide = 16;
 
 struct Cls {
     int phase;
+    bool fp32;        // transform precision of the class's fits
     bool cplx;
     int key;          // T (phase B) or dimension bucket (phases A, C)
     int2* items;      // device
@@ -75,7 +76,6 @@ __global__ void k_batch_tick(int* tstep, int k) { *tstep += k; }
 
 struct mtgp_batch_s {
     int nfits = 0, s = 1;
-    bool fp32 = true;
     std::vector<mtgp_t*> fits;
     std::vector<int> a;
     std::vector<long long> poff, yoff, partoff;
@@ -96,6 +96,8 @@ struct mtgp_batch_s {
     double* gtrace = nullptr;
     int nsm = 1;
     void* fdesc = nullptr;  // proposal descriptors (device), built on first use
+    float* pfeat = nullptr;  // mtgp_propose: features (nfits x 258) and prediction (nfits x 37), on first use
+    float* ppred = nullptr;
 };
 
 namespace {
@@ -164,13 +166,14 @@ int build_plan(mtgp_batch_s* b) {
         return hx.n[0] * hx.T * hx.T > hy.n[0] * hy.T * hy.T;
     });
     for (int ph = 0; ph < 3; ++ph) {
-        std::map<std::pair<int, int>, std::vector<int2>> items;
-        std::map<std::pair<int, int>, std::pair<size_t, int>> res;  // smem, threads
+        // class key: (transform precision, complex spectra, T or dimension bucket)
+        std::map<std::tuple<int, int, int>, std::vector<int2>> items;
+        std::map<std::tuple<int, int, int>, std::pair<size_t, int>> res;  // smem, threads
         for (int f : order) {
             const Handle& h = b->fits[f]->h;
             const int m = h.m[0], a = b->a[f];
             const int key = ph == 1 ? h.T : dbucket(h.d);
-            auto k = std::make_pair(h.cplx ? 1 : 0, key);
+            auto k = std::make_tuple(h.fp32 ? 1 : 0, h.cplx ? 1 : 0, key);
             const int nblk = ph == 1 ? (1 << a) : (1 << (m - a));
             for (int j = 0; j < nblk; ++j) items[k].push_back(make_int2(f, j));
             const size_t sm = fused_smem(ph, h.T, h.ncols, m, a, h.fp32, h.cplx);
@@ -182,13 +185,14 @@ int build_plan(mtgp_batch_s* b) {
         for (auto& kv : items) {
             Cls c;
             c.phase = ph;
-            c.cplx = kv.first.first != 0;
-            c.key = kv.first.second;
+            c.fp32 = std::get<0>(kv.first) != 0;
+            c.cplx = std::get<1>(kv.first) != 0;
+            c.key = std::get<2>(kv.first);
             c.nitems = (int)kv.second.size();
             c.smem = res[kv.first].first;
             c.threads = res[kv.first].second;
             const int T = ph == 1 ? c.key : 1;
-            const int per_sm = fused_resident_blocks(ph, b->fp32, c.cplx, T, c.key, c.threads, c.smem);
+            const int per_sm = fused_resident_blocks(ph, c.fp32, c.cplx, T, c.key, c.threads, c.smem);
             c.grid = std::min(c.nitems, per_sm * b->nsm);
             if (cudaMalloc(&c.items, sizeof(int2) * c.nitems) != cudaSuccess)
                 return bfail(MTGP_ERR_CUDA, "batch item table allocation failed");
@@ -394,8 +398,8 @@ void check_launch(const Cls& c, int T) {
     if (!on) return;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
-        std::fprintf(stderr, "batch launch failed: %s phase=%d cplx=%d key=%d T=%d grid=%d threads=%d smem=%zu items=%d\n",
-                     cudaGetErrorString(e), c.phase, (int)c.cplx, c.key, T, c.grid, c.threads, c.smem, c.nitems);
+        std::fprintf(stderr, "batch launch failed: %s phase=%d fp32=%d cplx=%d key=%d T=%d grid=%d threads=%d smem=%zu items=%d\n",
+                     cudaGetErrorString(e), c.phase, (int)c.fp32, (int)c.cplx, c.key, T, c.grid, c.threads, c.smem, c.nitems);
 }
 
 // the three phases of one batched NLL + gradient evaluation on stream st (classes forked to side streams)
@@ -405,7 +409,7 @@ void launch_eval(mtgp_batch_s* b, cudaStream_t st) {
         if (cl.size() == 1) {
             const Cls& c = cl[0];
             const int T = ph == 1 ? c.key : 1;
-            fused_phase(ph, b->fp32, c.cplx, T, c.key, nullptr, b->descs, c.items, c.nitems, c.grid, c.threads, c.smem, st);
+            fused_phase(ph, c.fp32, c.cplx, T, c.key, nullptr, b->descs, c.items, c.nitems, c.grid, c.threads, c.smem, st);
             check_launch(c, T);
             continue;
         }
@@ -415,7 +419,7 @@ void launch_eval(mtgp_batch_s* b, cudaStream_t st) {
             cudaStream_t ss = b->side[i % kSide];
             cudaStreamWaitEvent(ss, b->evfork, 0);
             const int T = ph == 1 ? c.key : 1;
-            fused_phase(ph, b->fp32, c.cplx, T, c.key, nullptr, b->descs, c.items, c.nitems, c.grid, c.threads, c.smem, ss);
+            fused_phase(ph, c.fp32, c.cplx, T, c.key, nullptr, b->descs, c.items, c.nitems, c.grid, c.threads, c.smem, ss);
             check_launch(c, T);
         }
         const int used = (int)std::min<size_t>(cl.size(), kSide);
@@ -442,20 +446,22 @@ void launch_steps(mtgp_batch_s* b, int steps, double lr, double* trace, cudaStre
 extern "C" {
 
 int mtgp_batch_create(mtgp_batch_t** out, int nfits, const int* kind, const int* d, const int* T, const int* m,
-                      const uint32_t* gen, const int* gen_cols, const uint32_t* shift, int s, int precision) {
+                      const uint32_t* gen, const int* gen_cols, const uint32_t* shift, int s, const int* precision) {
     if (!out) return bfail(MTGP_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (nfits < 1 || !kind || !d || !T || !m || !gen || !gen_cols || !shift)
+    if (nfits < 1 || !kind || !d || !T || !m || !gen || !gen_cols || !shift || !precision)
         return bfail(MTGP_ERR_INVALID_ARG, "nfits < 1 or NULL host array");
     if (s < 1) return bfail(MTGP_ERR_INVALID_ARG, "s must be >= 1");
-    if (precision & MTGP_NOISE_PER_TASK)
-        return bfail(MTGP_ERR_UNSUPPORTED, "batched fits take one noise variance per fit");
-    for (int f = 0; f < nfits; ++f)
+    for (int f = 0; f < nfits; ++f) {
+        if (precision[f] & MTGP_NOISE_PER_TASK)
+            return bfail(MTGP_ERR_UNSUPPORTED, "batched fits take one noise variance per fit");
+        if (precision[f] != MTGP_FP64 && precision[f] != MTGP_FP32_TRANSFORM)
+            return bfail(MTGP_ERR_INVALID_ARG, "precision[f] must be MTGP_FP64 or MTGP_FP32_TRANSFORM");
         if (T[f] < s) return bfail(MTGP_ERR_INVALID_ARG, "every fit needs T >= s");
+    }
     auto* b = new mtgp_batch_s();
     b->nfits = nfits;
     b->s = s;
-    b->fp32 = precision == MTGP_FP32_TRANSFORM;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -466,14 +472,14 @@ int mtgp_batch_create(mtgp_batch_t** out, int nfits, const int* kind, const int*
     for (int f = 0; f < nfits; ++f) {
         std::vector<int> mm(T[f], m[f]);
         mtgp_t* hf = nullptr;
-        int rc = mtgp_create(&hf, kind[f], d[f], T[f], mm.data(), gen + goff, gen_cols[f], shift + soff, precision);
+        int rc = mtgp_create(&hf, kind[f], d[f], T[f], mm.data(), gen + goff, gen_cols[f], shift + soff, precision[f]);
         if (rc) {
             mtgp_batch_destroy(b);
             return rc;
         }
         b->fits.push_back(hf);
         int a = 0, lgL = 0;
-        if (!fused_plan(m[f], hf->h.ncols, b->fp32, hf->h.cplx, -1, &a, &lgL)) {
+        if (!fused_plan(m[f], hf->h.ncols, hf->h.fp32, hf->h.cplx, -1, &a, &lgL)) {
             mtgp_batch_destroy(b);
             return bfail(MTGP_ERR_UNSUPPORTED, "a fit's size is not handled by the fused kernels (m >= 4, tiles <= 96 KB)");
         }
@@ -531,7 +537,7 @@ int mtgp_batch_destroy(mtgp_batch_t* b) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     for (auto* f : b->fits) mtgp_destroy(f);
     void* ptrs[] = {b->th_log, b->th_nat, b->g_nat, b->m1, b->m2, b->out, b->tau, b->partials, b->counters, b->pinfo,
-                    b->tstep, b->descs, b->fdesc};
+                    b->tstep, b->descs, b->fdesc, b->pfeat, b->ppred};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kSide; ++i) {
@@ -644,6 +650,53 @@ int mtgp_batch_set_theta_proposal(mtgp_batch_t* b, const float* pred, cudaStream
                                                             b->th_log, b->th_nat, b->m1, b->m2);
     cudaMemsetAsync(b->tstep, 0, sizeof(int), st);
     return launch_status("mtgp_batch_set_theta_proposal");
+}
+
+int mtgp_batch_fit(mtgp_batch_t* b, const double* theta0, int steps, double lr, int use_graph, double* theta_out,
+                   double* nll_out, double* trace, cudaStream_t st) {
+    if (!b || steps < 1) return bfail(MTGP_ERR_INVALID_ARG, "NULL handle or steps < 1");
+    if (!(lr > 0.0)) return bfail(MTGP_ERR_INVALID_ARG, "lr must be > 0");
+    int rc;
+    if (theta0) {
+        rc = mtgp_batch_set_theta(b, theta0, st);
+        if (rc) return rc;
+    }
+    rc = mtgp_batch_adam(b, steps, lr, use_graph, trace, st);
+    if (rc) return rc;
+    if (nll_out) {
+        // the objective at the parameters the last step produced (one more batched evaluation)
+        rc = mtgp_batch_nll_grad(b, nll_out, nullptr, st);
+        if (rc) return rc;
+    }
+    if (theta_out) return mtgp_batch_get_theta(b, theta_out, st);
+    return MTGP_OK;
+}
+
+int mtgp_propose(mtgp_batch_t* b, mtgp_mlp_t* net, float* pred, cudaStream_t st) {
+    if (!b || !net) return bfail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    int in_w = 0, out_w = 0, max_b = 0;
+    mlp_shape(net, &in_w, &out_w, &max_b);
+    if (in_w != kFeat || out_w != kOut)
+        return bfail(MTGP_ERR_INVALID_ARG, "the network must map 258 features to 37 outputs");
+    for (auto* f : b->fits)
+        if (!f->h.y_set) return bfail(MTGP_ERR_STATE, "mtgp_batch_set_y must be called first");
+    int rc = ensure_fdesc(b);
+    if (rc) return rc;
+    if (!b->pfeat) {
+        if (cudaMalloc(&b->pfeat, sizeof(float) * kFeat * (size_t)b->nfits) != cudaSuccess ||
+            cudaMalloc(&b->ppred, sizeof(float) * kOut * (size_t)b->nfits) != cudaSuccess)
+            return bfail(MTGP_ERR_CUDA, "proposal buffer allocation failed");
+    }
+    float* y = pred ? pred : b->ppred;
+    k_batch_features<<<b->nfits, 256, 0, st>>>(static_cast<const FeatDesc*>(b->fdesc), b->pfeat);
+    rc = launch_status("mtgp_propose (features)");
+    if (rc) return rc;
+    for (int r0 = 0; r0 < b->nfits; r0 += max_b) {
+        const int rows = std::min(max_b, b->nfits - r0);
+        rc = mtgp_mlp_forward(net, rows, b->pfeat + (size_t)r0 * kFeat, y + (size_t)r0 * kOut, st);
+        if (rc) return rc;
+    }
+    return mtgp_batch_set_theta_proposal(b, y, st);
 }
 
 int mtgp_batch_autotune(mtgp_batch_t* b, int reps, int* chosen, cudaStream_t st) {

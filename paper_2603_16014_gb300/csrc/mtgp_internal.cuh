@@ -308,6 +308,9 @@ size_t fused_smem(int phase, int T, int C, int m, int a, bool fp32, bool cplx);
 int fused_threads(int phase, int a, int d);
 int fused_resident_blocks(int phase, bool fp32, bool cplx, int T, int dmax, int threads, size_t smem);
 
+// k_mlp.cu: input width, output width and largest batch of a network
+void mlp_shape(const mtgp_mlp_t* m, int* in_width, int* out_width, int* max_batch);
+
 // records the message returned by mtgp_last_error_string for the calling thread (mtgp_api.cu)
 void mtgp_set_error(const char* msg);
 

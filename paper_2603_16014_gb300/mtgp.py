@@ -264,12 +264,19 @@ class Batch:
 
     ``problems``: objects with kind, d, m (equal sizes), gen, shift (e.g. inputs.Problem).
     Parameters are packed per fit as [eta, W (T x s), v, sigma2].
+    ``precision``: "fp32" or "fp64" for every fit, "auto" (FP32 transforms for digital nets, FP64 for
+    lattices, whose spectra decay below FP32 transform noise), or one of those per fit (a list).
     """
 
-    def __init__(self, problems, s: int = 2, precision: str = "fp32"):
+    def __init__(self, problems, s: int = 2, precision="fp32"):
         self.problems = list(problems)
         n = len(self.problems)
         kind = [LATTICE if p.kind == "lattice" else DNET for p in self.problems]
+        if isinstance(precision, str):
+            precision = [precision] * n
+        precision = [("fp64" if k == LATTICE else "fp32") if q == "auto" else q for q, k in zip(precision, kind)]
+        assert len(precision) == n and all(q in ("fp32", "fp64") for q in precision), precision
+        self.precision = precision
         d = [int(p.d) for p in self.problems]
         T = [len(p.m) for p in self.problems]
         m = [int(p.m[0]) for p in self.problems]
@@ -286,7 +293,8 @@ class Batch:
                                       _carr(ctypes.c_int, T), _carr(ctypes.c_int, m),
                                       gen.ctypes.data_as(ctypes.c_void_p), _carr(ctypes.c_int, gcols),
                                       shift.ctypes.data_as(ctypes.c_void_p), s,
-                                      FP32_TRANSFORM if precision == "fp32" else FP64), "mtgp_batch_create")
+                                      _carr(ctypes.c_int, [FP32_TRANSFORM if q == "fp32" else FP64 for q in precision])),
+              "mtgp_batch_create")
         self._h = h
         self.n, self.s = n, s
         po = (ctypes.c_longlong * (n + 1))()
@@ -333,6 +341,19 @@ class Batch:
     def adam(self, steps: int, lr: float, graph: bool = True, trace=None, stream=None):
         check(lib().mtgp_batch_adam(self._h, steps, lr, 1 if graph else 0, _ptr(trace), _stream(stream)),
               "mtgp_batch_adam")
+
+    def fit(self, theta0, steps: int, lr: float, graph: bool = True, trace=None, final_nll: bool = True,
+            stream=None):
+        """mtgp_batch_fit: ``steps`` Adam steps from theta0 (packed natural parameters, or None to continue
+        from the current parameters, e.g. after propose()); returns (final packed parameters, NLL at
+        them or None)."""
+        t0 = None if theta0 is None else _dev(theta0)
+        self._t = t0
+        th = torch.empty(self.nparams, dtype=torch.float64, device="cuda")
+        nll = torch.empty(self.n, dtype=torch.float64, device="cuda") if final_nll else None
+        check(lib().mtgp_batch_fit(self._h, _ptr(t0), int(steps), float(lr), 1 if graph else 0, _ptr(th), _ptr(nll),
+                                   _ptr(trace), _stream(stream)), "mtgp_batch_fit")
+        return th, nll
 
     def autotune(self, reps: int = 3, stream=None):
         chosen = (ctypes.c_int * self.n)()

@@ -136,7 +136,8 @@ def train(mlp: MLP, feats, targets, masks, steps: int, batch: int = 256, lr: flo
 
 
 def propose(batch, mlp: MLP, stream=None) -> torch.Tensor:
-    """Set every fit's parameters to the network's prediction from its features; returns the prediction."""
-    pred = mlp.forward(batch.features(stream), stream)
-    batch.set_theta_proposal(pred, stream)
+    """Set every fit's parameters to the network's prediction from its features (mtgp_propose: features,
+    forward pass and parameter map in one call); returns the prediction."""
+    pred = torch.empty((batch.n, mlp.widths[-1]), dtype=torch.float32, device="cuda")
+    check(lib().mtgp_propose(batch._h, mlp._h, _ptr(pred), _stream(stream)), "mtgp_propose")
     return pred

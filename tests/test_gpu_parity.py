@@ -240,6 +240,50 @@ def test_full_lattice_d16_T5_nested_vs_class_oracle():
               with_sigma2=True, h=1e-4, rtol=1e-6)
 
 
+@pytest.mark.parametrize("kind", ["lattice", "dnet"])
+def test_medium_nested_gradient_vs_class_oracle(kind):
+    """Nested sizes n = 2^12, 2^10, 2^8 (tree solver, FP64): every gradient entry against the residue-class
+    oracle's gradient (sum over classes of tr(G dM), built independently of the dense matrix)."""
+    p = inputs.make_problem(kind, 4, (12, 10, 8), seed=61, s=2, eta=(0.3, 1.5), v=0.1, sigma2=1e-6)
+    X = _points_oracle(p)
+    y = inputs.synth_y(p, X)
+    model = _model(p, "fp64")
+    model.set_y(torch.from_numpy(y))
+    out, tau, ge, gW, gv, gs = model.nll_grad(p.eta, p.W, p.v, p.sigma2)
+    model.sync()
+    L, g_eta, g_W, g_v, g_s2 = spectral.grad_by_class(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2)
+    N = sum(1 << x for x in p.m)
+    assert abs(out[0].item() - 0.5 * (L + N * np.log(2 * np.pi))) <= 1e-8 * abs(out[0].item())
+    gref = 0.5 * np.concatenate([g_eta, g_W.ravel(), g_v, [g_s2]])
+    got = np.concatenate([ge.cpu().numpy(), gW.cpu().numpy().ravel(), gv.cpu().numpy(), gs.cpu().numpy()])
+    scale = np.abs(gref).max()
+    assert np.all(np.abs(got - gref) <= TOL_GRAD["fp64"] * scale), (got, gref)
+
+
+def test_autograd_function_gradient_vs_dense_oracle():
+    """torch.autograd through mtgp.NLLFunction (the hand-written adjoint behind the autograd interface):
+    d(3 NLL + 2)/d(eta, W, v, sigma2) against 3/2 times the dense oracle's analytic gradient of L."""
+    from paper_2603_16014_gb300.mtgp import nll as nll_fn
+    for kind, d, m in (("lattice", 2, (6, 4)), ("dnet", 3, (5, 5, 5))):
+        p = inputs.make_problem(kind, d, m, seed=62, s=2, eta=0.6, v=0.2, sigma2=1e-4)
+        X = _points_oracle(p)
+        y = inputs.synth_y(p, X)
+        ref, g_eta, g_W, g_v, g_s2 = dense.nll_grad(p.kind, X, y, p.eta, p.W, p.v, p.sigma2)
+        model = _model(p, "fp64")
+        model.set_y(torch.from_numpy(y))
+        th = [torch.as_tensor(np.asarray(a, dtype=np.float64)).cuda().requires_grad_()
+              for a in (p.eta, p.W, p.v, [p.sigma2])]
+        loss = 3.0 * nll_fn(model, *th) + 2.0
+        grads = torch.autograd.grad(loss, th)
+        model.sync()
+        assert abs(loss.item() - (3.0 * ref["nll"] + 2.0)) <= 1e-8 * abs(3.0 * ref["nll"] + 2.0)
+        gref = 1.5 * np.concatenate([g_eta, g_W.ravel(), g_v, [g_s2]])
+        got = np.concatenate([g.detach().cpu().numpy().ravel() for g in grads])
+        assert grads[1].shape == th[1].shape and grads[3].shape == th[3].shape
+        assert np.all(np.abs(got - gref) <= TOL_GRAD["fp64"] * np.abs(gref).max()), (kind, got, gref)
+        model.close()
+
+
 # ----------------------------------------------------------------------------- full sizes, bench launch shapes
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
@@ -269,35 +313,48 @@ def test_full_size_posterior_sampled_outputs(precision):
     assert np.all(np.abs(var[vpick] - vref) <= tol * vprior), np.max(np.abs(var[vpick] - vref) / vprior)
 
 
+LATTICE_SAMPLE = (0, 77, 200, 255)
+DNET_SAMPLE = (256, 300, 401, 511)
+
+
 def test_full_size_batch_sampled_fits():
-    """The 512-fit mixed batch of the bench (FP32 transforms): sampled digital-net fits' NLL and
-    gradient against the per-frequency oracle."""
+    """The 512-fit mixed batch of the bench, in its precisions (digital nets with FP32 transforms,
+    lattices with FP64 transforms): sampled fits of both halves, NLL and gradient against the
+    per-frequency oracle at the precision's tolerance."""
     import os
     import sys
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import bench
     from paper_2603_16014_gb300.mtgp import Batch
     probs = bench.batch_problems(512)
-    ys = [inputs.synth_y(q, dense.all_points(q.kind, q.gen, q.shift, q.m)) if i in (256, 300, 401, 511) else
+    sample = LATTICE_SAMPLE + DNET_SAMPLE
+    ys = [inputs.synth_y(q, dense.all_points(q.kind, q.gen, q.shift, q.m)) if i in sample else
           np.random.default_rng(i).standard_normal(q.N) for i, q in enumerate(probs)]
-    b = Batch(probs, s=2, precision="fp32")
+    b = Batch(probs, s=2, precision="auto")
+    assert all(b.precision[f] == "fp64" for f in LATTICE_SAMPLE)
+    assert all(b.precision[f] == "fp32" for f in DNET_SAMPLE)
     b.set_y(torch.from_numpy(np.concatenate(ys)))
     th = [bench.default_theta(q) for q in probs]
     b.set_theta(torch.from_numpy(b.pack(th)))
     nll, g = b.nll_grad()
     torch.cuda.synchronize()
     nll, g = nll.cpu().numpy(), g.cpu().numpy()
-    for f in (256, 300, 401, 511):
+    for f in sample:
         q = probs[f]
-        assert q.kind == "dnet"
+        assert q.kind == ("lattice" if f in LATTICE_SAMPLE else "dnet")
         out, ge, gW, gv, gs = spectral.nll_grad_equal(q.kind, q.gen, q.shift, q.m, ys[f], *th[f])
-        assert abs(nll[f] - out["nll"]) <= 1e-5 * abs(out["nll"]), (f, nll[f], out["nll"])
         gref = 0.5 * np.concatenate([ge, np.ravel(gW), gv, [gs]])
         o0, o1 = b.param_offsets[f], b.param_offsets[f + 1]
-        # FP32 transforms of up to 29 columns of 2^16 entries: normwise 1e-3 (the eta entries are sums
-        # over C n terms of FP32-transformed adjoint weights; 1.8e-4 measured at T = 8)
         err = np.abs(g[o0:o1] - gref).max() / np.abs(gref).max()
-        assert err <= 1e-3, (f, err)
+        if q.kind == "lattice":
+            # FP64 mode: 1e-8 relative NLL; gradient normwise 1e-7
+            assert abs(nll[f] - out["nll"]) <= 1e-8 * abs(out["nll"]), (f, nll[f], out["nll"])
+            assert err <= 1e-7, (f, err)
+        else:
+            assert abs(nll[f] - out["nll"]) <= 1e-5 * abs(out["nll"]), (f, nll[f], out["nll"])
+            # FP32 transforms of up to 29 columns of 2^16 entries: normwise 1e-3 (the eta entries are sums
+            # over C n terms of FP32-transformed adjoint weights; 1.8e-4 measured at T = 8)
+            assert err <= 1e-3, (f, err)
     b.close()
 
 

@@ -272,3 +272,33 @@ def test_proposal_pipeline_on_training_fits():
     assert closer.mean() >= 0.75, (closer.mean(), nll0[:4], nll_p[:4], nll_lab[:4])
     net.close()
     b.close()
+
+
+def test_propose_entry_point_equals_composed_calls():
+    """mtgp_propose (features -> MLP forward -> parameter map in one C call) equals the three calls
+    made one by one, for a batch larger than the network's max_batch (chunked forward passes)."""
+    from paper_2603_16014_gb300 import _lib
+    from paper_2603_16014_gb300.mtgp import Batch
+    from paper_2603_16014_gb300.proposal import MLP, propose
+    probs = _fits(12, 20)
+    ys = _ys(probs)
+    b = Batch(probs, s=2, precision="auto")
+    b.set_y(torch.from_numpy(np.concatenate(ys)))
+    net = MLP(max_batch=8)
+    net.set_params(net.init_params(3))
+    net.fit_scaling(b.features())
+    pred = propose(b, net)
+    th_prop = b.get_theta()
+    ref_pred = net.forward(b.features())
+    b.set_theta_proposal(ref_pred)
+    th_ref = b.get_theta()
+    torch.cuda.synchronize()
+    assert torch.equal(pred, ref_pred)
+    assert torch.equal(th_prop, th_ref)
+    # a network of the wrong shape is refused
+    bad = MLP(widths=(258, 64, 36), max_batch=8)
+    with pytest.raises(_lib.MTGPError):
+        propose(b, bad)
+    bad.close()
+    net.close()
+    b.close()

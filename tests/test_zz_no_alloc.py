@@ -41,6 +41,7 @@ def test_static_nll_matches_handle_nll_on_consecutive_calls():
     from paper_2603_16014_gb300 import build
     from paper_2603_16014_gb300.mtgp import MTGP
     build.build()
+    from oracle import spectral
     cases = []
     for p, prec in _problems():
         X = dense.all_points(p.kind, p.gen, p.shift, p.m)
@@ -51,6 +52,12 @@ def test_static_nll_matches_handle_nll_on_consecutive_calls():
         model.sync()
         cases.append((p, prec, y, ref.cpu().numpy(), tau_ref.cpu().numpy()))
         model.close()
+        # the oracle on the same inputs (per-frequency Cholesky of the CPU oracle), so the comparison
+        # does not rest on the handle-based path alone
+        orc = spectral.nll_equal(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2)
+        out, _, status = _static_nll(p, y, prec)
+        assert status == 0
+        assert abs(out[0] - orc["nll"]) <= TOL[prec] * abs(orc["nll"]), (out[0], orc["nll"])
     # two passes over all problems: every call after the first finds the array holding another
     # problem's intermediates
     for _ in range(2):
