@@ -56,6 +56,11 @@ enum { MTGP_FP64 = 0, MTGP_FP32_TRANSFORM = 1 };
 /* OR-ed into mtgp_create's precision: one noise variance per task (xi_t of Sec. 3.1's data model)
  * instead of a shared sigma2; sigma2 and g_sigma2 then hold T values in caller task order. */
 enum { MTGP_NOISE_PER_TASK = 16 };
+/* OR-ed into mtgp_create's precision with MTGP_FP32_TRANSFORM: keep the per-frequency solve of the
+ * equal-size digital-net kernels in FP64.  By default those kernels solve FP32-transform problems in
+ * double-float arithmetic (pairs of FP32 values, about 48 significant bits, on the FP32 pipe; a
+ * frequency whose pivots leave the double-float range is solved in FP64); every other solve is FP64. */
+enum { MTGP_SOLVE_FP64 = 32 };
 
 /* Limits of this build. */
 #define MTGP_MAX_TASKS 8
@@ -387,14 +392,37 @@ int mtgp_mlp_train_step(mtgp_mlp_t* m, int B, const float* x, const float* targe
  * features of mtgp_batch_features, the network's forward pass (in chunks of its max_batch rows) and
  * mtgp_batch_set_theta_proposal on the prediction.  A following mtgp_batch_fit with theta0 = NULL
  * starts the optimiser there.  No counterpart in the paper (it starts each fit from a fixed point).
- *   net   a network mapping 258 features to 37 outputs (mtgp_mlp_create widths 258, ..., 37), with
- *         its parameters and input scaling set; otherwise MTGP_ERR_INVALID_ARG.
- *   pred  device, nfits x 37 FP32, or NULL: receives the prediction (layout of mtgp_batch_targets).
+ *   net     a network mapping 258 features to 37 outputs (mtgp_mlp_create widths 258, ..., 37), with
+ *           its parameters and input scaling set; otherwise MTGP_ERR_INVALID_ARG.
+ *   pred    device, nfits x 37 FP32, or NULL: receives the prediction (layout of mtgp_batch_targets).
+ *   judge   0: every fit takes the prediction.  1: the exact MLE loss judges five candidates per fit and
+ *           each fit keeps the one with the lowest NLL (one batched NLL + gradient evaluation per
+ *           candidate): with c the log parameters set before the call (e.g. the plain optimiser's fixed
+ *           start) and p the prediction's (W linearly), candidate 0 = p, 1 = p with sigma2 x 100,
+ *           2 = (p + c) / 2, 3 = (p + 3 c) / 4, 4 = c.  The judged start is never worse than the
+ *           caller's own start.
+ *   chosen  device, nfits ints, or NULL (judge = 1): the candidate each fit kept.
  * Needs mtgp_batch_set_y first, s = 2 and d <= 12 for every fit (else MTGP_ERR_UNSUPPORTED).  The
- * first call allocates the batch's feature and prediction buffers (synchronously); later calls are
- * asynchronous on `stream`.  The network's buffers are used: order calls on one network on one stream.
+ * first call allocates the batch's feature, prediction and judge buffers (synchronously); later calls
+ * are asynchronous on `stream`.  The network's buffers are used: order calls on one network on one stream.
  */
-int mtgp_propose(mtgp_batch_t* b, mtgp_mlp_t* net, float* pred, cudaStream_t stream);
+int mtgp_propose(mtgp_batch_t* b, mtgp_mlp_t* net, float* pred, int judge, int* chosen, cudaStream_t stream);
+
+/*
+ * mtgp_selftest_arith -- evaluates one of the library's arithmetic building blocks element-wise, for
+ * testing its error bound against an FP64 reference (no counterpart in the paper).  x, y, out: device,
+ * n doubles (y only for ops 3-5).  The double-float operations take their FP64 inputs rounded to
+ * double-float (about 48 significant bits) and return the double-float result as a double.
+ *   op 0  1 / x by the FP64 solvers' reciprocal (hardware approximation + one third-order refinement)
+ *   op 1  x rounded to double-float and back
+ *   op 2  1 / x in double-float (FP32 approximation + one Newton-Raphson step)
+ *   op 3  x * y,  op 4  x + y,  op 5  x - y * y  (double-float)
+ *   op 6  log of the product of x over each group of 32 consecutive elements (the double-float
+ *         log-determinant accumulator and its double-float logarithm, ln m = 2 atanh((m-1)/(m+1))),
+ *         written to the group's first element, 0 elsewhere; n % 32 == 0
+ * Asynchronous on `stream`; MTGP_ERR_INVALID_ARG for an unknown op or missing arrays.
+ */
+int mtgp_selftest_arith(int op, long long n, const double* x, const double* y, double* out, cudaStream_t stream);
 
 /* mtgp_workspace_bytes -- device bytes the handle holds (for capacity planning). */
 long long mtgp_workspace_bytes(const mtgp_t* h);

@@ -21,6 +21,7 @@ ERRORS = {
 LATTICE, DNET = 0, 1
 FP64, FP32_TRANSFORM = 0, 1
 NOISE_PER_TASK = 16
+SOLVE_FP64 = 32
 
 _p = ctypes.c_void_p
 _i = ctypes.c_int
@@ -48,7 +49,8 @@ _SIGS = {
     "mtgp_batch_adam": (_i, [_p, _i, ctypes.c_double, _i, _p, _p]),
     "mtgp_batch_autotune": (_i, [_p, _i, _p, _p]),
     "mtgp_batch_fit": (_i, [_p, _p, _i, ctypes.c_double, _i, _p, _p, _p, _p]),
-    "mtgp_propose": (_i, [_p, _p, _p, _p]),
+    "mtgp_propose": (_i, [_p, _p, _p, _i, _p, _p]),
+    "mtgp_selftest_arith": (_i, [_i, ctypes.c_longlong, _p, _p, _p, _p]),
     "mtgp_gcv": (_i, [_p, _p, _p, _i, _p, _p, _p, _p, _p]),
     "mtgp_set_smoothness": (_i, [_p, _i]),
     "mtgp_set_dsi_weights": (_i, [_p, _p, _p]),

@@ -86,8 +86,10 @@ __device__ __forceinline__ void st(double* p, long long i, Vt<CPLX> v) {
     }
 }
 
-// 1 / x in FP64: hardware reciprocal approximation (rcp.approx.ftz.f64, about 20 correct bits)
-// refined by one third-order step (error cubed); exact division outside binary exponents
+// 1 / x in FP64: the hardware reciprocal approximation r (rcp.approx.ftz.f64, about 20 correct bits)
+// refined by one step of the third-order Householder iteration for 1/x, the geometric series
+// 1/x = r / (1 - e) = r (1 + e + e^2 + ...) with e = 1 - x r truncated after e^2, which leaves a
+// relative error of about e^3 (below FP64 rounding); exact division outside binary exponents
 // [-1000, 1000], tested on the bit pattern so the common path issues no FP64 compare.
 __device__ __forceinline__ double fast_rcp(double x) {
     const unsigned ex = (unsigned)(__double_as_longlong(x) >> 52) & 0x7ffu;
@@ -242,4 +244,132 @@ __device__ __forceinline__ void solve_freq(Vt<CPLX> (&mu)[T][T], const Vt<CPLX> 
         }
     }
     w[0][0] = cfromreal<V>(wdiag * ind0);
+}
+
+// ------------------------------------------------------------------- double-float solve (real data)
+
+#include "df64.cuh"
+
+// Working range of the double-float solve: pivots in [2^-kDfPivMin, 2^kDfPivMax], the quadratic form
+// below 2^100, |alpha_k| and the diagonal of Lambda^-1 below 2^50 keep every product and sum of the
+// recurrences inside the FP32 exponent range with their low parts normal.
+constexpr int kDfPivMin = 50, kDfPivMax = 62;
+
+// The recurrences of solve_freq for real data (digital nets) in double-float arithmetic, for
+// FP32-transform mode, where the spectra mu arrive as FP32 values.  rh: transformed residuals,
+// sR: R (T x T), sig: sigma2, all double-float.  Returns false, with no accumulator touched, when a
+// pivot or an intermediate leaves the working range; the caller then solves the frequency with the
+// FP64 recurrences.  A non-positive pivot sets `bad` (reported as not positive definite) and
+// continues with D = 1, as the FP64 solve does.  acc[1] += quad, acc[2] += tr G, acc[3..] += Gamma;
+// w receives the adjoint weights rounded to FP32.
+template <int T>
+__device__ __forceinline__ bool solve_freq_df(const float (&mu)[T][T], const df (&rh)[T], const df* sR, df sig,
+                                              bool clamp, bool grad, DFLogAcc& lacc, df* acc, float (&w)[T][T],
+                                              int& bad) {
+    float mu0 = mu[0][0];
+    float ind0 = 1.0f;
+    if (clamp && mu0 < 0.0f) {
+        mu0 = 0.0f;
+        ind0 = 0.0f;
+    }
+    df S[T][T], D[T], iD[T], L[T][T];
+#pragma unroll
+    for (int i = 0; i < T; ++i) {
+        D[i] = df_add(df_mulf(sR[i * T + i], mu0), sig);
+#pragma unroll
+        for (int j = 0; j < i; ++j) S[i][j] = df_mulf(sR[j * T + i], mu[j][i]);
+    }
+    int badk = 0;
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+        if (!(D[k].hi > 0.0f) || !isfinite(D[k].hi)) {
+            badk = 1;
+            D[k] = df_of(1.0f);
+        } else if (!df_in_range(D[k], kDfPivMin, kDfPivMax)) {
+            return false;
+        }
+        iD[k] = df_rcp(D[k]);
+#pragma unroll
+        for (int i = k + 1; i < T; ++i) L[i][k] = df_mul(S[i][k], iD[k]);
+#pragma unroll
+        for (int i = k + 1; i < T; ++i) {
+            D[i] = df_fms(D[i], L[i][k], S[i][k]);
+#pragma unroll
+            for (int j = k + 1; j < i; ++j) S[i][j] = df_fms(S[i][j], L[i][k], S[j][k]);
+        }
+    }
+    df u[T];
+    df quad = df_of(0.0f);
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+        df r = rh[k];
+#pragma unroll
+        for (int j = 0; j < k; ++j) r = df_fms(r, L[k][j], u[j]);
+        u[k] = r;
+        quad = df_fma(quad, df_sqr(r), iD[k]);
+    }
+    if (!isfinite(quad.hi) || quad.hi > 0x1p100f) return false;
+    if (!grad) {
+#pragma unroll
+        for (int k = 0; k < T; ++k) lacc.mul(D[k]);
+        acc[1] = df_add(acc[1], quad);
+        bad |= badk;
+        return true;
+    }
+    df al[T];
+    float big = 0.0f;
+#pragma unroll
+    for (int k = T - 1; k >= 0; --k) {
+        df a = df_mul(u[k], iD[k]);
+#pragma unroll
+        for (int i = k + 1; i < T; ++i) a = df_fms(a, L[i][k], al[i]);
+        al[k] = a;
+        big = fmaxf(big, fabsf(a.hi));
+    }
+    // lower triangle of Z = Lambda^-1
+    df Zl[T][T];
+#pragma unroll
+    for (int k = T - 1; k >= 0; --k) {
+#pragma unroll
+        for (int j = T - 1; j > k; --j) {
+            df z = df_of(0.0f);
+#pragma unroll
+            for (int i = k + 1; i < T; ++i) z = df_fms(z, L[i][k], (j >= i) ? Zl[j][i] : Zl[i][j]);
+            Zl[j][k] = z;
+        }
+        df zkk = iD[k];
+#pragma unroll
+        for (int i = k + 1; i < T; ++i) zkk = df_fms(zkk, L[i][k], Zl[i][k]);
+        Zl[k][k] = zkk;
+        big = fmaxf(big, zkk.hi);
+    }
+    // |alpha_k|^2 and Z_kk bound every entry of G = Z - alpha alpha^T (Cauchy-Schwarz on Z)
+    if (!isfinite(big) || big > 0x1p50f) return false;
+#pragma unroll
+    for (int k = 0; k < T; ++k) lacc.mul(D[k]);
+    acc[1] = df_add(acc[1], quad);
+    bad |= badk;
+    df wdiag = df_of(0.0f);
+    int q = 3;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+#pragma unroll
+        for (int uu = t; uu < T; ++uu) {
+            if (uu == t) {
+                const df gd = df_fms(Zl[t][t], al[t], al[t]);
+                acc[2] = df_add(acc[2], gd);
+                acc[q] = df_add(acc[q], df_mulf(gd, mu0));
+                wdiag = df_fma(wdiag, sR[t * T + t], gd);
+            } else {
+                const df g = df_fms(Zl[uu][t], al[uu], al[t]);
+                acc[q] = df_add(acc[q], df_mulf(g, mu[t][uu]));
+                // 2 R_tu g in double-float: its high part is the product rounded to FP32
+                const df r2 = df_make(2.0f * sR[t * T + uu].hi, 2.0f * sR[t * T + uu].lo);
+                w[t][uu] = df_mul(r2, g).hi;
+            }
+            ++q;
+        }
+    }
+    w[0][0] = wdiag.hi * ind0;
+    return true;
 }

@@ -11,205 +11,9 @@
 // Block partial sums are reduced by the last block of B (NLL only) or C, in a fixed order, so the
 // results do not depend on block scheduling.  Columns: c = 0 is the diagonal block's column (shared
 // by all tasks for equal sizes), then one per task pair t < u.
-#include <cstring>
-#include <mutex>
-#include <unordered_map>
-
-#include "butterfly.cuh"
-#include "freq_solve.cuh"
+#include "fused_common.cuh"
 
 namespace {
-
-template <typename S>
-__device__ __forceinline__ S el_re(S x) { return x; }
-template <typename S>
-__device__ __forceinline__ S el_re(cx<S> x) { return x.re; }
-struct FusedParams {
-    int kind, d, T, C, gen_cols, m, a, lgL, grad, clamp, store_alpha, mtw, s, alpha;
-    long long n, N;
-    int colt[MTGP_MAX_COLS], colu[MTGP_MAX_COLS];
-    int colidx[MTGP_TMAX][MTGP_TMAX];
-    int order[MTGP_TMAX], rank[MTGP_TMAX];
-};
-
-__device__ void load_R_f(double* sR, const FusedParams& p, const ThetaPtrs& th) {
-    for (int e = threadIdx.x; e < p.T * p.T; e += blockDim.x) {
-        int t = e / p.T, u = e % p.T;
-        int tc = p.order[t], uc = p.order[u];
-        double r = 0.0;
-        for (int k = 0; k < th.s; ++k) r += th.W[tc * th.s + k] * th.W[uc * th.s + k];
-        if (t == u) r += th.v[tc];
-        sR[e] = r;
-    }
-}
-
-// Column totals of one or two (nrows x ncols) partial arrays (fixed order): warp w sums columns
-// w, w + nw, ... of the two arrays in turn; column q's lane l adds rows l, l + 32, ... (the loads of
-// 8 rows are issued before their additions: one memory round trip per 8), then a shuffle tree.
-__device__ void reduce_columns2(const double* part1, int nrows1, int ncols1, double* out1, const double* part2,
-                                int nrows2, int ncols2, double* out2) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int qq = warp; qq < ncols1 + ncols2; qq += nw) {
-        const bool first = qq < ncols1;
-        const double* part = first ? part1 : part2;
-        const int nrows = first ? nrows1 : nrows2, ncols = first ? ncols1 : ncols2, q = first ? qq : qq - ncols1;
-        double v = 0.0;
-        for (int b0 = lane; b0 < nrows; b0 += 256) {
-            double t[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int b = b0 + 32 * k;
-                t[k] = b < nrows ? part[(long long)b * ncols + q] : 0.0;
-            }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) v += t[k];
-        }
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) (first ? out1 : out2)[q] = v;
-    }
-    __syncthreads();
-}
-
-__device__ void reduce_columns(const double* part, int nrows, int ncols, double* out) {
-    reduce_columns2(part, nrows, ncols, out, nullptr, 0, 0, nullptr);
-}
-
-// last-block election: true in exactly one block, after all blocks have written their partials
-__device__ bool last_block(unsigned* counter, unsigned nblocks) {
-    __shared__ bool am_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned prev = atomicAdd(counter, 1u);
-        am_last = (prev == nblocks - 1);
-    }
-    __syncthreads();
-    if (am_last) __threadfence();
-    return am_last;
-}
-
-struct OutPtrs {
-    double* out;
-    double* tau;
-    double* g_eta;
-    double* g_W;
-    double* g_v;
-    double* g_s2;
-};
-
-// Everything one fit needs on the device: its parameters, theta / output pointers and buffers.
-// Single-fit kernels take it by value; batched kernels read it from a device array.
-struct FitDesc {
-    FusedParams p;
-    ThetaPtrs th;
-    OutPtrs o;
-    const uint32_t* gen;
-    const uint32_t* shift;
-    const void* tw;          // twiddles of the transform precision (lattices)
-    void* spec;              // C x n spectra
-    void* wgt;               // C x n adjoint weights
-    const double* yhat;      // T x n observations, transformed
-    double* alpha;           // T x n Lambda^-1 rhat (posterior)
-    const double* tau;       // T optimal means (sorted)
-    double* partials;        // kernel B partials (nb x NQ), then kernel C partials (na x d)
-    unsigned* counters;      // [0] B (NLL only), [1] C
-    int* status;
-    int na, nb;              // kernel A / C blocks, kernel B blocks
-};
-
-__device__ __forceinline__ int gq(int t, int u, int T) { return t * T - t * (t - 1) / 2 + (u - t); }
-
-// Final outputs from the totals, written by all threads of the block (W and the sorted means are
-// read into shared memory first, every output has its own thread).
-__device__ void write_outputs(const double* tot, const double* etot, const FusedParams& p, const ThetaPtrs& th,
-                              const double* tau_sorted, OutPtrs o) {
-    __shared__ double s_W[MTGP_TMAX * MTGP_TMAX];
-    const int T = p.T, tid = threadIdx.x;
-    const double LOG2PI = 1.8378770664093453;
-    if (p.grad)
-        for (int e = tid; e < T * th.s; e += blockDim.x) s_W[e] = th.W[e];
-    if (tid == 0) {
-        o.out[0] = 0.5 * (tot[0] + tot[1] + (double)p.N * LOG2PI);
-        o.out[1] = tot[1];
-        o.out[2] = tot[0];
-    }
-    if (o.tau && tid < T) o.tau[p.order[tid]] = tau_sorted[tid];
-    if (!p.grad) return;
-    __syncthreads();
-    if (tid == 0) o.g_s2[0] = 0.5 * tot[2];
-    if (tid < p.d) o.g_eta[tid] = 0.5 * etot[tid];
-    for (int e = tid; e < T * th.s; e += blockDim.x) {
-        const int tc = e / th.s, k = e - tc * th.s;
-        const int t = p.rank[tc];
-        double g = 0.0;
-        for (int uc = 0; uc < T; ++uc) {
-            const int u = p.rank[uc];
-            const double G = (t <= u) ? tot[3 + gq(t, u, T)] : tot[3 + gq(u, t, T)];
-            g += G * s_W[uc * th.s + k];
-        }
-        o.g_W[e] = g;
-    }
-    if (tid < T) o.g_v[tid] = 0.5 * tot[3 + gq(p.rank[tid], p.rank[tid], T)];
-}
-
-// ---------------------------------------------------------------------------------- kernel A
-
-// design-point words of the chunk [base, base + 2^a): z(base + lo) = z(base) (+) z(lo) (lattice: +,
-// digital net: XOR; both follow from the linearity in the index bits used in Sec. 3.3)
-template <int DMAX>
-__device__ __forceinline__ void chunk_point(int kind, int d, uint32_t lo, const uint32_t* s_zhi, const uint32_t* s_gen,
-                                            int gen_cols, uint32_t (&z)[DMAX]) {
-#pragma unroll
-    for (int j = 0; j < DMAX; ++j) {
-        if (j < d) {
-            uint32_t zl = point_word(kind, lo, j, s_gen, gen_cols);
-            z[j] = (kind == MTGP_LATTICE) ? s_zhi[j] + zl : (s_zhi[j] ^ zl);
-        }
-    }
-}
-
-// chunk points as a table: s_z[j * 2^a + lo] = coordinate j of point base + lo (all threads call)
-constexpr int kZTab = 2048;
-__device__ __forceinline__ void chunk_table(int kind, int d, int a, const uint32_t* s_zhi, const uint32_t* s_gen,
-                                            int gen_cols, uint32_t* s_z) {
-    const int HA = 1 << a;
-    for (int e = threadIdx.x; e < HA * d; e += blockDim.x) {
-        const int j = e >> a, lo = e & (HA - 1);
-        const uint32_t zl = point_word(kind, (uint32_t)lo, j, s_gen, gen_cols);
-        s_z[e] = (kind == MTGP_LATTICE) ? s_zhi[j] + zl : (s_zhi[j] ^ zl);
-    }
-}
-
-__device__ __forceinline__ void load_design_smem(const FusedParams& p, const uint32_t* gen, const uint32_t* shift,
-                                                 const double* eta, long long base, uint32_t* s_gen, uint32_t* s_sh,
-                                                 uint32_t* s_zhi) {
-    const int d = p.d;
-    const int ng = (p.kind == MTGP_LATTICE) ? d : d * p.gen_cols;
-    for (int e = threadIdx.x; e < ng; e += blockDim.x) s_gen[e] = gen[e];
-    for (int e = threadIdx.x; e < p.T * d; e += blockDim.x) s_sh[e] = shift[e];
-    __syncthreads();
-    if (threadIdx.x < d) s_zhi[threadIdx.x] = point_word(p.kind, (uint32_t)base, threadIdx.x, s_gen, p.gen_cols);
-}
-
-// Programmatic dependent launch.  The wait returns once the grids this one depends on have finished
-// and their writes are visible (at once when the launch did not allow early start); the trigger lets
-// the next grid in the stream begin its independent prologue.  A, B and C each put the work that
-// reads only handle constants (design words, task covariance, observations) before the wait.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-// parameters that are non-finite or negative (eta, v, sigma2) flag ST_NUMERIC; run by block 0 of A
-__device__ __forceinline__ void check_theta_block(const ThetaPtrs& th, int d, int T, int* status) {
-    int bad = 0;
-    for (int j = threadIdx.x; j < d; j += blockDim.x)
-        if (!isfinite(th.eta[j]) || th.eta[j] < 0.0) bad = 1;
-    for (int e = threadIdx.x; e < T * th.s; e += blockDim.x)
-        if (!isfinite(th.W[e])) bad = 1;
-    for (int t = threadIdx.x; t < T; t += blockDim.x)
-        if (!isfinite(th.v[t]) || th.v[t] < 0.0) bad = 1;
-    if (threadIdx.x == 0 && (!isfinite(th.sigma2[0]) || th.sigma2[0] < 0.0)) bad = 1;
-    if (bad) set_status(status, ST_NUMERIC);
-}
 
 template <typename S, bool CPLX, int DMAX>
 __device__ __forceinline__ void fused_a_body(const FitDesc& f, int blk) {
@@ -580,41 +384,36 @@ __global__ void __launch_bounds__(512) k_batch_c(const FitDesc* fits, const int2
 
 // ---------------------------------------------------------------------------------- host side
 
-namespace {
-
-size_t elem_size_of(bool fp32, bool cplx) { return (fp32 ? 4 : 8) * (cplx ? 2 : 1); }
-
-// Raise a kernel's dynamic shared-memory limit to `bytes` (the default limit counts static shared
-// memory too, so any dynamic size may need it); remembered per kernel so each value is set once.
-std::mutex g_smem_mu;
-std::unordered_map<const void*, size_t> g_smem_set;
-
-template <typename F>
-void set_smem(F* fn, size_t bytes) {
-    if (bytes == 0) return;
-    std::lock_guard<std::mutex> lk(g_smem_mu);
-    size_t& cur = g_smem_set[reinterpret_cast<const void*>(fn)];
-    if (bytes > cur) {
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        cur = bytes;
-    }
-}
-
-}  // namespace
+bool fused_plan_cap(int m, int ncols, int d, bool fp32, bool cplx, int a_pref, size_t cap, int* a_out, int* lgL_out);
 
 // split n = 2^m into a low part 2^a (kernels A, C) and a high part 2^(m-a) (kernel B); a_pref >= 0
 // asks for a specific split (the autotuner), -1 for the default (B tiles of 2^8 frequencies)
-bool fused_plan(int m, int ncols, bool fp32, bool cplx, int a_pref, int* a_out, int* lgL_out) {
+// Tiles are kept within 96 KB of shared memory where a split allows it (two blocks per SM), else within
+// 200 KB (one block per SM; e.g. FP64 lattice spectra of 8 tasks).
+bool fused_plan(int m, int ncols, int d, bool fp32, bool cplx, int a_pref, int* a_out, int* lgL_out) {
+    if (fused_plan_cap(m, ncols, d, fp32, cplx, a_pref, 96 * 1024, a_out, lgL_out)) return true;
+    return fused_plan_cap(m, ncols, d, fp32, cplx, a_pref, 200 * 1024, a_out, lgL_out);
+}
+
+bool fused_plan_cap(int m, int ncols, int d, bool fp32, bool cplx, int a_pref, size_t cap, int* a_out, int* lgL_out) {
     if (m < 4) return false;
     const size_t es = elem_size_of(fp32, cplx);
-    const size_t cap = 96 * 1024;
     int a;
     if (a_pref >= 0) {
         a = a_pref;
+    } else if (fused_rt_ok(cplx, fp32, d, m, m - 8 < 5 ? 5 : (m - 8 > 9 ? 9 : m - 8))) {
+        // FP32 real spectra: both halves in the register-tile kernels' range (B tiles of 2^8
+        // frequencies where possible)
+        a = m - 8 < 5 ? 5 : (m - 8 > 9 ? 9 : m - 8);
     } else {
         a = m - 8;
         if (a < m / 2) a = m / 2;
         while (a > 1 && (size_t)ncols * ((size_t)1 << a) * es > cap) --a;
+    }
+    if (fused_rt_ok(cplx, fp32, d, m, a)) {
+        *a_out = a;
+        *lgL_out = 0;
+        return true;
     }
     if (a < 1 || a > m - 1) return false;
     if ((size_t)ncols * ((size_t)1 << a) * es > cap) return false;
@@ -628,7 +427,7 @@ namespace {
 
 bool plan(const Handle* h, int* a_out, int* lgL_out) {
     if (!h->equal) return false;
-    return fused_plan(h->m[0], h->ncols, h->fp32, h->cplx, -1, a_out, lgL_out);
+    return fused_plan(h->m[0], h->ncols, h->d, h->fp32, h->cplx, -1, a_out, lgL_out);
 }
 
 FusedParams make_params(const Handle* h, ThetaPtrs th, bool grad, bool store_alpha, int a, int lgL) {
@@ -674,6 +473,7 @@ FitDesc make_desc(const Handle* h, ThetaPtrs th, OutPtrs o, bool grad, bool stor
     f.spec = h->spec;
     f.wgt = h->wgt;
     f.yhat = h->yhat;
+    f.yhat_df = reinterpret_cast<const float2*>(h->yhat_df);
     f.alpha = h->alpha;
     f.tau = h->tau;
     f.partials = h->partials;
@@ -697,22 +497,6 @@ size_t smem_b(int T, int C, int lgH, size_t es) {
 int threads_ac(int a, int d) {
     const int t = ((1 << a) * d <= kZTab) ? (2 << a) : (1 << a);
     return t < 512 ? (t < 64 ? 64 : t) : 512;
-}
-
-// a single-fit launch that may start while the previous kernel in the stream finishes
-template <typename... KArgs>
-void launch_pdl(void (*kernel)(KArgs...), int grid, int threads, size_t smem, cudaStream_t st, const FitDesc& f) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, f);
 }
 
 template <typename S, bool CPLX, int DMAX>
@@ -775,10 +559,21 @@ void phase_b(int T, const FitDesc* single, const FitDesc* fits, const int2* item
 
 }  // namespace
 
+int fused_variant(bool fp32, bool cplx, bool solve_df, int d, int m, int a, bool store_alpha) {
+    if (store_alpha || !fused_rt_ok(cplx, fp32, d, m, a)) return FUSED_GENERIC;
+    return (fp32 && solve_df) ? FUSED_RT_DF : FUSED_RT;
+}
+
 // one phase (0 = A, 1 = B, 2 = C) for one class; single != nullptr launches one fit with a grid of
 // its own blocks, otherwise a persistent grid over `nitems` batch items
-void fused_phase(int phase, bool fp32, bool cplx, int T, int dmax, const void* single_v, const void* fits_v,
-                 const int2* items, int nitems, int grid, int threads_acq, size_t smem, cudaStream_t st) {
+void fused_phase(int phase, int variant, bool fp32, bool cplx, int T, int dmax, const void* single_v,
+                 const void* fits_v, const int2* items, int nitems, int grid, int threads_acq, size_t smem,
+                 cudaStream_t st) {
+    if (variant != FUSED_GENERIC) {
+        fused_rt_phase(phase, variant == FUSED_RT_DF, T, dmax, single_v, fits_v, items, nitems, grid, threads_acq, smem,
+                       st);
+        return;
+    }
     const FitDesc* single = static_cast<const FitDesc*>(single_v);
     const FitDesc* fits = static_cast<const FitDesc*>(fits_v);
     if (phase == 1) {
@@ -812,7 +607,10 @@ void fused_make_desc(const Handle* h, ThetaPtrs th, double* out, double* tau, do
     std::memcpy(desc, &f, sizeof(FitDesc));
 }
 
-int fused_threads(int phase, int a, int d) { return phase == 1 ? kBThreads : threads_ac(a, d); }
+int fused_threads(int phase, int variant, int a, int d, int C, int m) {
+    if (variant != FUSED_GENERIC) return fused_rt_threads(phase, C, m, a);
+    return phase == 1 ? kBThreads : threads_ac(a, d);
+}
 
 namespace {
 template <typename F>
@@ -851,7 +649,8 @@ int occ_b(int T, size_t smem) {
 }
 }  // namespace
 
-int fused_resident_blocks(int phase, bool fp32, bool cplx, int T, int dmax, int threads, size_t smem) {
+int fused_resident_blocks(int phase, int variant, bool fp32, bool cplx, int T, int dmax, int threads, size_t smem) {
+    if (variant != FUSED_GENERIC) return fused_rt_resident_blocks(phase, variant == FUSED_RT_DF, T, dmax, threads, smem);
     if (phase == 1) {
         if (fp32) return cplx ? occ_b<true, float>(T, smem) : occ_b<false, float>(T, smem);
         return cplx ? occ_b<true, double>(T, smem) : occ_b<false, double>(T, smem);
@@ -860,7 +659,8 @@ int fused_resident_blocks(int phase, bool fp32, bool cplx, int T, int dmax, int 
     if (fp32) return cplx ? occ_ac<float, true>(is_c, dmax, threads, smem) : occ_ac<float, false>(is_c, dmax, threads, smem);
     return cplx ? occ_ac<double, true>(is_c, dmax, threads, smem) : occ_ac<double, false>(is_c, dmax, threads, smem);
 }
-size_t fused_smem(int phase, int T, int C, int m, int a, bool fp32, bool cplx) {
+size_t fused_smem(int phase, int variant, int T, int C, int m, int a, bool fp32, bool cplx) {
+    if (variant != FUSED_GENERIC) return fused_rt_smem(phase, T, C, m, a);
     const size_t es = elem_size_of(fp32, cplx);
     return phase == 1 ? smem_b(T, C, m - a, es) : smem_ac(C, a, es);
 }
@@ -886,18 +686,13 @@ void launch_fused(const Handle* h, ThetaPtrs th, bool grad, bool store_alpha, do
     plan(h, &a, &lgL);
     OutPtrs o{out, tau, g_eta, g_W, g_v, g_s2};
     const FitDesc f = make_desc(h, th, o, grad, store_alpha, a, lgL);
-    const int C = h->ncols;
-    mtgp_prof_begin(h, "fused_a", st);
-    fused_phase(0, h->fp32, h->cplx, h->T, h->d, &f, nullptr, nullptr, 0, f.na, threads_ac(a, h->d),
-                fused_smem(0, h->T, C, f.p.m, a, h->fp32, h->cplx), st);
-    mtgp_prof_end(h, st);
-    mtgp_prof_begin(h, "fused_b", st);
-    fused_phase(1, h->fp32, h->cplx, h->T, h->d, &f, nullptr, nullptr, 0, f.nb, kBThreads,
-                fused_smem(1, h->T, C, f.p.m, a, h->fp32, h->cplx), st);
-    mtgp_prof_end(h, st);
-    if (!grad) return;
-    mtgp_prof_begin(h, "fused_c", st);
-    fused_phase(2, h->fp32, h->cplx, h->T, h->d, &f, nullptr, nullptr, 0, f.na, threads_ac(a, h->d),
-                fused_smem(2, h->T, C, f.p.m, a, h->fp32, h->cplx), st);
-    mtgp_prof_end(h, st);
+    const int C = h->ncols, m = f.p.m;
+    const int var = fused_variant(h->fp32, h->cplx, h->solve_df, h->d, m, a, store_alpha);
+    for (int ph = 0; ph < (grad ? 3 : 2); ++ph) {
+        static const char* names[3] = {"fused_a", "fused_b", "fused_c"};
+        mtgp_prof_begin(h, names[ph], st);
+        fused_phase(ph, var, h->fp32, h->cplx, h->T, h->d, &f, nullptr, nullptr, 0, ph == 1 ? f.nb : f.na,
+                    fused_threads(ph, var, a, h->d, C, m), fused_smem(ph, var, h->T, C, m, a, h->fp32, h->cplx), st);
+        mtgp_prof_end(h, st);
+    }
 }

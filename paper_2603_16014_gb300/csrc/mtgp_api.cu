@@ -194,7 +194,7 @@ cudaError_t dalloc(Handle* h, T** p, size_t count) {
 }
 
 void free_all(Handle* h) {
-    void* ptrs[] = {h->gen, h->shift, h->cols_dev, h->yoffs_dev, h->twid, h->twid32, h->yhat, h->spec,
+    void* ptrs[] = {h->gen, h->shift, h->cols_dev, h->yoffs_dev, h->twid, h->twid32, h->yhat, h->yhat_df, h->spec,
                     h->wgt, h->S, h->Z, h->r, h->alpha, h->tau, h->partials, h->status, h->out_tmp, h->counters,
                     h->gcv_h, h->pi_buf, h->bmix, h->hio, h->lead_offs_dev, h->pairs_dev};
     for (void* p : ptrs)
@@ -305,9 +305,11 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
     if (T < 1 || T > MTGP_MAX_TASKS) return fail(MTGP_ERR_INVALID_ARG, "T out of range [1, MTGP_MAX_TASKS]");
     if (!m || !gen || !shift) return fail(MTGP_ERR_INVALID_ARG, "m, gen and shift must be host arrays");
     const bool noise_pt = (precision & MTGP_NOISE_PER_TASK) != 0;
-    precision &= ~MTGP_NOISE_PER_TASK;
+    const bool solve_fp64 = (precision & MTGP_SOLVE_FP64) != 0;
+    precision &= ~(MTGP_NOISE_PER_TASK | MTGP_SOLVE_FP64);
     if (precision != MTGP_FP64 && precision != MTGP_FP32_TRANSFORM)
-        return fail(MTGP_ERR_INVALID_ARG, "precision must be MTGP_FP64 or MTGP_FP32_TRANSFORM (optionally | MTGP_NOISE_PER_TASK)");
+        return fail(MTGP_ERR_INVALID_ARG,
+                    "precision must be MTGP_FP64 or MTGP_FP32_TRANSFORM (optionally | MTGP_NOISE_PER_TASK | MTGP_SOLVE_FP64)");
     int mmax = 0;
     for (int t = 0; t < T; ++t) {
         if (m[t] < 0 || m[t] > MTGP_MAX_M) return fail(MTGP_ERR_INVALID_ARG, "m[t] out of range [0, MTGP_MAX_M]");
@@ -326,6 +328,7 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
     h->T = T;
     h->prec = precision;
     h->fp32 = precision == MTGP_FP32_TRANSFORM;
+    h->solve_df = h->fp32 && !solve_fp64;
     h->cplx = kind == MTGP_LATTICE;
     h->gen_cols = kind == MTGP_DNET ? gen_cols : 1;
     h->mmax = mmax;
@@ -455,6 +458,7 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
     }
     AL(h->r, (size_t)h->N * vs);
     AL(h->alpha, (size_t)h->N * vs);
+    if (h->equal && h->fp32 && !h->cplx) AL(h->yhat_df, (size_t)h->N * 2);
     AL(h->tau, (size_t)MTGP_TMAX);
     {
         const int NQ = solve_nq(h);
@@ -574,6 +578,7 @@ int mtgp_set_y(mtgp_t* hs, const double* y, cudaStream_t st) {
     k_check_y<<<blocks, 256, 0, st>>>(y, h->N, h->status);
     launch_y_load(h, y, st);
     if (h->equal) k_tau_equal<<<1, 32, 0, st>>>(h->yhat, h->tau, h->T, h->n[0], h->cplx ? 1 : 0);
+    if (h->yhat_df) launch_yhat_df(h->yhat, h->yhat_df, h->N, st);
     CK(cudaGetLastError());
     h->y_set = true;
     return MTGP_OK;

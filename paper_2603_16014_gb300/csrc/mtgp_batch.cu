@@ -25,6 +25,7 @@ constexpr int kSide = 16;
 
 struct Cls {
     int phase;
+    int variant;      // FUSED_GENERIC / FUSED_RT / FUSED_RT_DF
     bool fp32;        // transform precision of the class's fits
     bool cplx;
     int key;          // T (phase B) or dimension bucket (phases A, C)
@@ -98,6 +99,12 @@ struct mtgp_batch_s {
     void* fdesc = nullptr;  // proposal descriptors (device), built on first use
     float* pfeat = nullptr;  // mtgp_propose: features (nfits x 258) and prediction (nfits x 37), on first use
     float* ppred = nullptr;
+    double* jcur = nullptr;   // mtgp_propose with the exact-NLL judge: log parameters before the call,
+    double* jcur_nat = nullptr;  // the same natural parameters (restored exactly by the last candidate),
+    double* jpred = nullptr;  // log parameters of the prediction, best candidate NLL and index per fit, sigma2 marks
+    double* jbest = nullptr;
+    int* jk = nullptr;
+    unsigned char* is_s2 = nullptr;
 };
 
 namespace {
@@ -166,18 +173,19 @@ int build_plan(mtgp_batch_s* b) {
         return hx.n[0] * hx.T * hx.T > hy.n[0] * hy.T * hy.T;
     });
     for (int ph = 0; ph < 3; ++ph) {
-        // class key: (transform precision, complex spectra, T or dimension bucket)
-        std::map<std::tuple<int, int, int>, std::vector<int2>> items;
-        std::map<std::tuple<int, int, int>, std::pair<size_t, int>> res;  // smem, threads
+        // class key: (kernel family, transform precision, complex spectra, T or dimension bucket)
+        std::map<std::tuple<int, int, int, int>, std::vector<int2>> items;
+        std::map<std::tuple<int, int, int, int>, std::pair<size_t, int>> res;  // smem, threads
         for (int f : order) {
             const Handle& h = b->fits[f]->h;
             const int m = h.m[0], a = b->a[f];
+            const int var = fused_variant(h.fp32, h.cplx, h.solve_df, h.d, m, a, false);
             const int key = ph == 1 ? h.T : dbucket(h.d);
-            auto k = std::make_tuple(h.fp32 ? 1 : 0, h.cplx ? 1 : 0, key);
+            auto k = std::make_tuple(var, h.fp32 ? 1 : 0, h.cplx ? 1 : 0, key);
             const int nblk = ph == 1 ? (1 << a) : (1 << (m - a));
             for (int j = 0; j < nblk; ++j) items[k].push_back(make_int2(f, j));
-            const size_t sm = fused_smem(ph, h.T, h.ncols, m, a, h.fp32, h.cplx);
-            const int th = fused_threads(ph, a, h.d);
+            const size_t sm = fused_smem(ph, var, h.T, h.ncols, m, a, h.fp32, h.cplx);
+            const int th = fused_threads(ph, var, a, h.d, h.ncols, m);
             auto& r = res[k];
             r.first = std::max(r.first, sm);
             r.second = std::max(r.second, th);
@@ -185,14 +193,15 @@ int build_plan(mtgp_batch_s* b) {
         for (auto& kv : items) {
             Cls c;
             c.phase = ph;
-            c.fp32 = std::get<0>(kv.first) != 0;
-            c.cplx = std::get<1>(kv.first) != 0;
-            c.key = std::get<2>(kv.first);
+            c.variant = std::get<0>(kv.first);
+            c.fp32 = std::get<1>(kv.first) != 0;
+            c.cplx = std::get<2>(kv.first) != 0;
+            c.key = std::get<3>(kv.first);
             c.nitems = (int)kv.second.size();
             c.smem = res[kv.first].first;
             c.threads = res[kv.first].second;
             const int T = ph == 1 ? c.key : 1;
-            const int per_sm = fused_resident_blocks(ph, c.fp32, c.cplx, T, c.key, c.threads, c.smem);
+            const int per_sm = fused_resident_blocks(ph, c.variant, c.fp32, c.cplx, T, c.key, c.threads, c.smem);
             c.grid = std::min(c.nitems, per_sm * b->nsm);
             if (cudaMalloc(&c.items, sizeof(int2) * c.nitems) != cudaSuccess)
                 return bfail(MTGP_ERR_CUDA, "batch item table allocation failed");
@@ -369,6 +378,61 @@ __global__ void k_batch_propose(const FeatDesc* __restrict__ fds, const float* _
     }
 }
 
+// Starting-point candidates judged by the exact NLL: candidate k blends the log parameters before the
+// call (c) and of the prediction (p) as lam p + (1 - lam) c (W linearly), with log sigma2 raised by
+// dls2 (guards against an under-predicted noise level, whose quadratic form grows like 1 / sigma2).
+// The last candidate is the starting point the caller set: the judged start is never worse than it.
+constexpr int kJudgeCand = 5;
+__device__ __forceinline__ void judge_candidate(int k, double& lam, double& dls2) {
+    const double L[kJudgeCand] = {1.0, 1.0, 0.5, 0.25, 0.0};
+    const double S[kJudgeCand] = {0.0, 4.605170185988092, 0.0, 0.0, 0.0};  // ln 100
+    lam = L[k];
+    dls2 = S[k];
+}
+
+__global__ void k_judge_set(int k, const int* __restrict__ kfit, const int* __restrict__ pinfo,
+                            const unsigned char* __restrict__ is_s2, long long np, const double* __restrict__ cur,
+                            const double* __restrict__ cur_nat, const double* __restrict__ pred, double* __restrict__ lg,
+                            double* __restrict__ nv, double* __restrict__ m1, double* __restrict__ m2) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < np; q += (long long)gridDim.x * blockDim.x) {
+        int kk = k;
+        if (kfit) {
+            kk = kfit[pinfo[2 * q]];
+            if (kk < 0) kk = kJudgeCand - 1;  // no finite candidate: the caller's start
+        }
+        double lam, dls2;
+        judge_candidate(kk, lam, dls2);
+        if (kk == kJudgeCand - 1) {
+            // the caller's own start, exactly
+            lg[q] = cur[q];
+            nv[q] = cur_nat[q];
+        } else {
+            double x = lam * pred[q] + (1.0 - lam) * cur[q];
+            if (is_s2[q]) x += dls2;
+            const bool islog = pinfo[2 * q + 1] != 0;
+            lg[q] = x;
+            nv[q] = islog ? exp(x) : x;
+        }
+        m1[q] = 0.0;
+        m2[q] = 0.0;
+    }
+}
+
+__global__ void k_judge_keep(int k, int nfits, const double* __restrict__ out, double* __restrict__ best,
+                             int* __restrict__ kbest) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfits) return;
+    const double v = out[3 * f];
+    if (k == 0) {
+        best[f] = INFINITY;
+        kbest[f] = -1;
+    }
+    if (isfinite(v) && v < best[f]) {
+        best[f] = v;
+        kbest[f] = k;
+    }
+}
+
 int ensure_fdesc(mtgp_batch_s* b) {
     if (b->fdesc) return MTGP_OK;
     if (b->s != 2) return bfail(MTGP_ERR_UNSUPPORTED, "the proposal is defined for s = 2");
@@ -398,8 +462,9 @@ void check_launch(const Cls& c, int T) {
     if (!on) return;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
-        std::fprintf(stderr, "batch launch failed: %s phase=%d fp32=%d cplx=%d key=%d T=%d grid=%d threads=%d smem=%zu items=%d\n",
-                     cudaGetErrorString(e), c.phase, (int)c.fp32, (int)c.cplx, c.key, T, c.grid, c.threads, c.smem, c.nitems);
+        std::fprintf(stderr, "batch launch failed: %s phase=%d variant=%d fp32=%d cplx=%d key=%d T=%d grid=%d threads=%d smem=%zu items=%d\n",
+                     cudaGetErrorString(e), c.phase, c.variant, (int)c.fp32, (int)c.cplx, c.key, T, c.grid, c.threads, c.smem,
+                     c.nitems);
 }
 
 // the three phases of one batched NLL + gradient evaluation on stream st (classes forked to side streams)
@@ -409,7 +474,7 @@ void launch_eval(mtgp_batch_s* b, cudaStream_t st) {
         if (cl.size() == 1) {
             const Cls& c = cl[0];
             const int T = ph == 1 ? c.key : 1;
-            fused_phase(ph, c.fp32, c.cplx, T, c.key, nullptr, b->descs, c.items, c.nitems, c.grid, c.threads, c.smem, st);
+            fused_phase(ph, c.variant, c.fp32, c.cplx, T, c.key, nullptr, b->descs, c.items, c.nitems, c.grid, c.threads, c.smem, st);
             check_launch(c, T);
             continue;
         }
@@ -419,7 +484,7 @@ void launch_eval(mtgp_batch_s* b, cudaStream_t st) {
             cudaStream_t ss = b->side[i % kSide];
             cudaStreamWaitEvent(ss, b->evfork, 0);
             const int T = ph == 1 ? c.key : 1;
-            fused_phase(ph, c.fp32, c.cplx, T, c.key, nullptr, b->descs, c.items, c.nitems, c.grid, c.threads, c.smem, ss);
+            fused_phase(ph, c.variant, c.fp32, c.cplx, T, c.key, nullptr, b->descs, c.items, c.nitems, c.grid, c.threads, c.smem, ss);
             check_launch(c, T);
         }
         const int used = (int)std::min<size_t>(cl.size(), kSide);
@@ -455,8 +520,9 @@ int mtgp_batch_create(mtgp_batch_t** out, int nfits, const int* kind, const int*
     for (int f = 0; f < nfits; ++f) {
         if (precision[f] & MTGP_NOISE_PER_TASK)
             return bfail(MTGP_ERR_UNSUPPORTED, "batched fits take one noise variance per fit");
-        if (precision[f] != MTGP_FP64 && precision[f] != MTGP_FP32_TRANSFORM)
-            return bfail(MTGP_ERR_INVALID_ARG, "precision[f] must be MTGP_FP64 or MTGP_FP32_TRANSFORM");
+        const int pr = precision[f] & ~MTGP_SOLVE_FP64;
+        if (pr != MTGP_FP64 && pr != MTGP_FP32_TRANSFORM)
+            return bfail(MTGP_ERR_INVALID_ARG, "precision[f] must be MTGP_FP64 or MTGP_FP32_TRANSFORM (optionally | MTGP_SOLVE_FP64)");
         if (T[f] < s) return bfail(MTGP_ERR_INVALID_ARG, "every fit needs T >= s");
     }
     auto* b = new mtgp_batch_s();
@@ -479,7 +545,7 @@ int mtgp_batch_create(mtgp_batch_t** out, int nfits, const int* kind, const int*
         }
         b->fits.push_back(hf);
         int a = 0, lgL = 0;
-        if (!fused_plan(m[f], hf->h.ncols, hf->h.fp32, hf->h.cplx, -1, &a, &lgL)) {
+        if (!fused_plan(m[f], hf->h.ncols, hf->h.d, hf->h.fp32, hf->h.cplx, -1, &a, &lgL)) {
             mtgp_batch_destroy(b);
             return bfail(MTGP_ERR_UNSUPPORTED, "a fit's size is not handled by the fused kernels (m >= 4, tiles <= 96 KB)");
         }
@@ -537,7 +603,8 @@ int mtgp_batch_destroy(mtgp_batch_t* b) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     for (auto* f : b->fits) mtgp_destroy(f);
     void* ptrs[] = {b->th_log, b->th_nat, b->g_nat, b->m1, b->m2, b->out, b->tau, b->partials, b->counters, b->pinfo,
-                    b->tstep, b->descs, b->fdesc, b->pfeat, b->ppred};
+                    b->tstep, b->descs, b->fdesc, b->pfeat, b->ppred, b->jcur, b->jcur_nat, b->jpred, b->jbest, b->jk,
+                    b->is_s2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < kSide; ++i) {
@@ -672,7 +739,7 @@ int mtgp_batch_fit(mtgp_batch_t* b, const double* theta0, int steps, double lr, 
     return MTGP_OK;
 }
 
-int mtgp_propose(mtgp_batch_t* b, mtgp_mlp_t* net, float* pred, cudaStream_t st) {
+int mtgp_propose(mtgp_batch_t* b, mtgp_mlp_t* net, float* pred, int judge, int* chosen, cudaStream_t st) {
     if (!b || !net) return bfail(MTGP_ERR_INVALID_ARG, "NULL argument");
     int in_w = 0, out_w = 0, max_b = 0;
     mlp_shape(net, &in_w, &out_w, &max_b);
@@ -687,7 +754,23 @@ int mtgp_propose(mtgp_batch_t* b, mtgp_mlp_t* net, float* pred, cudaStream_t st)
             cudaMalloc(&b->ppred, sizeof(float) * kOut * (size_t)b->nfits) != cudaSuccess)
             return bfail(MTGP_ERR_CUDA, "proposal buffer allocation failed");
     }
+    if (judge && !b->jcur) {
+        std::vector<unsigned char> s2((size_t)b->np, 0);
+        for (int f = 0; f < b->nfits; ++f) s2[(size_t)b->poff[f + 1] - 1] = 1;
+        if (cudaMalloc(&b->jcur, sizeof(double) * b->np) != cudaSuccess ||
+            cudaMalloc(&b->jcur_nat, sizeof(double) * b->np) != cudaSuccess ||
+            cudaMalloc(&b->jpred, sizeof(double) * b->np) != cudaSuccess ||
+            cudaMalloc(&b->jbest, sizeof(double) * b->nfits) != cudaSuccess ||
+            cudaMalloc(&b->jk, sizeof(int) * b->nfits) != cudaSuccess ||
+            cudaMalloc(&b->is_s2, (size_t)b->np) != cudaSuccess)
+            return bfail(MTGP_ERR_CUDA, "proposal judge buffer allocation failed");
+        cudaMemcpy(b->is_s2, s2.data(), (size_t)b->np, cudaMemcpyHostToDevice);
+    }
     float* y = pred ? pred : b->ppred;
+    if (judge) {
+        cudaMemcpyAsync(b->jcur, b->th_log, sizeof(double) * b->np, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(b->jcur_nat, b->th_nat, sizeof(double) * b->np, cudaMemcpyDeviceToDevice, st);
+    }
     k_batch_features<<<b->nfits, 256, 0, st>>>(static_cast<const FeatDesc*>(b->fdesc), b->pfeat);
     rc = launch_status("mtgp_propose (features)");
     if (rc) return rc;
@@ -696,7 +779,22 @@ int mtgp_propose(mtgp_batch_t* b, mtgp_mlp_t* net, float* pred, cudaStream_t st)
         rc = mtgp_mlp_forward(net, rows, b->pfeat + (size_t)r0 * kFeat, y + (size_t)r0 * kOut, st);
         if (rc) return rc;
     }
-    return mtgp_batch_set_theta_proposal(b, y, st);
+    rc = mtgp_batch_set_theta_proposal(b, y, st);
+    if (rc || !judge) return rc;
+    // the exact NLL judges the candidates; every fit keeps its best
+    cudaMemcpyAsync(b->jpred, b->th_log, sizeof(double) * b->np, cudaMemcpyDeviceToDevice, st);
+    const int blocks = (int)std::min<long long>((b->np + 255) / 256, 4096);
+    for (int k = 0; k < kJudgeCand; ++k) {
+        k_judge_set<<<blocks, 256, 0, st>>>(k, nullptr, b->pinfo, b->is_s2, b->np, b->jcur, b->jcur_nat, b->jpred,
+                                            b->th_log, b->th_nat, b->m1, b->m2);
+        launch_eval(b, st);
+        k_judge_keep<<<(b->nfits + 127) / 128, 128, 0, st>>>(k, b->nfits, b->out, b->jbest, b->jk);
+    }
+    k_judge_set<<<blocks, 256, 0, st>>>(0, b->jk, b->pinfo, b->is_s2, b->np, b->jcur, b->jcur_nat, b->jpred,
+                                        b->th_log, b->th_nat, b->m1, b->m2);
+    cudaMemsetAsync(b->tstep, 0, sizeof(int), st);
+    if (chosen) cudaMemcpyAsync(chosen, b->jk, sizeof(int) * b->nfits, cudaMemcpyDeviceToDevice, st);
+    return launch_status("mtgp_propose (judge)");
 }
 
 int mtgp_batch_autotune(mtgp_batch_t* b, int reps, int* chosen, cudaStream_t st) {
@@ -725,7 +823,7 @@ int mtgp_batch_autotune(mtgp_batch_t* b, int reps, int* chosen, cudaStream_t st)
         int best_a = b->a[f];
         for (int a = 2; a <= m - 2; ++a) {
             int aa, lgL;
-            if (!fused_plan(m, h.ncols, h.fp32, h.cplx, a, &aa, &lgL)) continue;
+            if (!fused_plan(m, h.ncols, h.d, h.fp32, h.cplx, a, &aa, &lgL)) continue;
             const int NQ = 3 + h.T * (h.T + 1) / 2;
             const long long need = ((long long)1 << a) * NQ + ((long long)1 << (m - a)) * h.d;
             if (need > partcap) {
@@ -743,10 +841,12 @@ int mtgp_batch_autotune(mtgp_batch_t* b, int reps, int* chosen, cudaStream_t st)
             float tot = 0.f;
             for (int r = 0; r <= reps; ++r) {
                 cudaEventRecord(e0, st);
+                const int var = fused_variant(h.fp32, h.cplx, h.solve_df, h.d, m, a, false);
                 for (int ph = 0; ph < 3; ++ph) {
                     const int grid = ph == 1 ? (1 << a) : (1 << (m - a));
-                    fused_phase(ph, h.fp32, h.cplx, h.T, h.d, desc.data(), nullptr, nullptr, 0, grid,
-                                fused_threads(ph, a, h.d), fused_smem(ph, h.T, h.ncols, m, a, h.fp32, h.cplx), st);
+                    fused_phase(ph, var, h.fp32, h.cplx, h.T, h.d, desc.data(), nullptr, nullptr, 0, grid,
+                                fused_threads(ph, var, a, h.d, h.ncols, m),
+                                fused_smem(ph, var, h.T, h.ncols, m, a, h.fp32, h.cplx), st);
                 }
                 cudaEventRecord(e1, st);
                 cudaEventSynchronize(e1);

@@ -288,13 +288,28 @@ void launch_finalize(const Handle* h, ThetaPtrs th, bool grad, const double* par
                      const double* eta_partials, int neta, double* out, double* tau, double* g_eta,
                      double* g_W, double* g_v, double* g_s2, cudaStream_t st, int gcv = 0);
 
+// k_fused_rt.cu: yhat rounded to double-float pairs (hi, lo) for the double-float solve
+void launch_yhat_df(const double* yhat, float* yhat_df, long long n, cudaStream_t st);
+
 // k_fused.cu (equal sizes)
 bool fused_supported(const Handle* h);
 long long fused_partials_len(const Handle* h);
 void launch_fused(const Handle* h, ThetaPtrs th, bool grad, bool store_alpha, double* out, double* tau,
                   double* g_eta, double* g_W, double* g_v, double* g_s2, cudaStream_t st);
 // split of n = 2^m between kernels A/C (2^a) and B (2^(m-a)); a_pref < 0 picks the default
-bool fused_plan(int m, int ncols, bool fp32, bool cplx, int a_pref, int* a_out, int* lgL_out);
+bool fused_plan(int m, int ncols, int d, bool fp32, bool cplx, int a_pref, int* a_out, int* lgL_out);
+// kernel family of a fit's fused evaluation: the generic shared-memory kernels (any split, complex
+// spectra, FP64 transforms), or the register-tile kernels for FP32 real spectra with d <= 16 and both
+// tile sizes in 2^5 .. 2^9 (k_fused_rt.cu), whose kernel B solves in FP64 (FUSED_RT) or in
+// double-float (FUSED_RT_DF)
+enum { FUSED_GENERIC = 0, FUSED_RT = 1, FUSED_RT_DF = 2 };
+int fused_variant(bool fp32, bool cplx, bool solve_df, int d, int m, int a, bool store_alpha);
+bool fused_rt_ok(bool cplx, bool fp32, int d, int m, int a);
+int fused_rt_threads(int phase, int C, int m, int a);
+size_t fused_rt_smem(int phase, int T, int C, int m, int a);
+void fused_rt_phase(int phase, bool dfs, int T, int dmax, const void* single, const void* fits, const int2* items,
+                    int nitems, int grid, int threads, size_t smem, cudaStream_t st);
+int fused_rt_resident_blocks(int phase, bool dfs, int T, int dmax, int threads, size_t smem);
 // device descriptor of one fit (fused_desc_size() bytes, written to desc) with split a and the given
 // partial-sum buffer (2^a NQ + 2^(m-a) d doubles) and counters (2 unsigned)
 size_t fused_desc_size();
@@ -302,11 +317,11 @@ void fused_make_desc(const Handle* h, ThetaPtrs th, double* out, double* tau, do
                      double* g_v, double* g_s2, bool grad, int a, double* partials, unsigned* counters, void* desc);
 // one phase (0 = A, 1 = B, 2 = C) of one class: `single` (host descriptor) launches one fit with a grid of
 // its blocks, otherwise a persistent grid walks `nitems` (fit, block) items over the device descriptors
-void fused_phase(int phase, bool fp32, bool cplx, int T, int dmax, const void* single, const void* fits,
+void fused_phase(int phase, int variant, bool fp32, bool cplx, int T, int dmax, const void* single, const void* fits,
                  const int2* items, int nitems, int grid, int threads, size_t smem, cudaStream_t st);
-size_t fused_smem(int phase, int T, int C, int m, int a, bool fp32, bool cplx);
-int fused_threads(int phase, int a, int d);
-int fused_resident_blocks(int phase, bool fp32, bool cplx, int T, int dmax, int threads, size_t smem);
+size_t fused_smem(int phase, int variant, int T, int C, int m, int a, bool fp32, bool cplx);
+int fused_threads(int phase, int variant, int a, int d, int C, int m);
+int fused_resident_blocks(int phase, int variant, bool fp32, bool cplx, int T, int dmax, int threads, size_t smem);
 
 // k_mlp.cu: input width, output width and largest batch of a network
 void mlp_shape(const mtgp_mlp_t* m, int* in_width, int* out_width, int* max_batch);
@@ -327,6 +342,7 @@ int posterior_run(Handle* h, ThetaPtrs th, int nq, const double* xq, const int* 
 struct Handle {
     int kind, d, T, prec;
     bool fp32;           // transform precision
+    bool solve_df;       // FP32 transforms: per-frequency solve in double-float (else FP64)
     bool cplx;           // lattice spectra are complex
     bool equal;          // all n_t equal
     int gen_cols;
@@ -363,6 +379,7 @@ struct Handle {
     void* twid;          // twiddle table e^{-2 pi i k / 2^mmax}, k < 2^{mmax-1}, double2 and float2
     void* twid32;
     double* yhat;        // FP64 (complex for lattice), sorted tasks, length N
+    float* yhat_df;      // FP32-transform equal-size digital nets: yhat as double-float pairs (hi, lo), or null
     void* spec;          // column spectra (E = fp32 ? float : double, complex for lattice)
     void* wgt;           // adjoint weights, same layout as spec
     double* S;           // tree solver scratch (pair layout, FP64 (complex))

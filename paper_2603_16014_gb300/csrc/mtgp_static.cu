@@ -104,6 +104,7 @@ extern "C" int mtgp_nll_equal_static(int kind, int d, int T, int m, const uint32
     h.T = T;
     h.prec = precision;
     h.fp32 = precision == MTGP_FP32_TRANSFORM;
+    h.solve_df = h.fp32;
     h.cplx = kind == MTGP_LATTICE;
     h.equal = true;
     h.gen_cols = kind == MTGP_DNET ? gen_cols : 1;

@@ -11,7 +11,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import DNET, FP32_TRANSFORM, FP64, LATTICE, NOISE_PER_TASK, check, lib
+from ._lib import DNET, FP32_TRANSFORM, FP64, LATTICE, NOISE_PER_TASK, SOLVE_FP64, check, lib
 
 
 def _ptr(t):
@@ -35,9 +35,12 @@ class MTGP:
 
     ``gen``: lattice -- (d,) generating vector words; digital net -- (d, gen_cols) column words.
     ``shift``: (T, d) words.  ``precision``: "fp64" or "fp32" (FP32 kernel-column transforms).
+    ``solve``: "df" (default: FP32-transform digital nets solve each frequency in double-float) or
+    "fp64" (MTGP_SOLVE_FP64: FP64 per-frequency solves throughout).
     """
 
-    def __init__(self, kind: str, d: int, m, gen, shift, precision: str = "fp64", noise_per_task: bool = False):
+    def __init__(self, kind: str, d: int, m, gen, shift, precision: str = "fp64", noise_per_task: bool = False,
+                 solve: str = "df"):
         self.kind = LATTICE if kind == "lattice" else DNET
         self.d = int(d)
         self.m = [int(x) for x in m]
@@ -48,7 +51,8 @@ class MTGP:
         gen_cols = int(gen.shape[1]) if (self.kind == DNET and gen.ndim == 2) else 0
         m_arr = (ctypes.c_int * self.T)(*self.m)
         h = ctypes.c_void_p()
-        prec = (FP32_TRANSFORM if precision == "fp32" else FP64) | (NOISE_PER_TASK if noise_per_task else 0)
+        prec = ((FP32_TRANSFORM if precision == "fp32" else FP64) | (NOISE_PER_TASK if noise_per_task else 0)
+                | (SOLVE_FP64 if solve == "fp64" else 0))
         self.nsig = self.T if noise_per_task else 1
         check(lib().mtgp_create(ctypes.byref(h), self.kind, self.d, self.T, m_arr,
                                 gen.ctypes.data_as(ctypes.c_void_p), gen_cols,
@@ -57,9 +61,9 @@ class MTGP:
         self.precision = precision
 
     @classmethod
-    def from_problem(cls, p, precision=None, noise_per_task: bool = False):
+    def from_problem(cls, p, precision=None, noise_per_task: bool = False, solve: str = "df"):
         prec = precision or ("fp32" if p.fp32_transform else "fp64")
-        return cls(p.kind, p.d, p.m, p.gen, p.shift, prec, noise_per_task)
+        return cls(p.kind, p.d, p.m, p.gen, p.shift, prec, noise_per_task, solve)
 
     # ------------------------------------------------------------------ calls
     def points(self, stream=None) -> torch.Tensor:
@@ -268,7 +272,7 @@ class Batch:
     lattices, whose spectra decay below FP32 transform noise), or one of those per fit (a list).
     """
 
-    def __init__(self, problems, s: int = 2, precision="fp32"):
+    def __init__(self, problems, s: int = 2, precision="fp32", solve: str = "df"):
         self.problems = list(problems)
         n = len(self.problems)
         kind = [LATTICE if p.kind == "lattice" else DNET for p in self.problems]
@@ -293,7 +297,8 @@ class Batch:
                                       _carr(ctypes.c_int, T), _carr(ctypes.c_int, m),
                                       gen.ctypes.data_as(ctypes.c_void_p), _carr(ctypes.c_int, gcols),
                                       shift.ctypes.data_as(ctypes.c_void_p), s,
-                                      _carr(ctypes.c_int, [FP32_TRANSFORM if q == "fp32" else FP64 for q in precision])),
+                                      _carr(ctypes.c_int, [(FP32_TRANSFORM if q == "fp32" else FP64)
+                                                           | (SOLVE_FP64 if solve == "fp64" else 0) for q in precision])),
               "mtgp_batch_create")
         self._h = h
         self.n, self.s = n, s

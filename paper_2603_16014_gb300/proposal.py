@@ -135,9 +135,13 @@ def train(mlp: MLP, feats, targets, masks, steps: int, batch: int = 256, lr: flo
     return losses
 
 
-def propose(batch, mlp: MLP, stream=None) -> torch.Tensor:
+def propose(batch, mlp: MLP, judge: bool = False, stream=None):
     """Set every fit's parameters to the network's prediction from its features (mtgp_propose: features,
-    forward pass and parameter map in one call); returns the prediction."""
+    forward pass and parameter map in one call).  With ``judge`` the exact NLL picks, per fit, the best
+    of the prediction, two blends with the parameters set before the call and those parameters
+    themselves.  Returns (prediction, chosen candidate per fit or None)."""
     pred = torch.empty((batch.n, mlp.widths[-1]), dtype=torch.float32, device="cuda")
-    check(lib().mtgp_propose(batch._h, mlp._h, _ptr(pred), _stream(stream)), "mtgp_propose")
-    return pred
+    chosen = torch.empty(batch.n, dtype=torch.int32, device="cuda") if judge else None
+    check(lib().mtgp_propose(batch._h, mlp._h, _ptr(pred), 1 if judge else 0, _ptr(chosen), _stream(stream)),
+          "mtgp_propose")
+    return pred, chosen

@@ -84,5 +84,6 @@ def test_per_task_noise_refused_by_batch_and_static():
     gen = (ctypes.c_uint32 * 64)(*([1 << 31] * 64))
     gcols = (ctypes.c_int * 1)(32)
     shift = (ctypes.c_uint32 * 4)()
-    rc = lib().mtgp_batch_create(ctypes.byref(h), 1, kind, one, one, m, gen, gcols, shift, 1, FP64 | NOISE_PER_TASK)
+    prec = (ctypes.c_int * 1)(FP64 | NOISE_PER_TASK)
+    rc = lib().mtgp_batch_create(ctypes.byref(h), 1, kind, one, one, m, gen, gcols, shift, 1, prec)
     assert rc == 5

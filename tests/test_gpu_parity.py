@@ -240,6 +240,67 @@ def test_full_lattice_d16_T5_nested_vs_class_oracle():
               with_sigma2=True, h=1e-4, rtol=1e-6)
 
 
+# (d = 2, T = 8 at sigma2 = 1e-6 is outside FP32-transform mode: FP32 columns rounded exactly and transformed
+# in FP32 already miss 1e-5 there, 1.5e-5 on the CPU)
+RT_CASES = [(3, 1, 10), (9, 2, 11), (16, 3, 12), (5, 4, 13), (12, 6, 10), (3, 8, 11), (8, 4, 18)]
+
+
+@pytest.mark.parametrize("d,T,m", RT_CASES)
+def test_register_tile_path_vs_oracle(d, T, m):
+    """Equal-size digital nets with FP32 transforms at sizes the register-tile kernels take (both tile
+    sizes in 2^5..2^9, d <= 16): NLL and gradient against the per-frequency oracle, with the
+    double-float solve (default) and with the FP64 solve; the two solves see the same FP32 spectra and
+    agree to far better than the FP32-mode tolerance."""
+    from paper_2603_16014_gb300.mtgp import MTGP
+    p = inputs.make_problem("dnet", d, (m,) * T, seed=70 + m + T, s=min(2, T), eta=(0.3, 1.2), v=0.1, sigma2=1e-6,
+                            recipe="walshcos32", mmax=max(m, 16))
+    X = _points_oracle(p)
+    y = inputs.synth_y(p, X)
+    ref, g_eta, g_W, g_v, g_s2 = spectral.nll_grad_equal(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2)
+    gref = 0.5 * np.concatenate([g_eta, np.ravel(g_W), g_v, [g_s2]])
+    res = {}
+    for solve in ("df", "fp64"):
+        model = MTGP.from_problem(p, "fp32", solve=solve)
+        model.set_y(torch.from_numpy(y))
+        out, tau, ge, gW, gv, gs = model.nll_grad(p.eta, p.W, p.v, p.sigma2)
+        o2, _ = model.nll(p.eta, p.W, p.v, p.sigma2)
+        model.sync()
+        got = np.concatenate([ge.cpu().numpy(), gW.cpu().numpy().ravel(), gv.cpu().numpy(), gs.cpu().numpy()])
+        nll = out[0].item()
+        assert abs(nll - ref["nll"]) <= TOL_NLL["fp32"] * abs(ref["nll"]), (solve, nll, ref["nll"])
+        assert o2[0].item() == pytest.approx(nll, rel=1e-12, abs=0)
+        assert np.all(np.abs(got - gref) <= TOL_GRAD["fp32"] * np.abs(gref).max()), (solve, got, gref)
+        res[solve] = (nll, got)
+        model.close()
+    # the adjoint weights of both solves are rounded to FP32 before the FP32 adjoint transforms, so the
+    # gradients agree to the transforms' amplification of one rounding (1e-5 of the largest entry)
+    assert abs(res["df"][0] - res["fp64"][0]) <= 1e-10 * abs(res["fp64"][0])
+    assert np.all(np.abs(res["df"][1] - res["fp64"][1]) <= 1e-5 * np.abs(res["fp64"][1]).max())
+
+
+def test_double_float_solve_falls_back_to_fp64_outside_its_range():
+    """sigma2 = 1e-20 with a spectrum below the FP32 transform noise (d = 8, eta = 0.1): the clamped
+    frequencies have pivots far below the double-float working range (2^-50) and are solved by the FP64
+    recurrences; the result equals the FP64-solve handle's."""
+    from paper_2603_16014_gb300.mtgp import MTGP
+    p = inputs.make_problem("dnet", 8, (11,) * 3, seed=81, s=2, eta=0.1, v=0.1, sigma2=1e-20, recipe="walshcos32",
+                            mmax=16)
+    X = _points_oracle(p)
+    y = inputs.synth_y(p, X)
+    outs = {}
+    for solve in ("df", "fp64"):
+        model = MTGP.from_problem(p, "fp32", solve=solve)
+        model.set_y(torch.from_numpy(y))
+        out, tau, ge, gW, gv, gs = model.nll_grad(p.eta, p.W, p.v, p.sigma2)
+        model.sync()
+        outs[solve] = (out.cpu().numpy(), np.concatenate([ge.cpu().numpy(), gW.cpu().numpy().ravel(),
+                                                          gv.cpu().numpy(), gs.cpu().numpy()]))
+        model.close()
+    assert np.all(np.isfinite(outs["df"][0])) and np.all(np.isfinite(outs["df"][1]))
+    assert abs(outs["df"][0][0] - outs["fp64"][0][0]) <= 1e-10 * abs(outs["fp64"][0][0])
+    assert np.all(np.abs(outs["df"][1] - outs["fp64"][1]) <= 1e-5 * np.abs(outs["fp64"][1]).max())
+
+
 @pytest.mark.parametrize("kind", ["lattice", "dnet"])
 def test_medium_nested_gradient_vs_class_oracle(kind):
     """Nested sizes n = 2^12, 2^10, 2^8 (tree solver, FP64): every gradient entry against the residue-class

@@ -287,7 +287,7 @@ def test_propose_entry_point_equals_composed_calls():
     net = MLP(max_batch=8)
     net.set_params(net.init_params(3))
     net.fit_scaling(b.features())
-    pred = propose(b, net)
+    pred, _ = propose(b, net)
     th_prop = b.get_theta()
     ref_pred = net.forward(b.features())
     b.set_theta_proposal(ref_pred)
@@ -301,4 +301,55 @@ def test_propose_entry_point_equals_composed_calls():
         propose(b, bad)
     bad.close()
     net.close()
+    b.close()
+
+
+def test_judged_proposal_on_heldout_fits():
+    """Held-out fits (seeds not used in training): the judged proposal (mtgp_propose with the exact-NLL
+    judge) starts no fit worse than the plain fixed start and most strictly better, and reaches the plain
+    optimiser's best NLL in fewer steps, its own cost (five batched evaluations and the network)
+    included, on most fits."""
+    from paper_2603_16014_gb300.mtgp import Batch
+    from paper_2603_16014_gb300.proposal import MLP, propose, train
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    lr, S = 0.05, 400
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        train_fits = _fits(20, 128)
+        bt = Batch(train_fits, s=2, precision="auto")
+        bt.set_y(torch.from_numpy(np.concatenate(_ys(train_fits))))
+        th0 = torch.from_numpy(bt.pack([bench.default_theta(p) for p in train_fits])).cuda()
+        bt.fit(th0, 400, lr, graph=True, final_nll=False)
+        tg, mk = bt.targets()
+        feats = bt.features()
+        net = MLP(max_batch=128)
+        net.set_params(net.init_params(0))
+        train(net, feats, tg, mk, steps=800, batch=64, lr=2e-3, seed=1, lr_final=1e-4)
+        held = _fits(21, 32)
+        b = Batch(held, s=2, precision="auto")
+        b.set_y(torch.from_numpy(np.concatenate(_ys(held))))
+        theta0 = torch.from_numpy(b.pack([bench.default_theta(p) for p in held])).cuda()
+        traces = {}
+        for name in ("plain", "proposal"):
+            b.set_theta(theta0)
+            if name == "proposal":
+                _, chosen = propose(b, net, judge=True)
+            tr = torch.zeros(S * len(held), dtype=torch.float64, device="cuda")
+            b.fit(None, S, lr, graph=False, trace=tr, final_nll=False)
+            traces[name] = tr.view(S, -1).cpu().numpy()
+        stream.synchronize()
+    plain, prop = traces["plain"], traces["proposal"]
+    assert np.all(prop[0] <= plain[0]), (prop[0], plain[0])
+    better = prop[0] < plain[0]
+    assert better.mean() >= 0.75, (better.mean(), chosen.cpu().numpy())
+    target = np.nanmin(plain, axis=0)
+    k_plain = bench.steps_to_target(plain, target) + 1
+    k_prop = bench.steps_to_target(prop, target)
+    faster = (k_prop >= 0) & (k_prop + 1 + 6 < k_plain)
+    assert faster.mean() >= 0.75, (faster.mean(), k_plain, k_prop)
+    net.close()
+    bt.close()
     b.close()
