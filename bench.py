@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--eval-steps", type=int, default=2000, help="proposal: Adam steps per held-out run")
     ap.add_argument("--queries", type=int, default=1 << 16, help="posterior: mean-only queries")
     ap.add_argument("--queries-var", type=int, default=1 << 10, help="posterior: mean + variance queries")
+    ap.add_argument("--queries-full", type=int, default=1 << 20,
+                    help="posterior: one mean-only and one mean + variance call over this many queries (0: skip)")
     ap.add_argument("--sweep-m", type=int, nargs="+", default=[16, 18, 20, 22, 24], help="sweep: log2 n values")
     return ap.parse_args()
 
@@ -825,8 +827,10 @@ def run_nested(args):
     print(json.dumps(line), flush=True)
 
 
-def posterior_measure(nq_mean=1 << 16, nq_var=1 << 10, steps=5, cpu_seconds=10.0):
-    """Posterior mean-only and mean + variance query throughput on the d = 8 digital-net fit."""
+def posterior_measure(nq_mean=1 << 16, nq_var=1 << 10, steps=5, cpu_seconds=10.0, nq_full=0):
+    """Posterior mean-only and mean + variance query throughput on the d = 8 digital-net fit; with nq_full,
+    also one mean-only and one mean + variance call over nq_full queries (the 2^20 seeded uniform
+    queries of the learned-proposal workload), timed end to end on the device."""
     import torch
 
     from paper_2603_16014_gb300 import inputs
@@ -844,6 +848,21 @@ def posterior_measure(nq_mean=1 << 16, nq_var=1 << 10, steps=5, cpu_seconds=10.0
         model.sync()
         t = sum(ms) / len(ms)
         res[name] = {"queries": nq, "ms_per_call": t, "queries_per_s": nq / (t / 1e3)}
+    full = None
+    if nq_full:
+        _, xq, task = inputs.query_points(nq_full, p.d, seed=5, tasks=p.T)
+        xq_d, task_d = torch.from_numpy(xq).cuda(), torch.from_numpy(task).cuda()
+        full = {"queries": nq_full}
+        for name, var in (("mean", False), ("mean_var", True)):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            model.posterior(*th, xq_d, task_d, variance=var)
+            e1.record(stream)
+            model.sync()
+            full[name + "_s"] = e0.elapsed_time(e1) / 1e3
+            full[name + "_queries_per_s"] = nq_full / full[name + "_s"]
+        del xq_d, task_d
     model.profile(True)
     _, xq, task = inputs.query_points(nq_var, p.d, seed=3, tasks=p.T)
     model.posterior(*th, torch.from_numpy(xq).cuda(), torch.from_numpy(task).cuda(), variance=True)
@@ -861,6 +880,8 @@ def posterior_measure(nq_mean=1 << 16, nq_var=1 << 10, steps=5, cpu_seconds=10.0
            "mean": res["mean"], "mean_var": res["mean_var"],
            "kernel_pairs_per_s_mean": pairs_s,
            "kernels_ms_mean_var_call": {k: v[0] for k, v in prof.items()}}
+    if full:
+        out["full_queries"] = full
     if cpu_seconds:
         from oracle import spectral
         Xq, _, tq = inputs.query_points(64, p.d, seed=3, tasks=p.T)
@@ -877,7 +898,7 @@ def run_posterior(args):
     import torch
     torch.cuda.set_device(0)
     r = posterior_measure(args.queries, args.queries_var, max(args.steps // 10, 2),
-                          0.0 if args.no_cpu_baseline else 10.0)
+                          0.0 if args.no_cpu_baseline else 10.0, nq_full=args.queries_full)
     line = {"metric": "posterior queries per second (mean; mean + variance)", "n_gpus": 1, "higher_is_better": True,
             "data": "synthetic", **r}
     print(json.dumps(line), flush=True)

@@ -102,6 +102,7 @@ struct FitDesc {
     void* wgt;               // C x n adjoint weights
     const double* yhat;      // T x n observations, transformed
     const float2* yhat_df;   // the same as double-float pairs (FP32-transform digital nets), or null
+    const uint32_t* rtw;     // design words of the register-tile kernels (rt_words_len layout), or null
     double* alpha;           // T x n Lambda^-1 rhat (posterior)
     const double* tau;       // T optimal means (sorted)
     double* partials;        // kernel B partials (nb x NQ), then kernel C partials (na x d)
@@ -114,13 +115,15 @@ __device__ __forceinline__ int gq(int t, int u, int T) { return t * T - t * (t -
 
 // Final outputs from the totals, written by all threads of the block (W and the sorted means are
 // read into shared memory first, every output has its own thread).
+// W_staged: W already in shared memory (caller staged it, with a barrier since), or null to load it here
 __device__ void write_outputs(const double* tot, const double* etot, const FusedParams& p, const ThetaPtrs& th,
-                              const double* tau_sorted, OutPtrs o) {
-    __shared__ double s_W[MTGP_TMAX * MTGP_TMAX];
+                              const double* tau_sorted, OutPtrs o, const double* W_staged = nullptr) {
+    __shared__ double s_Wl[MTGP_TMAX * MTGP_TMAX];
+    const double* s_W = W_staged ? W_staged : s_Wl;
     const int T = p.T, tid = threadIdx.x;
     const double LOG2PI = 1.8378770664093453;
-    if (p.grad)
-        for (int e = tid; e < T * th.s; e += blockDim.x) s_W[e] = th.W[e];
+    if (p.grad && !W_staged)
+        for (int e = tid; e < T * th.s; e += blockDim.x) s_Wl[e] = th.W[e];
     if (tid == 0) {
         o.out[0] = 0.5 * (tot[0] + tot[1] + (double)p.N * LOG2PI);
         o.out[1] = tot[1];

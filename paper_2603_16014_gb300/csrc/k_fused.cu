@@ -474,6 +474,7 @@ FitDesc make_desc(const Handle* h, ThetaPtrs th, OutPtrs o, bool grad, bool stor
     f.wgt = h->wgt;
     f.yhat = h->yhat;
     f.yhat_df = reinterpret_cast<const float2*>(h->yhat_df);
+    f.rtw = h->rt_words;
     f.alpha = h->alpha;
     f.tau = h->tau;
     f.partials = h->partials;
@@ -673,11 +674,13 @@ bool fused_supported(const Handle* h) {
     return plan(h, &a, &lgL);
 }
 
+// B blocks' rows hold NQ sums (generic kernels) or NQ + 1 slots (register-tile kernels: the pivot product
+// as mantissa and exponent), then C blocks' d sums
 long long fused_partials_len(const Handle* h) {
     int a, lgL;
     if (!plan(h, &a, &lgL)) return 0;
     const int NQ = 3 + h->T * (h->T + 1) / 2;
-    return ((long long)1 << (a - lgL)) * NQ + ((long long)1 << (h->m[0] - a)) * h->d;
+    return ((long long)1 << (a - lgL)) * (NQ + 1) + ((long long)1 << (h->m[0] - a)) * h->d;
 }
 
 void launch_fused(const Handle* h, ThetaPtrs th, bool grad, bool store_alpha, double* out, double* tau, double* g_eta,

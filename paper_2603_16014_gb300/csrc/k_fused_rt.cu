@@ -74,10 +74,26 @@ struct RtDesign {
 };
 
 // fills RtDesign for the chunk starting at `base` with 2^loge words per lane (all threads call; ends
-// with a barrier); reads only handle constants, so it runs before the grid dependency wait
+// with a barrier); reads only handle constants, so it runs before the grid dependency wait.  With the
+// handle's word table the chunk's words are one round of loads; without it (the no-allocation entry
+// point) they are assembled from the generating matrices.
 __device__ __forceinline__ void rt_design(const FitDesc& f, long long base, int loge, RtDesign& s) {
     const FusedParams& p = f.p;
     const int d = p.d, E = 1 << loge;
+    if (f.rtw) {
+        const long long n32 = p.n >> 5;
+        const uint32_t* zl = f.rtw;
+        const uint32_t* z32 = f.rtw + 32 * d;
+        const uint32_t* dl = z32 + (long long)d * n32;
+        for (int e = threadIdx.x; e < 32 * d; e += blockDim.x) s.zl[e >> 5][e & 31] = zl[e];
+        for (int e = threadIdx.x; e < E * d; e += blockDim.x) {
+            const int j = e >> loge, k = e & (E - 1);
+            s.zh[j][k] = z32[(long long)j * n32 + (base >> 5) + k];
+        }
+        for (int e = threadIdx.x; e < p.C * d; e += blockDim.x) s.dl[e / d][e % d] = dl[e];
+        __syncthreads();
+        return;
+    }
     for (int e = threadIdx.x; e < d * p.gen_cols; e += blockDim.x) s.gen[e] = f.gen[e];
     for (int e = threadIdx.x; e < p.C * d; e += blockDim.x) {
         const int c = e / d, j = e - c * d;
@@ -101,25 +117,47 @@ __device__ __forceinline__ void rt_design(const FitDesc& f, long long base, int 
 // double-float (every factor from the exact product eta_j K_j) and rounded to FP32 once: that halves the
 // FP32 spectra's error against the d roundings of a plain FP32 product (the NLL error of FP32-transform
 // mode follows it).  Items go to the shared tile (column-major, 2^a per column).
+// the factor 1 + eta_j K_j of one item in double-float (from the exact product eta_j K_j)
+__device__ __forceinline__ df rt_factor(const RtDesign& s, const float* s_eta, int j, int lane, int e, int c) {
+    const float k = dsi2_kernel<float>(s.zl[j][lane] ^ s.zh[j][e] ^ s.dl[c][j]);
+    const float ej = s_eta[j];
+    const float pk = __fmul_rn(ej, k);
+    df f = two_sum(1.0f, pk);
+    f.lo = __fadd_rn(f.lo, __fmaf_rn(ej, k, -pk));
+    return f;
+}
+
+// prod_j (1 + eta_j K_j) of one (column, element) item: the d factors are independent, so they are
+// formed first and multiplied in a balanced tree (depth log2 DMAX instead of a chain of d products)
+template <int DMAX>
+__device__ __forceinline__ float rt_item(const RtDesign& s, const float* s_eta, int d, int a, int it) {
+    const int c = it >> a, lo = it & ((1 << a) - 1), lane = lo & 31, e = lo >> 5;
+    df f[DMAX];
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) f[j] = j < d ? rt_factor(s, s_eta, j, lane, e, c) : df_of(1.0f);
+#pragma unroll
+    for (int w = 1; w < DMAX; w <<= 1)
+#pragma unroll
+        for (int j = 0; j + w < DMAX; j += 2 * w) f[j] = df_mul(f[j], f[j + w]);
+    return f[0].hi;
+}
+
+// The chunk's column entries prod_j (1 + eta_j K_j), (column, element) items spread over the block, each
+// formed in double-float and rounded to FP32 once: that halves the FP32 spectra's error against the d
+// roundings of a plain FP32 product (the NLL error of FP32-transform mode follows it).  Two items per
+// iteration give each thread two independent chains.  Items go to the shared tile (column-major, 2^a
+// per column).
 template <int DMAX>
 __device__ __forceinline__ void rt_a_generate(const RtDesign& s, const float* s_eta, int d, int C, int a, float* tile) {
-    const int HA = 1 << a, n_items = C << a;
-    for (int it = threadIdx.x; it < n_items; it += blockDim.x) {
-        const int c = it >> a, lo = it & (HA - 1), lane = lo & 31, e = lo >> 5;
-        df q = df_of(1.0f);
-#pragma unroll
-        for (int j = 0; j < DMAX; ++j) {
-            if (j < d) {
-                const float k = dsi2_kernel<float>(s.zl[j][lane] ^ s.zh[j][e] ^ s.dl[c][j]);
-                const float ej = s_eta[j];
-                const float pk = __fmul_rn(ej, k);
-                df fj = two_sum(1.0f, pk);
-                fj.lo = __fadd_rn(fj.lo, __fmaf_rn(ej, k, -pk));
-                q = df_mul(q, fj);
-            }
-        }
-        tile[it] = q.hi;
+    const int n_items = C << a, stride = blockDim.x;
+    int it = threadIdx.x;
+    for (; it + stride < n_items; it += 2 * stride) {
+        const float v0 = rt_item<DMAX>(s, s_eta, d, a, it);
+        const float v1 = rt_item<DMAX>(s, s_eta, d, a, it + stride);
+        tile[it] = v0;
+        tile[it + stride] = v1;
     }
+    if (it < n_items) tile[it] = rt_item<DMAX>(s, s_eta, d, a, it);
 }
 
 // forward stages 0..a-1 of one column: shared tile -> registers -> global (contiguous)
@@ -239,22 +277,37 @@ __device__ __forceinline__ void block_sums_df(const df* s_v, int rows, int ncols
     }
 }
 
-// Column totals of one or two (rows x cols) arrays of double-float partials (fixed order, one warp per
-// column, 8 loads in flight per lane), rounded to FP64 by lane 0 into out1 / out2.
-__device__ void reduce_columns_df2(const double* p1, int r1, int c1, double* o1, const double* p2, int r2, int c2,
-                                   double* o2) {
+// Final totals of the register-tile kernels' partial sums (the last block; fixed order, one warp per
+// column, 8 loads in flight per lane).  Kernel B's rows hold NQ + 1 slots: the block's pivot product as a
+// double-float mantissa (slot 0) and binary exponent (slot 1), then the NQ - 1 sums; kernel C's rows hold
+// d sums.  Column 0 of tot becomes the log-determinant (one logarithm for the whole evaluation), columns
+// 1.. the other totals; etot the d eta totals (if pc is given).  Totals are rounded to FP64 by lane 0.
+__device__ void rt_final_totals(const double* pb, int nb, int NQ, const double* pc, int na, int d, double* tot,
+                                double* etot) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int qq = warp; qq < c1 + c2; qq += nw) {
-        const bool first = qq < c1;
-        const double* part = first ? p1 : p2;
-        const int nrows = first ? r1 : r2, ncols = first ? c1 : c2, q = first ? qq : qq - c1;
+    const int NQR = NQ + 1, ncol = NQ + (pc ? d : 0);
+    for (int col = warp; col < ncol; col += nw) {
+        if (col == 0) {
+            DFLogAcc acc;
+            acc.init();
+            for (int r = lane; r < nb; r += 32) {
+                acc.mul(get_df(pb + (long long)r * NQR));
+                acc.expo += __float_as_int(get_df(pb + (long long)r * NQR + 1).hi);
+            }
+            acc.warp_product();
+            if (lane == 0) tot[0] = df_to_double(acc.log_df());
+            continue;
+        }
+        const bool inb = col < NQ;
+        const double* part = inb ? pb + col + 1 : pc + (col - NQ);
+        const int nrows = inb ? nb : na, stride = inb ? NQR : d;
         df v = df_of(0.0f);
         for (int b0 = lane; b0 < nrows; b0 += 256) {
             df t[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int bb = b0 + 32 * k;
-                t[k] = bb < nrows ? get_df(part + (long long)bb * ncols + q) : df_of(0.0f);
+                t[k] = bb < nrows ? get_df(part + (long long)bb * stride) : df_of(0.0f);
             }
 #pragma unroll
             for (int k = 0; k < 8; ++k) v = df_add(v, t[k]);
@@ -266,7 +319,10 @@ __device__ void reduce_columns_df2(const double* p1, int r1, int c1, double* o1,
             w.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
             v = df_add(v, w);
         }
-        if (lane == 0) (first ? o1 : o2)[q] = df_to_double(v);
+        if (lane == 0) {
+            if (inb) tot[col] = df_to_double(v);
+            else etot[col - NQ] = df_to_double(v);
+        }
     }
     __syncthreads();
 }
@@ -370,6 +426,7 @@ __device__ __forceinline__ void rt_b_body(const FitDesc& f, int blk) {
     lacc_df.init();
     LogAcc lacc;
     lacc.init();
+    bool any_fb = !DFS;  // FP64 sums to fold into the double-float ones
     const double sig = s_sig;
     const df sigdf = df_from_double(sig);
     for (int r = threadIdx.x; r < HB; r += blockDim.x) {
@@ -397,6 +454,7 @@ __device__ __forceinline__ void rt_b_body(const FitDesc& f, int blk) {
                 lacc_df.mul_fp64(o.mant);
                 lacc_df.expo += o.expo;
                 bad |= o.bad;
+                any_fb = true;
             }
         } else {
             double mu[T][T], w[T][T], al[T], rh[T];
@@ -435,18 +493,23 @@ __device__ __forceinline__ void rt_b_body(const FitDesc& f, int blk) {
             rt_b_pass(true, loge, nullptr, wgt + (long long)c * p.n + lo0, p.a, s_sp + c * HB, lane);
         __syncthreads();  // the tile area is reused for the partial sums
     }
-    // block partial sums as double-float pairs: entries 1.. through shared memory (one warp per entry),
-    // entry 0 the block's log-determinant
-    double* partials = f.partials + (long long)blk * NQ;
+    // block partial sums as double-float pairs: the pivot product as mantissa and exponent (slots 0, 1),
+    // then the other sums through shared memory, one warp per entry (slots 2..)
+    double* partials = f.partials + (long long)blk * (NQ + 1);
     const int nt = blockDim.x;
     df* s_v = reinterpret_cast<df*>(smem_raw);
+    if (any_fb) {
 #pragma unroll
-    for (int q = 1; q < NQ; ++q) {
-        const df fb = df_from_double(acc[q]);
-        s_v[(q - 1) * nt + threadIdx.x] = DFS ? df_add(accd[DFS ? q : 0], fb) : fb;
+        for (int q = 1; q < NQ; ++q) {
+            const df fb = df_from_double(acc[q]);
+            s_v[(q - 1) * nt + threadIdx.x] = DFS ? df_add(accd[DFS ? q : 0], fb) : fb;
+        }
+    } else {
+#pragma unroll
+        for (int q = 1; q < NQ; ++q) s_v[(q - 1) * nt + threadIdx.x] = accd[DFS ? q : 0];
     }
     __syncthreads();
-    block_sums_df(s_v, nt, NQ - 1, partials + 1);
+    block_sums_df(s_v, nt, NQ - 1, partials + 2);
     if (threadIdx.x == 0) {
         DFLogAcc tot;
         tot.init();
@@ -454,11 +517,12 @@ __device__ __forceinline__ void rt_b_body(const FitDesc& f, int blk) {
             tot.mul(s_lm[w]);
             tot.expo += s_le[w];
         }
-        put_df(partials, tot.log_df());
+        put_df(partials, tot.mant);
+        put_df(partials + 1, df_make(__int_as_float(tot.expo), 0.0f));
     }
     if (grad) return;  // kernel C finishes
     if (!last_block(f.counters, f.nb)) return;
-    reduce_columns_df2(f.partials, f.nb, NQ, s_tot, nullptr, 0, 0, nullptr);
+    rt_final_totals(f.partials, f.nb, NQ, nullptr, 0, 0, s_tot, nullptr);
     write_outputs(s_tot, nullptr, p, th, f.tau, f.o);
     if (threadIdx.x == 0) *f.counters = 0u;
 }
@@ -481,30 +545,53 @@ __device__ __forceinline__ void rt_c_transform(const float* in, float* tile, int
 //   dL/deta_j += w K_j prod_{k != j} (1 + eta_k K_k)
 // with prefix / suffix products (no division by 1 + eta K, which may vanish)
 template <int DMAX>
-__device__ __forceinline__ void rt_c_contract(const RtDesign& s, const float* s_eta, int d, int C, int a,
-                                              const float* tile, float (&part)[DMAX]) {
-    const int HA = 1 << a, n_items = C << a;
-    for (int it = threadIdx.x; it < n_items; it += blockDim.x) {
-        const int c = it >> a, lo = it & (HA - 1), lane = lo & 31, e = lo >> 5;
-        float kv[DMAX], pre[DMAX];
-        float pr = 1.0f;
+__device__ __forceinline__ void rt_c_item(const RtDesign& s, const float* s_eta, int d, int a, int it, const float* tile,
+                                          float (&part)[DMAX]) {
+    const int c = it >> a, lo = it & ((1 << a) - 1), lane = lo & 31, e = lo >> 5;
+    float kv[DMAX], fv[DMAX], pre[DMAX];
 #pragma unroll
-        for (int j = 0; j < DMAX; ++j) {
-            if (j < d) {
-                kv[j] = dsi2_kernel<float>(s.zl[j][lane] ^ s.zh[j][e] ^ s.dl[c][j]);
-                pre[j] = pr;
-                pr *= fmaf(s_eta[j], kv[j], 1.0f);
-            }
-        }
-        float suf = tile[it];
-#pragma unroll
-        for (int j = DMAX - 1; j >= 0; --j) {
-            if (j < d) {
-                part[j] = fmaf(kv[j] * pre[j], suf, part[j]);
-                suf *= fmaf(s_eta[j], kv[j], 1.0f);
-            }
+    for (int j = 0; j < DMAX; ++j) {
+        if (j < d) {
+            kv[j] = dsi2_kernel<float>(s.zl[j][lane] ^ s.zh[j][e] ^ s.dl[c][j]);
+            fv[j] = fmaf(s_eta[j], kv[j], 1.0f);
         }
     }
+    float pr = 1.0f;
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) {
+        if (j < d) {
+            pre[j] = pr;
+            pr *= fv[j];
+        }
+    }
+    float suf = tile[it];
+#pragma unroll
+    for (int j = DMAX - 1; j >= 0; --j) {
+        if (j < d) {
+            part[j] = fmaf(kv[j] * pre[j], suf, part[j]);
+            suf *= fv[j];
+        }
+    }
+}
+
+// the eta contractions of the chunk, (column, element) items spread over the block, two per iteration:
+//   dL/deta_j += w K_j prod_{k != j} (1 + eta_k K_k)
+// with prefix / suffix products (no division by 1 + eta K, which may vanish)
+template <int DMAX>
+__device__ __forceinline__ void rt_c_contract(const RtDesign& s, const float* s_eta, int d, int C, int a,
+                                              const float* tile, float (&part)[DMAX]) {
+    const int n_items = C << a, stride = blockDim.x;
+    float part2[DMAX];
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) part2[j] = 0.0f;
+    int it = threadIdx.x;
+    for (; it + stride < n_items; it += 2 * stride) {
+        rt_c_item<DMAX>(s, s_eta, d, a, it, tile, part);
+        rt_c_item<DMAX>(s, s_eta, d, a, it + stride, tile, part2);
+    }
+    if (it < n_items) rt_c_item<DMAX>(s, s_eta, d, a, it, tile, part);
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) part[j] += part2[j];
 }
 
 template <int DMAX>
@@ -520,7 +607,10 @@ __device__ __forceinline__ void rt_c_body(const FitDesc& f, int blk) {
     float* tile = reinterpret_cast<float*>(smem_raw);  // C x 2^a adjoint weights
     const int loge = p.a - 5, d = p.d;
     const long long base = (long long)blk << p.a;
+    __shared__ double s_W[MTGP_TMAX * MTGP_TMAX];
     if (threadIdx.x < d) s_eta[threadIdx.x] = d2f(f.th.eta[threadIdx.x]);
+    // W for the final outputs, staged now so the last block does not wait for it
+    for (int e = threadIdx.x; e < p.T * f.th.s; e += blockDim.x) s_W[e] = f.th.W[e];
     rt_design(f, base, loge, s);
     pdl_wait();  // the adjoint weights and kernel B's partial sums
     pdl_trigger();
@@ -552,7 +642,7 @@ __device__ __forceinline__ void rt_c_body(const FitDesc& f, int blk) {
         }
     }
     __syncthreads();
-    double* partials_c = f.partials + (long long)f.nb * (3 + p.T * (p.T + 1) / 2);
+    double* partials_c = f.partials + (long long)f.nb * (4 + p.T * (p.T + 1) / 2);  // after B's NQ + 1 slots
     if (threadIdx.x < d) {
         S v = S(0);
         for (int w = 0; w < nw; ++w) v += s_red[w][threadIdx.x];
@@ -560,22 +650,22 @@ __device__ __forceinline__ void rt_c_body(const FitDesc& f, int blk) {
     }
     if (!last_block(f.counters + 1, f.na)) return;
     const int NQ = 3 + p.T * (p.T + 1) / 2;
-    reduce_columns_df2(f.partials, f.nb, NQ, s_tot, partials_c, f.na, d, s_etot);
-    write_outputs(s_tot, s_etot, p, f.th, f.tau, f.o);
+    rt_final_totals(f.partials, f.nb, NQ, partials_c, f.na, d, s_tot, s_etot);
+    write_outputs(s_tot, s_etot, p, f.th, f.tau, f.o, s_W);
     if (threadIdx.x == 0) f.counters[1] = 0u;
 }
 
 // ---------------------------------------------------------------------------------- kernels
 
 template <int DMAX>
-__global__ void __launch_bounds__(512) k_rt_a(FitDesc f) { rt_a_body<DMAX>(f, blockIdx.x); }
+__global__ void __launch_bounds__(512, 2) k_rt_a(FitDesc f) { rt_a_body<DMAX>(f, blockIdx.x); }
 template <int T, bool DFS>
 __global__ void __launch_bounds__(kRtBThreads, (T <= 4 ? 2 : 1)) k_rt_b(FitDesc f) { rt_b_body<T, DFS>(f, blockIdx.x); }
 template <int DMAX>
-__global__ void __launch_bounds__(512) k_rt_c(FitDesc f) { rt_c_body<DMAX>(f, blockIdx.x); }
+__global__ void __launch_bounds__(512, 2) k_rt_c(FitDesc f) { rt_c_body<DMAX>(f, blockIdx.x); }
 
 template <int DMAX>
-__global__ void __launch_bounds__(512) k_rt_batch_a(const FitDesc* fits, const int2* items, int nitems) {
+__global__ void __launch_bounds__(512, 2) k_rt_batch_a(const FitDesc* fits, const int2* items, int nitems) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int2 w = items[it];
         rt_a_body<DMAX>(fits[w.x], w.y);
@@ -591,7 +681,7 @@ __global__ void __launch_bounds__(kRtBThreads, (T <= 4 ? 2 : 1)) k_rt_batch_b(co
     }
 }
 template <int DMAX>
-__global__ void __launch_bounds__(512) k_rt_batch_c(const FitDesc* fits, const int2* items, int nitems) {
+__global__ void __launch_bounds__(512, 2) k_rt_batch_c(const FitDesc* fits, const int2* items, int nitems) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int2 w = items[it];
         rt_c_body<DMAX>(fits[w.x], w.y);
@@ -720,4 +810,45 @@ __global__ void k_yhat_df(const double* __restrict__ yhat, float2* __restrict__ 
 void launch_yhat_df(const double* yhat, float* yhat_df, long long n, cudaStream_t st) {
     const long long blocks = (n + 255) / 256;
     k_yhat_df<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(yhat, reinterpret_cast<float2*>(yhat_df), n);
+}
+
+namespace {
+// z_j(l), l < 32; z_j(32 k), k < n / 32; Delta_t XOR Delta_u per column (digital nets, equal sizes)
+__global__ void k_rt_words(uint32_t* __restrict__ out, int d, int C, long long n32, const uint32_t* __restrict__ gen,
+                           int gen_cols, const uint32_t* __restrict__ shift, const int2* __restrict__ cols) {
+    const long long tot = 32LL * d + (long long)d * n32 + (long long)C * d;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        uint32_t w;
+        if (e < 32LL * d) {
+            w = point_word(MTGP_DNET, (uint32_t)(e & 31), (int)(e >> 5), gen, gen_cols);
+        } else if (e < 32LL * d + (long long)d * n32) {
+            const long long r = e - 32LL * d;
+            const int j = (int)(r / n32);
+            w = point_word(MTGP_DNET, (uint32_t)((r - j * n32) << 5), j, gen, gen_cols);
+        } else {
+            const long long r = e - 32LL * d - (long long)d * n32;
+            const int c = (int)(r / d), j = (int)(r - (long long)c * d);
+            w = shift[cols[c].x * d + j] ^ shift[cols[c].y * d + j];
+        }
+        out[e] = w;
+    }
+}
+}  // namespace
+
+long long rt_words_len(const Handle* h) {
+    if (!h->equal || !h->fp32 || h->cplx || h->d > 16 || h->m[0] < 10) return 0;
+    return 32LL * h->d + (long long)h->d * (h->n[0] >> 5) + (long long)h->ncols * h->d;
+}
+
+void launch_rt_words(const Handle* h, cudaStream_t st) {
+    int2 cols[MTGP_MAX_COLS];
+    for (int c = 0; c < h->ncols; ++c) cols[c] = make_int2(h->cols[c].t, h->cols[c].u);
+    int2* dcols = nullptr;
+    if (cudaMalloc(&dcols, sizeof(int2) * h->ncols) != cudaSuccess) return;
+    cudaMemcpy(dcols, cols, sizeof(int2) * h->ncols, cudaMemcpyHostToDevice);
+    const long long tot = rt_words_len(h);
+    k_rt_words<<<(unsigned)((tot + 255) / 256 < 1024 ? (tot + 255) / 256 : 1024), 256, 0, st>>>(
+        h->rt_words, h->d, h->ncols, h->n[0] >> 5, h->gen, h->gen_cols, h->shift, dcols);
+    cudaStreamSynchronize(st);
+    cudaFree(dcols);
 }

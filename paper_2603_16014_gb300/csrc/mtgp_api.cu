@@ -194,7 +194,8 @@ cudaError_t dalloc(Handle* h, T** p, size_t count) {
 }
 
 void free_all(Handle* h) {
-    void* ptrs[] = {h->gen, h->shift, h->cols_dev, h->yoffs_dev, h->twid, h->twid32, h->yhat, h->yhat_df, h->spec,
+    void* ptrs[] = {h->gen, h->shift, h->cols_dev, h->yoffs_dev, h->twid, h->twid32, h->yhat, h->yhat_df, h->rt_words,
+                    h->spec,
                     h->wgt, h->S, h->Z, h->r, h->alpha, h->tau, h->partials, h->status, h->out_tmp, h->counters,
                     h->gcv_h, h->pi_buf, h->bmix, h->hio, h->lead_offs_dev, h->pairs_dev};
     for (void* p : ptrs)
@@ -459,6 +460,7 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
     AL(h->r, (size_t)h->N * vs);
     AL(h->alpha, (size_t)h->N * vs);
     if (h->equal && h->fp32 && !h->cplx) AL(h->yhat_df, (size_t)h->N * 2);
+    if (rt_words_len(h) > 0) AL(h->rt_words, (size_t)rt_words_len(h));
     AL(h->tau, (size_t)MTGP_TMAX);
     {
         const int NQ = solve_nq(h);
@@ -499,6 +501,7 @@ int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32
         return fail(MTGP_ERR_CUDA, "uploading handle descriptors failed");
     }
     launch_twiddles(h, 0);
+    if (h->rt_words) launch_rt_words(h, 0);
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_all(h);

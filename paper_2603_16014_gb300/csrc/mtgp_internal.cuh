@@ -89,6 +89,20 @@ __device__ __forceinline__ S dsi2_kernel(uint32_t X) {
     return (S)1.5 - (S)b * x - (S)2.5 * pow2_neg<S>(b);
 }
 
+// FP32 without conversion instructions (they issue through the MIO queue): x = X 2^-32 is assembled from
+// X shifted to its leading one (the exponent field from clz, the mantissa rounded to nearest with ties
+// away from zero), beta = clz(X) + 1 as the float 2^23 + beta - 2^23 (exact), 2^-beta from its exponent.
+template <>
+__device__ __forceinline__ float dsi2_kernel<float>(uint32_t X) {
+    const int lz = __clz(X);
+    const uint32_t m = X << lz;                                   // leading one at bit 31
+    const float x = __uint_as_float((uint32_t)(125 - lz) * 8388608u + (m >> 8) + ((m >> 7) & 1u));
+    const float bf = __int_as_float(0x4B000000 | (lz + 1)) - 8388608.0f;
+    const float pw = __int_as_float((126 - lz) << 23);            // 2^-(lz + 1)
+    const float k = __fmaf_rn(-2.5f, pw, __fmaf_rn(-bf, x, 1.5f));
+    return X == 0u ? 1.5f : k;
+}
+
 // FP64 forms assembled on the integer pipe.  |v| 2^-s as a double from integer fields: exact for
 // v < 2^53, truncated to 53 significant bits above; the callers' scalings never underflow.
 __device__ __forceinline__ double u64_times_pow2(unsigned long long v, int s, bool negative) {
@@ -290,6 +304,10 @@ void launch_finalize(const Handle* h, ThetaPtrs th, bool grad, const double* par
 
 // k_fused_rt.cu: yhat rounded to double-float pairs (hi, lo) for the double-float solve
 void launch_yhat_df(const double* yhat, float* yhat_df, long long n, cudaStream_t st);
+// k_fused_rt.cu: theta-independent design words of the register-tile kernels, per handle:
+// z_j(l) for the 32 lane offsets (d x 32), z_j(32 k) for k < n / 32 (d x n/32), shift XORs per column (C x d)
+long long rt_words_len(const Handle* h);
+void launch_rt_words(const Handle* h, cudaStream_t st);
 
 // k_fused.cu (equal sizes)
 bool fused_supported(const Handle* h);
@@ -311,7 +329,7 @@ void fused_rt_phase(int phase, bool dfs, int T, int dmax, const void* single, co
                     int nitems, int grid, int threads, size_t smem, cudaStream_t st);
 int fused_rt_resident_blocks(int phase, bool dfs, int T, int dmax, int threads, size_t smem);
 // device descriptor of one fit (fused_desc_size() bytes, written to desc) with split a and the given
-// partial-sum buffer (2^a NQ + 2^(m-a) d doubles) and counters (2 unsigned)
+// partial-sum buffer (2^a (NQ + 1) + 2^(m-a) d doubles) and counters (2 unsigned)
 size_t fused_desc_size();
 void fused_make_desc(const Handle* h, ThetaPtrs th, double* out, double* tau, double* g_eta, double* g_W,
                      double* g_v, double* g_s2, bool grad, int a, double* partials, unsigned* counters, void* desc);
@@ -380,6 +398,7 @@ struct Handle {
     void* twid32;
     double* yhat;        // FP64 (complex for lattice), sorted tasks, length N
     float* yhat_df;      // FP32-transform equal-size digital nets: yhat as double-float pairs (hi, lo), or null
+    uint32_t* rt_words;  // the same handles: design words of the register-tile kernels (rt_words_len), or null
     void* spec;          // column spectra (E = fp32 ? float : double, complex for lattice)
     void* wgt;           // adjoint weights, same layout as spec
     double* S;           // tree solver scratch (pair layout, FP64 (complex))
