@@ -1068,6 +1068,22 @@ def converged(trace, window: int, tol: float = 1e-6):
         return (best[-window - 1] - best[-1]) <= tol * np.abs(best[-1])
 
 
+def unreached_summary(prop, target, reached, window):
+    """The held-out fits whose proposal run never reached the target: how far above it the run ended
+    (median relative excess of its best NLL) and how many of those runs had converged (a different local
+    optimum rather than a slower approach)."""
+    import numpy as np
+    miss = ~reached
+    if not miss.any():
+        return {"fits": 0}
+    with np.errstate(invalid="ignore"):
+        best = np.nanmin(np.where(np.isfinite(prop[:, miss]), prop[:, miss], np.nan), axis=0)
+        excess = (best - target[miss]) / np.abs(target[miss])
+    return {"fits": int(miss.sum()), "best_excess_median": float(np.nanmedian(excess)),
+            "best_excess_max": float(np.nanmax(excess)),
+            "converged_fraction": float(np.mean(converged(prop[:, miss], window)))}
+
+
 def proposal_measure(train_fits, label_steps, train_steps, eval_fits, eval_steps, pool, lr=0.05):
     """Learned starting point on held-out fits.  Training: mixed fits labelled by `label_steps` batched
     Adam steps, the MLP trained by the library's BF16 kernels.  Held-out: every fit optimised from the
@@ -1181,6 +1197,7 @@ def proposal_measure(train_fits, label_steps, train_steps, eval_fits, eval_steps
                                      "proposal": prop_ms + float(np.median(k_prop)) * step_ms},
         "ms_per_batched_step": step_ms, "proposal_overhead_ms": prop_ms,
         "plain_converged_fraction": float(np.mean(converged(plain[:, valid], max(S // 10, 10)))),
+        "unreached": unreached_summary(prop[:, valid], target[valid], reached, max(S // 10, 10)),
         "train": {"fits": train_fits, "finite_labels": n_ok, "label_steps": label_steps, "label_s": t_lab,
                   "host_input_s": gen_s, "mlp_steps": train_steps, "mlp_train_s": t_train,
                   "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-50:].mean())},

@@ -543,24 +543,20 @@ __device__ __forceinline__ void rt_c_transform(const float* in, float* tile, int
 
 // the eta contractions of the chunk, one (column, element) item per thread:
 //   dL/deta_j += w K_j prod_{k != j} (1 + eta_k K_k)
-// with prefix / suffix products (no division by 1 + eta K, which may vanish)
+// with prefix / suffix products (no division by 1 + eta K, which may vanish).  The forward pass keeps
+// only the factors and K_j times the prefix product, so an item holds 2 d values.
 template <int DMAX>
 __device__ __forceinline__ void rt_c_item(const RtDesign& s, const float* s_eta, int d, int a, int it, const float* tile,
                                           float (&part)[DMAX]) {
     const int c = it >> a, lo = it & ((1 << a) - 1), lane = lo & 31, e = lo >> 5;
-    float kv[DMAX], fv[DMAX], pre[DMAX];
-#pragma unroll
-    for (int j = 0; j < DMAX; ++j) {
-        if (j < d) {
-            kv[j] = dsi2_kernel<float>(s.zl[j][lane] ^ s.zh[j][e] ^ s.dl[c][j]);
-            fv[j] = fmaf(s_eta[j], kv[j], 1.0f);
-        }
-    }
+    float fv[DMAX], kp[DMAX];
     float pr = 1.0f;
 #pragma unroll
     for (int j = 0; j < DMAX; ++j) {
         if (j < d) {
-            pre[j] = pr;
+            const float k = dsi2_kernel<float>(s.zl[j][lane] ^ s.zh[j][e] ^ s.dl[c][j]);
+            fv[j] = fmaf(s_eta[j], k, 1.0f);
+            kp[j] = k * pr;
             pr *= fv[j];
         }
     }
@@ -568,30 +564,33 @@ __device__ __forceinline__ void rt_c_item(const RtDesign& s, const float* s_eta,
 #pragma unroll
     for (int j = DMAX - 1; j >= 0; --j) {
         if (j < d) {
-            part[j] = fmaf(kv[j] * pre[j], suf, part[j]);
+            part[j] = fmaf(kp[j], suf, part[j]);
             suf *= fv[j];
         }
     }
 }
 
-// the eta contractions of the chunk, (column, element) items spread over the block, two per iteration:
+// the eta contractions of the chunk, (column, element) items spread over the block, two per iteration
+// (d <= 8; one for larger d, whose two items would not fit the register budget):
 //   dL/deta_j += w K_j prod_{k != j} (1 + eta_k K_k)
 // with prefix / suffix products (no division by 1 + eta K, which may vanish)
 template <int DMAX>
 __device__ __forceinline__ void rt_c_contract(const RtDesign& s, const float* s_eta, int d, int C, int a,
                                               const float* tile, float (&part)[DMAX]) {
     const int n_items = C << a, stride = blockDim.x;
-    float part2[DMAX];
-#pragma unroll
-    for (int j = 0; j < DMAX; ++j) part2[j] = 0.0f;
     int it = threadIdx.x;
-    for (; it + stride < n_items; it += 2 * stride) {
-        rt_c_item<DMAX>(s, s_eta, d, a, it, tile, part);
-        rt_c_item<DMAX>(s, s_eta, d, a, it + stride, tile, part2);
-    }
-    if (it < n_items) rt_c_item<DMAX>(s, s_eta, d, a, it, tile, part);
+    if constexpr (DMAX <= 8) {
+        float part2[DMAX];
 #pragma unroll
-    for (int j = 0; j < DMAX; ++j) part[j] += part2[j];
+        for (int j = 0; j < DMAX; ++j) part2[j] = 0.0f;
+        for (; it + stride < n_items; it += 2 * stride) {
+            rt_c_item<DMAX>(s, s_eta, d, a, it, tile, part);
+            rt_c_item<DMAX>(s, s_eta, d, a, it + stride, tile, part2);
+        }
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j) part[j] += part2[j];
+    }
+    for (; it < n_items; it += stride) rt_c_item<DMAX>(s, s_eta, d, a, it, tile, part);
 }
 
 template <int DMAX>

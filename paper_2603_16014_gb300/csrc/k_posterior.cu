@@ -442,6 +442,7 @@ std::mutex g_post_mu;
 }  // namespace
 
 void posterior_release(const Handle* h) {
+    posterior_df_release(h);
     std::lock_guard<std::mutex> lk(g_post_mu);
     auto it = g_post.find(h);
     if (it == g_post.end()) return;
@@ -492,6 +493,7 @@ int posterior_run(Handle* h, ThetaPtrs th, int nq, const double* xq, const int* 
     for (int t = 0; t < h->T; ++t)
         k_beta_finish<<<grid_for(h->n[t]), 256, 0, st>>>(ps->beta_c, ps->beta, h->n[t], h->yoff[t], h->cplx ? 1 : 0,
                                                        1.0 / sqrt((double)h->n[t]));
+    if (posterior_df_ok(h)) return posterior_df_run(h, th, nq, ps->xq, task, ps->design, ps->beta, mean, var, st);
     PostParams pp;
     pp.kind = h->kind;
     pp.alpha = h->smooth;

@@ -352,6 +352,13 @@ void mtgp_prof_begin(const Handle* h, const char* name, cudaStream_t st);
 void mtgp_prof_end(const Handle* h, cudaStream_t st);
 
 // k_posterior.cu
+// k_posterior_df.cu: posterior of equal-size FP32-transform digital nets in double-float arithmetic
+// (order-2 DSI kernel, d <= 16, n = 2^10 .. 2^18); xqw: query words, design: sorted design words, beta64:
+// K~^-1 r (FP64, sorted layout)
+bool posterior_df_ok(const Handle* h);
+void posterior_df_release(const Handle* h);
+int posterior_df_run(const Handle* h, ThetaPtrs th, int nq, const uint32_t* xqw, const int* task, const uint32_t* design,
+                     const double* beta64, double* mean, double* var, cudaStream_t st);
 int posterior_run(Handle* h, ThetaPtrs th, int nq, const double* xq, const int* task, double* mean,
                   double* var, cudaStream_t st);
 
