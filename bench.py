@@ -226,6 +226,17 @@ def fp32_peak_tflops(peaks) -> float:
 RT_OPS = {"word": 1, "kernel": 16, "a_factor": 9, "a_dfmul": 7, "c_contract": 5}
 
 
+# Lane operations of the double-float posterior per (query, design point) pair, counted from its arithmetic:
+# per dimension the XOR (1), the exact DSI kernel value 2^33 K as an integer split into two floats and joined
+# by TwoSum (24), eta K (double-float product, 7), 1 + eta K (10) and the running product (7); then the
+# contribution to the sum with beta (15).  A double-float Walsh butterfly output costs 11.
+PD_OPS_DIM, PD_OPS_ACC, RT_OPS_DF_STAGE = 49, 15, 11
+
+
+def pd_pair_ops(d: int) -> int:
+    return d * PD_OPS_DIM + PD_OPS_ACC
+
+
 def rt_item_ops(kernel: str, d: int, a: int) -> int:
     o = RT_OPS
     if kernel == "a":
@@ -898,13 +909,24 @@ def posterior_measure(nq_mean=1 << 16, nq_var=1 << 10, steps=5, cpu_seconds=10.0
     model.profile(False)
     N = p.N
     pairs_s = res["mean"]["queries_per_s"] * N
-    fp64_ops = pairs_s * (2 * p.d + 1)           # per pair: d (DFMA, DMUL) factor steps + one DFMA with beta
-    roof = {"bound": "alu", "kernel": "k_post_mean_part", "achieved": fp64_ops / 1e12, "unit": "T FP64 instr/s",
-            "peak": FP64_PEAK_TFLOPS / 2, "frac": fp64_ops / 1e12 / (FP64_PEAK_TFLOPS / 2),
-            "peak_source": "FP64 instruction issue rate = nominal 1.25 TFLOP/s / 2 flops per DFMA"}
+    peaks = measured_peaks()
+    lane_peak = SMS * FP32_LANES * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    mean_ops = pairs_s * pd_pair_ops(p.d)
+    roof = {"bound": "alu", "kernel": "k_pd_mean (double-float posterior mean)", "achieved": mean_ops / 1e12,
+            "unit": "T lane-ops/s", "peak": lane_peak, "frac": mean_ops / 1e12 / lane_peak,
+            "peak_source": "FP32/INT32 lane operations: 152 SMs x 128 lanes x measured max SM clock",
+            "work_model": f"{pd_pair_ops(p.d)} lane operations per (query, design point) pair at d={p.d}"}
+    if "var_rows" in prof:
+        rows_s = prof["var_rows"][0] / 1e3
+        a_split = min(max(p.m[0] - 8, 5), 9)
+        vals = nq_var * N
+        ops = vals * (pd_pair_ops(p.d) + DF_FLOPS["mul"] + RT_OPS_DF_STAGE * a_split)
+        roof["variance_rows"] = {"kernel": "k_pd_rows (rows, mean contribution, Walsh stages 0..a-1)",
+                                 "achieved": ops / rows_s / 1e12, "frac": ops / rows_s / 1e12 / lane_peak,
+                                 "work_model": "pair operations + R_tu product + 11 per element and stage"}
     out = {"value": res["mean"]["queries_per_s"], "unit": "queries/s", "roofline": roof,
            "config": {"workload": "posterior_dnet_d8_T4_n2^16", "d": p.d, "T": p.T, "N": N,
-                      "precision": "FP32 transforms / FP64 kernel sums"},
+                      "precision": "FP32 spectra / double-float kernel values, transforms and sums"},
            "mean": res["mean"], "mean_var": res["mean_var"],
            "kernel_pairs_per_s_mean": pairs_s,
            "kernels_ms_mean_var_call": {k: v[0] for k, v in prof.items()}}
