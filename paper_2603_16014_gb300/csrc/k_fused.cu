@@ -675,12 +675,12 @@ bool fused_supported(const Handle* h) {
 }
 
 // B blocks' rows hold NQ sums (generic kernels) or NQ + 1 slots (register-tile kernels: the pivot product
-// as mantissa and exponent), then C blocks' d sums
+// as mantissa and exponent), then C blocks' d sums, then NQ totals of B's rows (register-tile kernel C)
 long long fused_partials_len(const Handle* h) {
     int a, lgL;
     if (!plan(h, &a, &lgL)) return 0;
     const int NQ = 3 + h->T * (h->T + 1) / 2;
-    return ((long long)1 << (a - lgL)) * (NQ + 1) + ((long long)1 << (h->m[0] - a)) * h->d;
+    return ((long long)1 << (a - lgL)) * (NQ + 1) + ((long long)1 << (h->m[0] - a)) * h->d + NQ;
 }
 
 void launch_fused(const Handle* h, ThetaPtrs th, bool grad, bool store_alpha, double* out, double* tau, double* g_eta,

@@ -277,64 +277,73 @@ __device__ __forceinline__ void block_sums_df(const df* s_v, int rows, int ncols
     }
 }
 
-// Final totals of the register-tile kernels' partial sums (the last block; fixed order, one warp per
-// column, 8 loads in flight per lane).  Kernel B's rows hold NQ + 1 slots: the block's pivot product as a
-// double-float mantissa (slot 0) and binary exponent (slot 1), then the NQ - 1 sums; kernel C's rows hold
-// d sums.  Column 0 of tot becomes the log-determinant (one logarithm for the whole evaluation), columns
-// 1.. the other totals; etot the d eta totals (if pc is given).  Totals are rounded to FP64 by lane 0.
-__device__ void rt_final_totals(const double* pb, int nb, int NQ, const double* pc, int na, int d, double* tot,
-                                double* etot) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int NQR = NQ + 1, ncol = NQ + (pc ? d : 0);
-    for (int col = warp; col < ncol; col += nw) {
-        if (col == 0) {
-            // the rows' mantissas and exponents loaded 8 at a time before they are multiplied in (the same
-            // order as one row after another): one memory round trip per 8 rows instead of one per row
-            DFLogAcc acc;
-            acc.init();
-            for (int b0 = lane; b0 < nb; b0 += 256) {
-                df mk[8];
-                int ek[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int bb = b0 + 32 * k;
-                    mk[k] = bb < nb ? get_df(pb + (long long)bb * NQR) : df_of(1.0f);
-                    ek[k] = bb < nb ? __float_as_int(get_df(pb + (long long)bb * NQR + 1).hi) : 0;
-                }
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    acc.mul(mk[k]);
-                    acc.expo += ek[k];
-                }
-            }
-            acc.warp_product();
-            if (lane == 0) tot[0] = df_to_double(acc.log_df());
-            continue;
-        }
-        const bool inb = col < NQ;
-        const double* part = inb ? pb + col + 1 : pc + (col - NQ);
-        const int nrows = inb ? nb : na, stride = inb ? NQR : d;
-        df v = df_of(0.0f);
-        for (int b0 = lane; b0 < nrows; b0 += 256) {
-            df t[8];
+// Total of one column of the register-tile kernels' partial sums, by one warp (fixed order, 8 loads in
+// flight per lane; the total is valid in lane 0).  Kernel B's rows hold NQ + 1 slots: the block's pivot
+// product as a double-float mantissa (slot 0) and binary exponent (slot 1), then the NQ - 1 sums; column 0
+// is the log-determinant (one logarithm for the whole evaluation), columns 1 .. NQ - 1 the sums, columns
+// NQ .. NQ + d - 1 kernel C's d sums (rows of d).
+__device__ double rt_column_total(const double* pb, int nb, int NQ, const double* pc, int na, int d, int col) {
+    const int lane = threadIdx.x & 31;
+    const int NQR = NQ + 1;
+    if (col == 0) {
+        // the rows' mantissas and exponents loaded 8 at a time before they are multiplied in (the same
+        // order as one row after another): one memory round trip per 8 rows instead of one per row
+        DFLogAcc acc;
+        acc.init();
+        for (int b0 = lane; b0 < nb; b0 += 256) {
+            df mk[8];
+            int ek[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int bb = b0 + 32 * k;
-                t[k] = bb < nrows ? get_df(part + (long long)bb * stride) : df_of(0.0f);
+                mk[k] = bb < nb ? get_df(pb + (long long)bb * NQR) : df_of(1.0f);
+                ek[k] = bb < nb ? __float_as_int(get_df(pb + (long long)bb * NQR + 1).hi) : 0;
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) v = df_add(v, t[k]);
+            for (int k = 0; k < 8; ++k) {
+                acc.mul(mk[k]);
+                acc.expo += ek[k];
+            }
+        }
+        acc.warp_product();
+        return df_to_double(acc.log_df());
+    }
+    const bool inb = col < NQ;
+    const double* part = inb ? pb + col + 1 : pc + (col - NQ);
+    const int nrows = inb ? nb : na, stride = inb ? NQR : d;
+    df v = df_of(0.0f);
+    for (int b0 = lane; b0 < nrows; b0 += 256) {
+        df t[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int bb = b0 + 32 * k;
+            t[k] = bb < nrows ? get_df(part + (long long)bb * stride) : df_of(0.0f);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            df w;
-            w.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
-            w.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
-            v = df_add(v, w);
-        }
+        for (int k = 0; k < 8; ++k) v = df_add(v, t[k]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        df w;
+        w.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+        v = df_add(v, w);
+    }
+    return df_to_double(v);
+}
+
+// Final totals (the last block, one warp per column): tot[0 .. NQ - 1] from kernel B's rows, or copied from
+// btot when earlier blocks already formed them; etot the d eta totals of kernel C's rows (if pc is given).
+__device__ void rt_final_totals(const double* pb, int nb, int NQ, const double* pc, int na, int d, double* tot,
+                                double* etot, const double* btot = nullptr) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int ncol = NQ + (pc ? d : 0);
+    if (btot && (int)threadIdx.x < NQ) tot[threadIdx.x] = btot[threadIdx.x];
+    for (int col = (btot ? NQ : 0) + warp; col < ncol; col += nw) {
+        const double v = rt_column_total(pb, nb, NQ, pc, na, d, col);
         if (lane == 0) {
-            if (inb) tot[col] = df_to_double(v);
-            else etot[col - NQ] = df_to_double(v);
+            if (col < NQ) tot[col] = v;
+            else etot[col - NQ] = v;
         }
     }
     __syncthreads();
@@ -584,15 +593,15 @@ __device__ __forceinline__ void rt_c_item(const RtDesign& s, const float* s_eta,
 }
 
 // the eta contractions of the chunk, (column, element) items spread over the block, two per iteration
-// (d <= 8; one for larger d, whose two items would not fit the register budget):
+// (PAIR and d <= 8; otherwise one, within the register budget):
 //   dL/deta_j += w K_j prod_{k != j} (1 + eta_k K_k)
 // with prefix / suffix products (no division by 1 + eta K, which may vanish)
-template <int DMAX>
+template <int DMAX, bool PAIR>
 __device__ __forceinline__ void rt_c_contract(const RtDesign& s, const float* s_eta, int d, int C, int a,
                                               const float* tile, float (&part)[DMAX]) {
     const int n_items = C << a, stride = blockDim.x;
     int it = threadIdx.x;
-    if constexpr (DMAX <= 8) {
+    if constexpr (PAIR && DMAX <= 8) {
         float part2[DMAX];
 #pragma unroll
         for (int j = 0; j < DMAX; ++j) part2[j] = 0.0f;
@@ -606,7 +615,9 @@ __device__ __forceinline__ void rt_c_contract(const RtDesign& s, const float* s_
     for (; it < n_items; it += stride) rt_c_item<DMAX>(s, s_eta, d, a, it, tile, part);
 }
 
-template <int DMAX>
+// PAIR: two contraction items in flight per thread (the single-fit kernel; the batch kernel, which keeps more
+// state live across its item loop, takes one at a time within the register budget)
+template <int DMAX, bool PAIR>
 __device__ __forceinline__ void rt_c_body(const FitDesc& f, int blk) {
     using S = float;
     const FusedParams& p = f.p;
@@ -627,6 +638,16 @@ __device__ __forceinline__ void rt_c_body(const FitDesc& f, int blk) {
     pdl_wait();  // the adjoint weights and kernel B's partial sums
     pdl_trigger();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int NQ = 3 + p.T * (p.T + 1) / 2;
+    double* partials_c = f.partials + (long long)f.nb * (NQ + 1);  // after B's NQ + 1 slots per block
+    double* btot = partials_c + (long long)f.na * d;
+    // kernel B's column totals, column q by block q mod na, on the last warp (idle while the first warps
+    // transform the columns): the last block then reduces only kernel C's rows
+    if (warp == nw - 1)
+        for (int col = blk; col < NQ; col += f.na) {
+            const double v = rt_column_total(f.partials, f.nb, NQ, nullptr, 0, 0, col);
+            if (lane == 0) btot[col] = v;
+        }
     const S* wgt = reinterpret_cast<const S*>(f.wgt);
     for (int c = warp; c < p.C; c += nw) {
         const float* in = wgt + (long long)c * p.n + base;
@@ -643,7 +664,7 @@ __device__ __forceinline__ void rt_c_body(const FitDesc& f, int blk) {
     S part[DMAX];
 #pragma unroll
     for (int j = 0; j < DMAX; ++j) part[j] = S(0);
-    rt_c_contract<DMAX>(s, s_eta, d, p.C, p.a, tile, part);
+    rt_c_contract<DMAX, PAIR>(s, s_eta, d, p.C, p.a, tile, part);
     // the d block sums: a shuffle tree per warp, one shared row per warp, warps added in order
 #pragma unroll
     for (int j = 0; j < DMAX; ++j) {
@@ -654,15 +675,13 @@ __device__ __forceinline__ void rt_c_body(const FitDesc& f, int blk) {
         }
     }
     __syncthreads();
-    double* partials_c = f.partials + (long long)f.nb * (4 + p.T * (p.T + 1) / 2);  // after B's NQ + 1 slots
     if (threadIdx.x < d) {
         S v = S(0);
         for (int w = 0; w < nw; ++w) v += s_red[w][threadIdx.x];
         put_df(partials_c + (long long)blk * d + threadIdx.x, df_of(v));
     }
     if (!last_block(f.counters + 1, f.na)) return;
-    const int NQ = 3 + p.T * (p.T + 1) / 2;
-    rt_final_totals(f.partials, f.nb, NQ, partials_c, f.na, d, s_tot, s_etot);
+    rt_final_totals(f.partials, f.nb, NQ, partials_c, f.na, d, s_tot, s_etot, btot);
     write_outputs(s_tot, s_etot, p, f.th, f.tau, f.o, s_W);
     if (threadIdx.x == 0) f.counters[1] = 0u;
 }
@@ -674,7 +693,7 @@ __global__ void __launch_bounds__(512, 2) k_rt_a(FitDesc f) { rt_a_body<DMAX>(f,
 template <int T, bool DFS>
 __global__ void __launch_bounds__(kRtBThreads, (T <= 4 ? 2 : 1)) k_rt_b(FitDesc f) { rt_b_body<T, DFS>(f, blockIdx.x); }
 template <int DMAX>
-__global__ void __launch_bounds__(512, 2) k_rt_c(FitDesc f) { rt_c_body<DMAX>(f, blockIdx.x); }
+__global__ void __launch_bounds__(512, 2) k_rt_c(FitDesc f) { rt_c_body<DMAX, true>(f, blockIdx.x); }
 
 template <int DMAX>
 __global__ void __launch_bounds__(512, 2) k_rt_batch_a(const FitDesc* fits, const int2* items, int nitems) {
@@ -696,7 +715,7 @@ template <int DMAX>
 __global__ void __launch_bounds__(512, 2) k_rt_batch_c(const FitDesc* fits, const int2* items, int nitems) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int2 w = items[it];
-        rt_c_body<DMAX>(fits[w.x], w.y);
+        rt_c_body<DMAX, false>(fits[w.x], w.y);
         __syncthreads();
     }
 }

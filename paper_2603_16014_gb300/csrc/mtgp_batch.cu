@@ -143,7 +143,7 @@ int build_plan(mtgp_batch_s* b) {
         const Handle& h = b->fits[f]->h;
         const int NQ = 3 + h.T * (h.T + 1) / 2;
         const int m = h.m[0], a = b->a[f];
-        b->partoff[f + 1] = b->partoff[f] + ((long long)1 << a) * (NQ + 1) + ((long long)1 << (m - a)) * h.d;
+        b->partoff[f + 1] = b->partoff[f] + ((long long)1 << a) * (NQ + 1) + ((long long)1 << (m - a)) * h.d + NQ;
     }
     cudaFree(b->partials);
     b->partials = nullptr;
@@ -825,7 +825,7 @@ int mtgp_batch_autotune(mtgp_batch_t* b, int reps, int* chosen, cudaStream_t st)
             int aa, lgL;
             if (!fused_plan(m, h.ncols, h.d, h.fp32, h.cplx, a, &aa, &lgL)) continue;
             const int NQ = 3 + h.T * (h.T + 1) / 2;
-            const long long need = ((long long)1 << a) * (NQ + 1) + ((long long)1 << (m - a)) * h.d;
+            const long long need = ((long long)1 << a) * (NQ + 1) + ((long long)1 << (m - a)) * h.d + NQ;
             if (need > partcap) {
                 cudaFree(part);
                 partcap = need;
