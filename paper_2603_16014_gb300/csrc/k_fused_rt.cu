@@ -602,21 +602,18 @@ __device__ __forceinline__ void rt_c_contract(const RtDesign& s, const float* s_
     const int n_items = C << a, stride = blockDim.x;
     int it = threadIdx.x;
     if constexpr (PAIR && DMAX <= 8) {
-        float part2[DMAX];
-#pragma unroll
-        for (int j = 0; j < DMAX; ++j) part2[j] = 0.0f;
+        // both items add into the same sums in item order, so the result equals one item at a time; only
+        // their kernel values and products overlap
         for (; it + stride < n_items; it += 2 * stride) {
             rt_c_item<DMAX>(s, s_eta, d, a, it, tile, part);
-            rt_c_item<DMAX>(s, s_eta, d, a, it + stride, tile, part2);
+            rt_c_item<DMAX>(s, s_eta, d, a, it + stride, tile, part);
         }
-#pragma unroll
-        for (int j = 0; j < DMAX; ++j) part[j] += part2[j];
     }
     for (; it < n_items; it += stride) rt_c_item<DMAX>(s, s_eta, d, a, it, tile, part);
 }
 
-// PAIR: two contraction items in flight per thread (the single-fit kernel; the batch kernel, which keeps more
-// state live across its item loop, takes one at a time within the register budget)
+// PAIR: two contraction items per loop iteration (the single-fit kernel; the batch kernel, which keeps more
+// state live across its item loop, takes one at a time within the register budget); the sums are the same
 template <int DMAX, bool PAIR>
 __device__ __forceinline__ void rt_c_body(const FitDesc& f, int blk) {
     using S = float;
