@@ -244,6 +244,16 @@ def rt_item_ops(kernel: str, d: int, a: int) -> int:
     return d * (o["word"] + o["kernel"] + o["c_contract"]) + a
 
 
+def fp64_equivalent(n: int, T: int, avg_s: float) -> dict:
+    """Kernel B in the units of an FP64 solve: the factorisation, inverse, solves and G of one frequency
+    take about T^3/3 + T^3 + 3 T^2 FP64 flops, counted as 120 at T = 4 (the figure of the solve's
+    specification), against the nominal FP64 peak."""
+    per = 120.0 * (4 * T ** 3 / 3 + 3 * T * T) / (4 * 64 / 3 + 48)
+    tf = n * per / avg_s / 1e12
+    return {"flops_per_frequency": per, "achieved_tflops": tf, "peak_tflops": FP64_PEAK_TFLOPS,
+            "frac": tf / FP64_PEAK_TFLOPS}
+
+
 def roofline_fused(name: str, avg_s: float, n: int, T: int, C: int, d: int, a: int, peaks) -> dict:
     """Roofline of one fused kernel of the digital-net evaluation (FP32 transforms, register tiles).
     Kernel B against the FP32 FMA peak with the double-float solve's FP32 flops per frequency; kernels
@@ -260,7 +270,8 @@ def roofline_fused(name: str, avg_s: float, n: int, T: int, C: int, d: int, a: i
                 "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                 "traffic": profile_traffic(kernel), "flops_per_launch": flops, "avg_launch_us": avg_s * 1e6,
                 "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flops x measured max SM clock ({mhz} MHz)",
-                "work_model": f"{df_solve_flops_per_freq(T, True)} FP32 flops per frequency (double-float recurrences)"}
+                "work_model": f"{df_solve_flops_per_freq(T, True)} FP32 flops per frequency (double-float recurrences)",
+                "fp64_equivalent": fp64_equivalent(n, T, avg_s)}
     which = "a" if name == "fused_a" else "c"
     per_item = rt_item_ops(which, d, a)
     ops = n * C * per_item
