@@ -1205,6 +1205,7 @@ def proposal_measure(train_fits, label_steps, train_steps, eval_fits, eval_steps
     with np.errstate(invalid="ignore"):
         target = np.nanmin(np.where(np.isfinite(plain), plain, np.nan), axis=0)
     valid = np.isfinite(target)
+    kinds = np.array([p.kind for p in probs])
     k_plain = steps_to_target(plain[:, valid], target[valid]) + 1
     k_prop = steps_to_target(prop[:, valid], target[valid])
     reached = k_prop >= 0
@@ -1231,6 +1232,12 @@ def proposal_measure(train_fits, label_steps, train_steps, eval_fits, eval_steps
         "ms_per_batched_step": step_ms, "proposal_overhead_ms": prop_ms,
         "plain_converged_fraction": float(np.mean(converged(plain[:, valid], max(S // 10, 10)))),
         "unreached": unreached_summary(prop[:, valid], target[valid], reached, max(S // 10, 10)),
+        "by_kind": {kd: {"fits": int(np.sum(kinds[valid] == kd)),
+                         "reached_fraction": float(reached[kinds[valid] == kd].mean()),
+                         "faster_fraction": float(faster[kinds[valid] == kd].mean()),
+                         "median_steps": float(np.median(k_prop[kinds[valid] == kd])),
+                         "plain_median_steps": float(np.median(k_plain[kinds[valid] == kd]))}
+                    for kd in ("lattice", "dnet") if np.any(kinds[valid] == kd)},
         "train": {"fits": train_fits, "finite_labels": n_ok, "label_steps": label_steps, "label_s": t_lab,
                   "host_input_s": gen_s, "mlp_steps": train_steps, "mlp_train_s": t_train,
                   "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-50:].mean())},
