@@ -474,6 +474,8 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "nll": outs[0][0].item(),
     }
+    if world == 1:
+        line["solve_variants"] = solve_variants(p, y, th, outs, K, args.warmup, flush, stream, value)
     if world == 1 and not args.no_plain:
         pv, pnll = plain_arm(p, model, y, 10, flush, stream)
         line["vs_plain"] = {"plain_evals_per_s": pv, "speedup": value / pv, "plain_nll": pnll,
@@ -764,6 +766,29 @@ def plain_torch_nll_grad(p, Xw, yhat):
         return nll, eta.grad, W.grad, v.grad, s2.grad
 
     return step
+
+
+def solve_variants(p, y, th, outs, steps, warmup, flush, stream, value_df):
+    """The same evaluation with the per-frequency solves in FP64 (MTGP_SOLVE_FP64) beside the default
+    double-float solves: evals/s of both and the relative differences of their NLL and gradient."""
+    import numpy as np
+    import torch
+
+    from paper_2603_16014_gb300.mtgp import MTGP
+
+    m64 = MTGP.from_problem(p, "fp32", solve="fp64")
+    m64.set_y(torch.from_numpy(y))
+    o64 = m64.nll_grad(*th)
+    ms = _timed(lambda: m64.nll_grad(*th, outs=o64), steps, max(warmup, 3), flush, stream)
+    m64.sync()
+    v64 = 1e3 * len(ms) / sum(ms)
+    g_df = torch.cat([o.reshape(-1) for o in outs[2:]]).cpu().numpy()
+    g_64 = torch.cat([o.reshape(-1) for o in o64[2:]]).cpu().numpy()
+    n_df, n_64 = outs[0][0].item(), o64[0][0].item()
+    m64.close()
+    return {"double_float": {"evals_per_s": value_df}, "fp64": {"evals_per_s": v64},
+            "speedup": value_df / v64, "nll_rel_diff": abs(n_df - n_64) / abs(n_64),
+            "grad_diff_rel_max": float(np.max(np.abs(g_df - g_64)) / np.max(np.abs(g_64)))}
 
 
 def plain_arm(p, model, y, steps, flush, stream):
