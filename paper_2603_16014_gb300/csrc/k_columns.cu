@@ -5,6 +5,7 @@
 // in radical-inverse order, generated on the fly from the index i (Def. 2.1 / 2.2, Eq. 2.4-2.6).
 // The task covariance R and the noise enter later, per frequency, so the columns depend on eta only.
 #include "mtgp_internal.cuh"
+#include "kernel_df.cuh"
 
 namespace {
 
@@ -190,6 +191,88 @@ k_eta_grad(const void* omega, ColParams cp, int ncols, int kind, int d, const ui
     }
 }
 
+// The same contraction for FP64 fits in double-float arithmetic (no mixture, d <= DMAX):
+// K_j s exact (digital nets) or to ~2^-47 (lattices), the factors, prefix products and the per-thread sums
+// as double-float pairs on the FP32 pipe, the block sums in FP64.  Only the eta gradient depends on it;
+// its terms carry ~2^-46 relative error against the FP64 gradient tolerance of 1e-7.
+template <bool CPLX, int DMAX>
+__global__ void __launch_bounds__(kThreads)
+k_eta_grad_df(const void* omega, ColParams cp, int ncols, int kind, int d, const uint32_t* __restrict__ gen,
+              int gen_cols, const uint32_t* __restrict__ shift, const double* __restrict__ eta,
+              double* __restrict__ partials) {
+    __shared__ df s_es[DMAX];
+    __shared__ double s_red[kThreads / 32][DMAX];
+    __shared__ uint32_t s_dt[DMAX], s_du[DMAX], s_zhi[DMAX];
+    __shared__ uint32_t s_zlo[DMAX * kThreads];
+    const int tid = threadIdx.x;
+    const double sinv = kval_scale_inv(kind);
+    if (tid < d) s_es[tid] = df_from_double(eta[tid] * sinv);
+    for (int j = 0; j < d; ++j) s_zlo[j * kThreads + tid] = point_word(kind, (uint32_t)tid, j, gen, gen_cols);
+    const Si2Consts sc = si2_consts(cp.alpha);
+    df acc[DMAX];
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) acc[j] = df_of(0.0f);
+    const long long ntiles = cp.tile0[ncols];
+    for (long long g = blockIdx.x; g < ntiles; g += gridDim.x) {
+        int c = 0;
+        while (c + 1 < ncols && g >= cp.tile0[c + 1]) ++c;
+        const ColDesc cd = cp.cols[c];
+        const long long t0 = (g - cp.tile0[c]) * kThreads;
+        __syncthreads();  // the previous tile's reads of the shared words are done
+        if (tid < d) {
+            s_zhi[tid] = point_word(kind, (uint32_t)t0, tid, gen, gen_cols);
+            s_dt[tid] = shift[cd.t * d + tid];
+            s_du[tid] = shift[cd.u * d + tid];
+        }
+        __syncthreads();
+        const long long i = t0 + tid;
+        if (i >= cd.n) continue;
+        double w;
+        if (CPLX) {
+            const cx<double> o = reinterpret_cast<const cx<double>*>(omega)[(cd.role == 2 ? cd.src : cd.off) + i];
+            w = cd.role == 2 ? o.im : o.re;
+        } else {
+            w = reinterpret_cast<const double*>(omega)[cd.off + i];
+        }
+        df fv[DMAX], kp[DMAX];
+        df pr = df_of(1.0f);
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j) {
+            if (j < d) {
+                const uint32_t z = combine_word(kind, s_zhi[j], s_zlo[j * kThreads + tid]);
+                const df ks = kval_scaled_df(kind, pair_word(kind, z, s_dt[j], s_du[j]), sc);
+                fv[j] = df_one_plus(df_mul(s_es[j], ks));
+                kp[j] = df_mul(ks, pr);
+                pr = df_mul(pr, fv[j]);
+            }
+        }
+        // the adjoint weight rides in the suffix product: suf = w prod_{l > j} (1 + eta_l K_l)
+        df suf = df_from_double(w);
+#pragma unroll
+        for (int j = DMAX - 1; j >= 0; --j) {
+            if (j < d) {
+                acc[j] = df_fma(acc[j], kp[j], suf);
+                suf = df_mul(suf, fv[j]);
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < DMAX; ++j) {
+        if (j < d) {
+            double v = df_to_double(acc[j]) * sinv;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) s_red[warp][j] = v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < d) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_red[w][threadIdx.x];
+        partials[(long long)blockIdx.x * d + threadIdx.x] = v;
+    }
+}
+
 // F(a), F(b) from Z = F(a + i b) for real a, b (Hermitian spectra): F(a)[f] = (Z[f] + conj Z[-f]) / 2,
 // F(b)[f] = -i (Z[f] - conj Z[-f]) / 2, -f = (n - f) mod n.  One thread takes f and -f together, so
 // the lead's array is overwritten in place.
@@ -298,6 +381,12 @@ int eta_grad_blocks(const Handle* h) {
     return (int)b;
 }
 
+// FP64 fits whose eta contraction runs in double-float: the SI kernels of smoothness 1..4 and the order-2
+// DSI kernel (no mixture), d <= 16
+static bool eta_grad_df_ok(const Handle* h) {
+    return !h->fp32 && !h->dsi_mix && h->d <= 16;
+}
+
 void launch_eta_grad(const Handle* h, const double* eta, const void* omega, double* partials, int nblk,
                      cudaStream_t st) {
     ColParams cp = make_params(h);
@@ -310,6 +399,18 @@ void launch_eta_grad(const Handle* h, const double* eta, const void* omega, doub
     } else if (h->fp32) {
         if (h->cplx) MTGP_ETA_GRAD(float, true, false);
         else MTGP_ETA_GRAD(float, false, false);
+    } else if (eta_grad_df_ok(h)) {
+#define MTGP_ETA_GRAD_DF(C, DM) \
+    k_eta_grad_df<C, DM><<<nblk, kThreads, 0, st>>>(omega, cp, h->ncols, h->kind, h->d, h->gen, h->gen_cols, h->shift, \
+                                                    eta, partials)
+        if (h->d <= 8) {
+            if (h->cplx) MTGP_ETA_GRAD_DF(true, 8);
+            else MTGP_ETA_GRAD_DF(false, 8);
+        } else {
+            if (h->cplx) MTGP_ETA_GRAD_DF(true, 16);
+            else MTGP_ETA_GRAD_DF(false, 16);
+        }
+#undef MTGP_ETA_GRAD_DF
     } else {
         if (h->cplx) MTGP_ETA_GRAD(double, true, false);
         else MTGP_ETA_GRAD(double, false, false);

@@ -12,6 +12,7 @@
 // results do not depend on block scheduling.  Columns: c = 0 is the diagonal block's column (shared
 // by all tasks for equal sizes), then one per task pair t < u.
 #include "fused_common.cuh"
+#include "kernel_df.cuh"
 
 namespace {
 
@@ -231,6 +232,34 @@ __device__ __forceinline__ void fused_b_body(const FitDesc& f, int blk) {
 
 // ---------------------------------------------------------------------------------- kernel C
 
+// eta contraction of one item over dimensions 0 .. nd-1 of X in double-float: pd_j += K_j s pre_j suf_j,
+// pre_j = pre0 prod_{k < j} (1 + eta_k K_k), suf_j = suf0 prod_{j < k < nd} (1 + eta_k K_k) (suf0 carries the
+// adjoint weight); es_j = eta_j / s.  Returns pre0 times the product of the nd factors.
+template <int NH>
+__device__ __forceinline__ df contract_df_pass(const uint32_t* X, int nd, const df* es, int kind, const Si2Consts& sc,
+                                               df pre0, df suf0, df* pd) {
+    df fv[NH], kp[NH];
+    df pr = pre0;
+#pragma unroll
+    for (int j = 0; j < NH; ++j) {
+        if (j < nd) {
+            const df ks = kval_scaled_df(kind, X[j], sc);
+            fv[j] = df_one_plus(df_mul(es[j], ks));
+            kp[j] = df_mul(ks, pr);
+            pr = df_mul(pr, fv[j]);
+        }
+    }
+    df suf = suf0;
+#pragma unroll
+    for (int j = NH - 1; j >= 0; --j) {
+        if (j < nd) {
+            pd[j] = df_fma(pd[j], kp[j], suf);
+            suf = df_mul(suf, fv[j]);
+        }
+    }
+    return pr;
+}
+
 template <typename S, bool CPLX, int DMAX>
 __device__ __forceinline__ void fused_c_body(const FitDesc& f, int blk) {
     using E = typename El<S, CPLX>::T;
@@ -302,12 +331,61 @@ __device__ __forceinline__ void fused_c_body(const FitDesc& f, int blk) {
             }
         }
     };
-    if (ztab) {
+    // FP64 fits (d <= 16): the contraction in double-float on the FP32 pipe (kernel_df.cuh), K_j s exact for
+    // digital nets and to ~2^-47 for lattices, sums rescaled by 1/s at the end; it feeds only the eta
+    // gradient (FP64 tolerance 1e-7 of its largest entry against ~2^-46 per term)
+    bool done = false;
+    if constexpr (std::is_same<S, double>::value && DMAX <= 16) {
+        __shared__ df s_es[DMAX];
+        const double sinv = kval_scale_inv(p.kind);
+        if (threadIdx.x < d) s_es[threadIdx.x] = df_from_double(eta[threadIdx.x] * sinv);
+        __syncthreads();
+        const Si2Consts sc = si2_consts(p.alpha);
+        df pd[DMAX];
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j) pd[j] = df_of(0.0f);
+        auto item_df = [&](const uint32_t* zc, int zstride, int c, double w) {
+            const int t = p.colt[c], u = p.colu[c];
+            uint32_t X[DMAX];
+#pragma unroll
+            for (int j = 0; j < DMAX; ++j)
+                X[j] = j < d ? pair_word(p.kind, zc[j * zstride], s_sh[t * d + j], s_sh[u * d + j]) : 0u;
+            const df wd = df_from_double(w);
+            if constexpr (DMAX <= 8) {
+                contract_df_pass<DMAX>(X, d, s_es, p.kind, sc, df_of(1.0f), wd, pd);
+            } else {
+                // two passes of 8 dimensions: the upper factors' product rides in the lower pass's suffix,
+                // the lower factors' product in the upper pass's prefix (upper factors formed twice)
+                df up = df_of(1.0f);
+#pragma unroll
+                for (int j = 8; j < DMAX; ++j)
+                    if (j < d) up = df_mul(up, df_one_plus(df_mul(s_es[j], kval_scaled_df(p.kind, X[j], sc))));
+                const df lowp = contract_df_pass<8>(X, d < 8 ? d : 8, s_es, p.kind, sc, df_of(1.0f), df_mul(wd, up), pd);
+                contract_df_pass<8>(X + 8, d - 8, s_es + 8, p.kind, sc, lowp, wd, pd + 8);
+            }
+        };
+        if (ztab) {
+            for (int e = threadIdx.x; e < HA * p.C; e += blockDim.x) {
+                const int c = e >> p.a, lo = e & (HA - 1);
+                item_df(s_z + lo, HA, c, (double)el_re(buf[e]));
+            }
+        } else {
+            for (int lo = threadIdx.x; lo < HA; lo += blockDim.x) {
+                uint32_t z[DMAX];
+                chunk_point<DMAX>(p.kind, d, (uint32_t)lo, s_zhi, s_gen, p.gen_cols, z);
+                for (int c = 0; c < p.C; ++c) item_df(z, 1, c, (double)el_re(buf[c * HA + lo]));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < DMAX; ++j) part[j] = (S)(df_to_double(pd[j]) * sinv);
+        done = true;
+    }
+    if (!done && ztab) {
         for (int e = threadIdx.x; e < HA * p.C; e += blockDim.x) {
             const int c = e >> p.a, lo = e & (HA - 1);
             item(s_z + lo, HA, c, el_re(buf[e]));
         }
-    } else {
+    } else if (!done) {
         for (int lo = threadIdx.x; lo < HA; lo += blockDim.x) {
             uint32_t z[DMAX];
             chunk_point<DMAX>(p.kind, d, (uint32_t)lo, s_zhi, s_gen, p.gen_cols, z);

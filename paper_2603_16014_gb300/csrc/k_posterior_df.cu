@@ -25,7 +25,7 @@
 #include <cstring>
 
 #include "mtgp_internal.cuh"
-#include "df64.cuh"
+#include "kernel_df.cuh"
 
 namespace {
 
@@ -39,27 +39,6 @@ struct PdParams {
     int colidx[MTGP_TMAX][MTGP_TMAX];
     long long coloff[MTGP_MAX_COLS];
 };
-
-// v exactly as a float for |v| < 2^22: the bias 2^23 + 2^22 puts v into the mantissa field
-__device__ __forceinline__ float small_int_float(int v) { return __int_as_float(0x4B400000 + v) - 12582912.0f; }
-
-// 2^33 K(X / 2^32) for the order-2 DSI kernel: 3 2^32 - 2 b X - 5 2^(32 - b), b = clz(X) + 1, and 3 2^32
-// at X = 0 (K(0) = 3/2).  |.| < 2^34; split as 2^20 Ih + Il (|Ih| < 2^14, 0 <= Il < 2^20), both exact
-// floats, and joined by TwoSum: the double-float value is exact.
-__device__ __forceinline__ df dsi2_scaled_df(uint32_t X) {
-    const int b = __clz(X) + 1;
-    const long long t5 = X ? (5LL << (b <= 32 ? 32 - b : 0)) : 0LL;
-    const long long I = (3LL << 32) - 2LL * (long long)b * (long long)X - t5;
-    const int ih = (int)(I >> 20), il = (int)(I & 0xFFFFFLL);
-    return two_sum(small_int_float(ih) * 1048576.0f, small_int_float(il));
-}
-
-// 1 + t for a double-float t
-__device__ __forceinline__ df df_one_plus(df t) {
-    df s = two_sum(1.0f, t.hi);
-    s.lo = __fadd_rn(s.lo, t.lo);
-    return fast_two_sum(s.hi, s.lo);
-}
 
 // Q(x, x') = prod_j (1 + eta_j K(X_j)) from the XORed words X_j = x_j XOR x'_j, with es_j = eta_j 2^-33 (the
 // scale of dsi2_scaled_df)
