@@ -36,7 +36,7 @@ L2_FLUSH_BYTES = 256 << 20
 # sources whose kernels a profile summary's DRAM traffic figure describes
 KERNEL_SOURCES = ["paper_2603_16014_gb300/csrc/" + f for f in
                   ("k_fused_rt.cu", "k_fused.cu", "fused_common.cuh", "freq_solve.cuh", "df64.cuh", "butterfly.cuh",
-                   "mtgp_internal.cuh")]
+                   "mtgp_internal.cuh", "kernel_df.cuh")]
 
 
 def parse():
