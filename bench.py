@@ -1257,6 +1257,9 @@ def proposal_measure(train_fits, label_steps, train_steps, eval_fits, eval_steps
         "ms_per_batched_step": step_ms, "proposal_overhead_ms": prop_ms,
         "plain_converged_fraction": float(np.mean(converged(plain[:, valid], max(S // 10, 10)))),
         "unreached": unreached_summary(prop[:, valid], target[valid], reached, max(S // 10, 10)),
+        "by_choice": ({str(k): {"fits": int(np.sum(chosen[valid] == k)),
+                               "reached_fraction": float(reached[chosen[valid] == k].mean())}
+                       for k in range(5) if np.any(chosen[valid] == k)} if chosen is not None else None),
         "by_kind": {kd: {"fits": int(np.sum(kinds[valid] == kd)),
                          "reached_fraction": float(reached[kinds[valid] == kd].mean()),
                          "faster_fraction": float(faster[kinds[valid] == kd].mean()),
