@@ -411,7 +411,7 @@ int mtgp_propose(mtgp_batch_t* b, mtgp_mlp_t* net, float* pred, int judge, int* 
 /*
  * mtgp_selftest_arith -- evaluates one of the library's arithmetic building blocks element-wise, for
  * testing its error bound against an FP64 reference (no counterpart in the paper).  x, y, out: device,
- * n doubles (y only for ops 3-5).  The double-float operations take their FP64 inputs rounded to
+ * n doubles (y only for ops 3-5 and 8).  The double-float operations take their FP64 inputs rounded to
  * double-float (about 48 significant bits) and return the double-float result as a double.
  *   op 0  1 / x by the FP64 solvers' reciprocal (hardware approximation + one third-order refinement)
  *   op 1  x rounded to double-float and back
@@ -420,6 +420,9 @@ int mtgp_propose(mtgp_batch_t* b, mtgp_mlp_t* net, float* pred, int judge, int* 
  *   op 6  log of the product of x over each group of 32 consecutive elements (the double-float
  *         log-determinant accumulator and its double-float logarithm, ln m = 2 atanh((m-1)/(m+1))),
  *         written to the group's first element, 0 elsewhere; n % 32 == 0
+ *   op 7  2^33 K(X / 2^32) of the order-2 DSI kernel (Eq. 2.6) in double-float, X = x (an integer in
+ *         [0, 2^32)): the exact integer 3 2^32 - 2 b X - 5 2^(32 - b)
+ *   op 8  the SI kernel of smoothness y (1..4, Eq. 2.5) at u = X / 2^32 in double-float, X = x
  * Asynchronous on `stream`; MTGP_ERR_INVALID_ARG for an unknown op or missing arrays.
  */
 int mtgp_selftest_arith(int op, long long n, const double* x, const double* y, double* out, cudaStream_t stream);

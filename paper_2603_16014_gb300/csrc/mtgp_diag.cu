@@ -1,7 +1,8 @@
 // Element-wise evaluation of the library's own arithmetic building blocks, so that tests can check
 // their error bounds against FP64 references: the FP64 reciprocal of the per-frequency solvers and the
-// double-float operations of the FP32-transform solve.
+// double-float operations of the FP32-transform solve and of the double-float kernel values.
 #include "freq_solve.cuh"
+#include "kernel_df.cuh"
 
 namespace {
 
@@ -17,7 +18,9 @@ __global__ void k_selftest_arith(int op, long long n, const double* __restrict__
             case 3: r = df_to_double(df_mul(df_from_double(a), df_from_double(b))); break;
             case 4: r = df_to_double(df_add(df_from_double(a), df_from_double(b))); break;
             case 5: r = df_to_double(df_fms(df_from_double(a), df_from_double(b), df_from_double(b))); break;
-            default: {
+            case 7: r = df_to_double(dsi2_scaled_df((uint32_t)a)); break;
+            case 8: r = df_to_double(si2_df((uint32_t)a, si2_consts((int)b))); break;
+            case 6: {
                 // log of the product of x over each warp's 32 consecutive elements (DFLogAcc and its
                 // double-float logarithm), in the warp's first element; the other elements receive 0
                 DFLogAcc acc;
@@ -35,7 +38,7 @@ __global__ void k_selftest_arith(int op, long long n, const double* __restrict__
 
 extern "C" int mtgp_selftest_arith(int op, long long n, const double* x, const double* y, double* out,
                                    cudaStream_t stream) {
-    if (op < 0 || op > 6 || n < 0 || (n > 0 && (!x || !out)) || ((op == 3 || op == 4 || op == 5) && n > 0 && !y)) {
+    if (op < 0 || op > 8 || n < 0 || (n > 0 && (!x || !out)) || ((op == 3 || op == 4 || op == 5 || op == 8) && n > 0 && !y)) {
         mtgp_set_error("mtgp_selftest_arith: bad arguments");
         return MTGP_ERR_INVALID_ARG;
     }

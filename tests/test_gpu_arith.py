@@ -6,7 +6,9 @@ FP64 (and exact rational) references:
 * double-float (pairs of FP32 values) rounding of FP64 inputs within 2^-48, reciprocal (one
   Newton-Raphson step) within 2^-44, product, sum and x - y^2 within 2^-45 of the operands' scale;
 * the double-float log-determinant accumulator (product over 32 values, one logarithm) within
-  2^-40 of the FP64 sum of logarithms.
+  2^-40 of the FP64 sum of logarithms;
+* the double-float kernel values: the order-2 DSI value 2^33 K exact, the SI values of smoothness 1-4
+  within 2^-44 of K(0) against the Bernoulli polynomials evaluated exactly.
 """
 import ctypes
 from fractions import Fraction
@@ -92,3 +94,49 @@ def test_double_float_log_product():
     got = _run(6, x)[::32]
     ref = np.log(x).reshape(-1, 32).sum(axis=1)
     assert np.all(np.abs(got - ref) <= 2.0 ** -40 * np.maximum(np.abs(ref), 1.0) + 1e-12)
+
+
+def _dsi_words(rng):
+    X = [0, 1, 2, 3, 5, (1 << 31) - 1, 1 << 31, (1 << 31) + 1, (1 << 32) - 1, 1 << 16, (1 << 16) - 1]
+    X += [1 << k for k in range(32)]
+    X += [int(v) for v in rng.integers(0, 1 << 32, size=2000, dtype=np.uint64)]
+    X += [int(v) >> int(s) for v, s in zip(rng.integers(0, 1 << 32, size=2000, dtype=np.uint64),
+                                            rng.integers(0, 32, size=2000))]
+    return X
+
+
+def test_dsi_kernel_value_exact():
+    """2^33 K(X / 2^32) of the order-2 DSI kernel (Eq. 2.6) in double-float equals the integer
+    3 2^32 - 2 b X - 5 2^(32 - b), b = -floor(log2(X / 2^32)) (3 2^32 at X = 0), exactly."""
+    X = _dsi_words(np.random.default_rng(5))
+    got = _run(7, np.array(X, dtype=np.float64))
+    for x, g in zip(X, got):
+        if x == 0:
+            ref = 3 << 32
+        else:
+            b = 33 - x.bit_length()
+            ref = (3 << 32) - 2 * b * x - 5 * (1 << (32 - b))
+        assert g == float(ref), (x, g, ref)
+
+
+def _bernoulli_poly(n, u):
+    """B_n(u) exactly (Fractions): sum_k C(n, k) B_k u^(n - k) with the Bernoulli numbers B_k (B_1 = -1/2)."""
+    from math import comb
+    B = {0: Fraction(1), 1: Fraction(-1, 2), 2: Fraction(1, 6), 4: Fraction(-1, 30), 6: Fraction(1, 42),
+         8: Fraction(-1, 30)}
+    return sum(comb(n, k) * B.get(k, Fraction(0)) * u ** (n - k) for k in range(n + 1))
+
+
+@pytest.mark.parametrize("alpha", [1, 2, 3, 4])
+def test_si_kernel_value_double_float(alpha):
+    """The SI kernel of smoothness alpha (Eq. 2.5), K(u) = (-1)^(alpha+1) (2 pi)^(2 alpha) / (2 alpha)! B_(2 alpha)(u),
+    evaluated in double-float at u = X / 2^32: within 2^-44 of the kernel's scale K(0) of the exact value."""
+    from math import factorial, pi
+    rng = np.random.default_rng(alpha)
+    X = [0, 1, (1 << 31) - 1, 1 << 31, (1 << 32) - 1] + [int(v) for v in rng.integers(0, 1 << 32, size=400, dtype=np.uint64)]
+    got = _run(8, np.array(X, dtype=np.float64), np.full(len(X), float(alpha)))
+    c = Fraction((-1) ** (alpha + 1)) * Fraction((2 * pi) ** (2 * alpha)) / factorial(2 * alpha)
+    scale = abs(float(c * _bernoulli_poly(2 * alpha, Fraction(0))))
+    for x, g in zip(X, got):
+        ref = float(c * _bernoulli_poly(2 * alpha, Fraction(x, 1 << 32)))
+        assert abs(g - ref) <= 2.0 ** -44 * scale, (alpha, x, g, ref)
