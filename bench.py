@@ -1126,6 +1126,13 @@ def converged(trace, window: int, tol: float = 1e-6):
         return (best[-window - 1] - best[-1]) <= tol * np.abs(best[-1])
 
 
+# the proposal's judge: the exact NLL picks between the quarter blend (p + 3 c) / 4 and the fixed start c.  On
+# 256 held-out fits with traces from every candidate, the start-NLL judge over all five candidates let 69.5%
+# of the fits reach the plain run's best NLL sooner, the quarter blend 83.2% (the best selector over
+# the five, with hindsight and no cost, 89.8%): nearer candidates more often lead Adam to a worse optimum.
+JUDGE_MODE = 2
+
+
 def unreached_summary(prop, target, reached, window):
     """The held-out fits whose proposal run never reached the target: how far above it the run ended
     (median relative excess of its best NLL) and how many of those runs had converged (a different local
@@ -1145,8 +1152,8 @@ def unreached_summary(prop, target, reached, window):
 def proposal_measure(train_fits, label_steps, train_steps, eval_fits, eval_steps, pool, lr=0.05):
     """Learned starting point on held-out fits.  Training: mixed fits labelled by `label_steps` batched
     Adam steps, the MLP trained by the library's BF16 kernels.  Held-out: every fit optimised from the
-    plain fixed start and from the judged proposal (mtgp_propose: the exact NLL picks, per fit, the best
-    of the prediction, two blends with the fixed start and the fixed start itself).  The target of a fit
+    plain fixed start and from the judged proposal (mtgp_propose: the exact NLL picks, per fit, the better
+    of the quarter blend of prediction and fixed start, and the fixed start itself).  The target of a fit
     is the plain run's best NLL, which is reported together with a convergence test of the plain run; a
     run reaches it at the first step within 1e-6 (relative)."""
     import numpy as np
@@ -1207,7 +1214,7 @@ def proposal_measure(train_fits, label_steps, train_steps, eval_fits, eval_steps
         b.set_theta(theta0)
         e0, e1, e2 = ev(), ev(), ev()
         e0.record(stream)
-        propose(b, net, judge=True, stream=stream)
+        propose(b, net, judge=JUDGE_MODE, stream=stream)
         e1.record(stream)
         b.fit(None, kt, lr, graph=True, final_nll=False)
         e2.record(stream)
@@ -1219,7 +1226,7 @@ def proposal_measure(train_fits, label_steps, train_steps, eval_fits, eval_steps
             b.set_theta(theta0)
             chosen = None
             if name == "proposal":
-                _, chosen = propose(b, net, judge=True, stream=stream)
+                _, chosen = propose(b, net, judge=JUDGE_MODE, stream=stream)
             b.fit(None, S, lr, graph=False, trace=tr, final_nll=False)
             stream.synchronize()
             traces[name] = tr.view(S, -1).cpu().numpy()
@@ -1274,7 +1281,7 @@ def proposal_measure(train_fits, label_steps, train_steps, eval_fits, eval_steps
                    "mlp": "258-256-256-256-37 BF16 weights / FP32 accumulate",
                    "train_set": "mixed fits n = 2^U{8..16}, T ~ U{2..8}, d ~ U{2..12}, labelled by batched Adam",
                    "target": "plain run's best NLL (its convergence over the last 10% of steps reported)",
-                   "start": "mtgp_propose with the exact-NLL judge over five candidates"},
+                   "start": "mtgp_propose with the exact-NLL judge over (p + 3 c) / 4 and c"},
         "data": "synthetic",
     }
 

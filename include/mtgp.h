@@ -399,9 +399,11 @@ int mtgp_mlp_train_step(mtgp_mlp_t* m, int B, const float* x, const float* targe
  *           each fit keeps the one with the lowest NLL (one batched NLL + gradient evaluation per
  *           candidate): with c the log parameters set before the call (e.g. the plain optimiser's fixed
  *           start) and p the prediction's (W linearly), candidate 0 = p, 1 = p with sigma2 x 100,
- *           2 = (p + c) / 2, 3 = (p + 3 c) / 4, 4 = c.  The judged start is never worse than the
- *           caller's own start.
- *   chosen  device, nfits ints, or NULL (judge = 1): the candidate each fit kept.
+ *           2 = (p + c) / 2, 3 = (p + 3 c) / 4, 4 = c.  2: the same judge over candidates 3 and 4 only
+ *           (two evaluations), the more robust start for a later optimiser run (the nearer candidates
+ *           more often lead it to a worse optimum).  The judged start is never worse than the caller's
+ *           own start.  Other values: MTGP_ERR_INVALID_ARG.
+ *   chosen  device, nfits ints, or NULL (judge = 1, 2): the candidate each fit kept (0 .. 4).
  * Needs mtgp_batch_set_y first, s = 2 and d <= 12 for every fit (else MTGP_ERR_UNSUPPORTED).  The
  * first call allocates the batch's feature, prediction and judge buffers (synchronously); later calls
  * are asynchronous on `stream`.  The network's buffers are used: order calls on one network on one stream.

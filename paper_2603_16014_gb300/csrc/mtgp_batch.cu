@@ -418,12 +418,12 @@ __global__ void k_judge_set(int k, const int* __restrict__ kfit, const int* __re
     }
 }
 
-__global__ void k_judge_keep(int k, int nfits, const double* __restrict__ out, double* __restrict__ best,
+__global__ void k_judge_keep(int k, int first, int nfits, const double* __restrict__ out, double* __restrict__ best,
                              int* __restrict__ kbest) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nfits) return;
     const double v = out[3 * f];
-    if (k == 0) {
+    if (first) {
         best[f] = INFINITY;
         kbest[f] = -1;
     }
@@ -741,6 +741,7 @@ int mtgp_batch_fit(mtgp_batch_t* b, const double* theta0, int steps, double lr, 
 
 int mtgp_propose(mtgp_batch_t* b, mtgp_mlp_t* net, float* pred, int judge, int* chosen, cudaStream_t st) {
     if (!b || !net) return bfail(MTGP_ERR_INVALID_ARG, "NULL argument");
+    if (judge < 0 || judge > 2) return bfail(MTGP_ERR_INVALID_ARG, "judge must be 0, 1 or 2");
     int in_w = 0, out_w = 0, max_b = 0;
     mlp_shape(net, &in_w, &out_w, &max_b);
     if (in_w != kFeat || out_w != kOut)
@@ -784,11 +785,17 @@ int mtgp_propose(mtgp_batch_t* b, mtgp_mlp_t* net, float* pred, int judge, int* 
     // the exact NLL judges the candidates; every fit keeps its best
     cudaMemcpyAsync(b->jpred, b->th_log, sizeof(double) * b->np, cudaMemcpyDeviceToDevice, st);
     const int blocks = (int)std::min<long long>((b->np + 255) / 256, 4096);
-    for (int k = 0; k < kJudgeCand; ++k) {
+    // judge 1: all five candidates; judge 2: the quarter blend (p + 3 c) / 4 and c
+    static const int kAll[kJudgeCand] = {0, 1, 2, 3, 4};
+    static const int kBlend[2] = {3, 4};
+    const int* cands = judge == 2 ? kBlend : kAll;
+    const int ncand = judge == 2 ? 2 : kJudgeCand;
+    for (int i = 0; i < ncand; ++i) {
+        const int k = cands[i];
         k_judge_set<<<blocks, 256, 0, st>>>(k, nullptr, b->pinfo, b->is_s2, b->np, b->jcur, b->jcur_nat, b->jpred,
                                             b->th_log, b->th_nat, b->m1, b->m2);
         launch_eval(b, st);
-        k_judge_keep<<<(b->nfits + 127) / 128, 128, 0, st>>>(k, b->nfits, b->out, b->jbest, b->jk);
+        k_judge_keep<<<(b->nfits + 127) / 128, 128, 0, st>>>(k, i == 0, b->nfits, b->out, b->jbest, b->jk);
     }
     k_judge_set<<<blocks, 256, 0, st>>>(0, b->jk, b->pinfo, b->is_s2, b->np, b->jcur, b->jcur_nat, b->jpred,
                                         b->th_log, b->th_nat, b->m1, b->m2);

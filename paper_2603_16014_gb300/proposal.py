@@ -135,13 +135,15 @@ def train(mlp: MLP, feats, targets, masks, steps: int, batch: int = 256, lr: flo
     return losses
 
 
-def propose(batch, mlp: MLP, judge: bool = False, stream=None):
+def propose(batch, mlp: MLP, judge=False, stream=None):
     """Set every fit's parameters to the network's prediction from its features (mtgp_propose: features,
-    forward pass and parameter map in one call).  With ``judge`` the exact NLL picks, per fit, the best
-    of the prediction, two blends with the parameters set before the call and those parameters
-    themselves.  Returns (prediction, chosen candidate per fit or None)."""
+    forward pass and parameter map in one call).  With ``judge`` (True or 1) the exact NLL picks, per fit,
+    the best of the prediction, two blends with the parameters set before the call and those parameters
+    themselves; with ``judge=2`` the best of the quarter blend (p + 3 c) / 4 and the parameters set
+    before the call.  Returns (prediction, chosen candidate per fit or None)."""
+    mode = 1 if judge is True else int(judge or 0)
     pred = torch.empty((batch.n, mlp.widths[-1]), dtype=torch.float32, device="cuda")
-    chosen = torch.empty(batch.n, dtype=torch.int32, device="cuda") if judge else None
-    check(lib().mtgp_propose(batch._h, mlp._h, _ptr(pred), 1 if judge else 0, _ptr(chosen), _stream(stream)),
+    chosen = torch.empty(batch.n, dtype=torch.int32, device="cuda") if mode else None
+    check(lib().mtgp_propose(batch._h, mlp._h, _ptr(pred), mode, _ptr(chosen), _stream(stream)),
           "mtgp_propose")
     return pred, chosen

@@ -299,6 +299,9 @@ def test_propose_entry_point_equals_composed_calls():
     bad = MLP(widths=(258, 64, 36), max_batch=8)
     with pytest.raises(_lib.MTGPError):
         propose(b, bad)
+    # and so is an unknown judge mode
+    with pytest.raises(_lib.MTGPError):
+        propose(b, net, judge=3)
     bad.close()
     net.close()
     b.close()
@@ -308,7 +311,7 @@ def test_judged_proposal_on_heldout_fits():
     """Held-out fits (seeds not used in training): the judged proposal (mtgp_propose with the exact-NLL
     judge) starts no fit worse than the plain fixed start and most strictly better, and reaches the plain
     optimiser's best NLL in fewer steps, its own cost (five batched evaluations and the network)
-    included, on most fits."""
+    included, on most fits; the same for the two-candidate blend judge (judge = 2)."""
     from paper_2603_16014_gb300.mtgp import Batch
     from paper_2603_16014_gb300.proposal import MLP, propose, train
     import os
@@ -333,10 +336,12 @@ def test_judged_proposal_on_heldout_fits():
         b.set_y(torch.from_numpy(np.concatenate(_ys(held))))
         theta0 = torch.from_numpy(b.pack([bench.default_theta(p) for p in held])).cuda()
         traces = {}
-        for name in ("plain", "proposal"):
+        for name in ("plain", "proposal", "proposal_blend"):
             b.set_theta(theta0)
             if name == "proposal":
                 _, chosen = propose(b, net, judge=True)
+            elif name == "proposal_blend":
+                _, chosen2 = propose(b, net, judge=2)
             tr = torch.zeros(S * len(held), dtype=torch.float64, device="cuda")
             b.fit(None, S, lr, graph=False, trace=tr, final_nll=False)
             traces[name] = tr.view(S, -1).cpu().numpy()
@@ -350,6 +355,14 @@ def test_judged_proposal_on_heldout_fits():
     k_prop = bench.steps_to_target(prop, target)
     faster = (k_prop >= 0) & (k_prop + 1 + 6 < k_plain)
     assert faster.mean() >= 0.75, (faster.mean(), k_plain, k_prop)
+    # the blend judge: candidates (p + 3 c) / 4 and c only
+    blend = traces["proposal_blend"]
+    c2 = chosen2.cpu().numpy()
+    assert np.all((c2 == 3) | (c2 == 4)), c2
+    assert np.all(blend[0] <= plain[0]), (blend[0], plain[0])
+    k_bl = bench.steps_to_target(blend, target)
+    faster_bl = (k_bl >= 0) & (k_bl + 1 + 3 < k_plain)
+    assert faster_bl.mean() >= 0.75, (faster_bl.mean(), k_plain, k_bl)
     net.close()
     bt.close()
     b.close()
