@@ -111,27 +111,45 @@ class MLP:
 
 
 def train(mlp: MLP, feats, targets, masks, steps: int, batch: int = 256, lr: float = 1e-3, seed: int = 0,
-          lr_final: float = 1e-4, stream=None) -> torch.Tensor:
+          lr_final: float = 1e-4, stream=None, val_fraction: float = 0.0, eval_every: int = 100) -> torch.Tensor:
     """Adam on minibatches drawn by seeded epoch permutations; returns the per-step losses (device).
 
     The learning rate decays geometrically from lr to lr_final.  Input scaling comes from the
-    training features.
+    training features.  With ``val_fraction`` > 0 a seeded share of the rows is held out: every
+    ``eval_every`` steps the masked loss on it (mtgp_mlp_gradients) is taken, and the network ends with
+    the parameters of the lowest held-out loss (early stopping: the network otherwise overfits the
+    few thousand labelled fits, and its proposals for unseen fits get worse).
     """
     feats = _dev(feats, torch.float32)
     targets = _dev(targets, torch.float32)
     masks = _dev(masks, torch.float32)
     n = feats.shape[0]
-    batch = min(batch, n, mlp.max_batch)
     rng = np.random.default_rng(seed)
+    idx = np.arange(n)
+    val = None
+    if val_fraction > 0.0:
+        perm = rng.permutation(n)
+        nv = min(max(1, int(round(val_fraction * n))), mlp.max_batch, n - 1)
+        val = torch.as_tensor(np.sort(perm[:nv]).astype(np.int32)).cuda()
+        idx = np.sort(perm[nv:])
+    batch = min(batch, len(idx), mlp.max_batch)
     order = []
     while len(order) < steps * batch:
-        order.extend(rng.permutation(n).tolist())
+        order.extend(idx[rng.permutation(len(idx))].tolist())
     rows = torch.as_tensor(np.asarray(order[:steps * batch], dtype=np.int32)).cuda()
     losses = torch.zeros(steps, dtype=torch.float32, device="cuda")
     mlp.fit_scaling(feats, stream)
     decay = (lr_final / lr) ** (1.0 / max(steps - 1, 1))
+    best, best_params = np.inf, None
     for k in range(steps):
         mlp.train_step(feats, targets, masks, rows[k * batch:(k + 1) * batch], lr * decay ** k, losses[k:k + 1], stream)
+        if val is not None and ((k + 1) % eval_every == 0 or k == steps - 1):
+            vl, _ = mlp.gradients(feats, targets, masks, rows=val, stream=stream)
+            v = float(vl.item())
+            if v < best:
+                best, best_params = v, mlp.get_params()
+    if best_params is not None:
+        mlp.set_params(*best_params)
     return losses
 
 
