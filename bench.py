@@ -1194,7 +1194,8 @@ def proposal_measure(train_fits, label_steps, train_steps, eval_fits, eval_steps
     with torch.cuda.stream(stream):
         e0, e1 = ev(), ev()
         e0.record(stream)
-        losses = train(net, X, Y, M, steps=train_steps, batch=min(256, X.shape[0]), lr=1e-3, seed=1, lr_final=3e-5)
+        losses = train(net, X, Y, M, steps=train_steps, batch=min(256, X.shape[0]), lr=1e-3, seed=1, lr_final=3e-5,
+                       val_fraction=0.1)
         e1.record(stream)
         stream.synchronize()
     t_train = e0.elapsed_time(e1) / 1e3
@@ -1278,7 +1279,8 @@ def proposal_measure(train_fits, label_steps, train_steps, eval_fits, eval_steps
                   "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-50:].mean())},
         "config": {"workload": "proposal_heldout", "eval_fits": len(probs), "T": 4, "n": 65536, "d": 8,
                    "kinds": "half lattice (FP64), half digital net (FP32 transforms)", "eval_steps": S, "lr": lr,
-                   "mlp": "258-256-256-256-37 BF16 weights / FP32 accumulate",
+                   "mlp": "258-256-256-256-37 BF16 weights / FP32 accumulate, early stopping on 10% held-out "
+                          "training fits",
                    "train_set": "mixed fits n = 2^U{8..16}, T ~ U{2..8}, d ~ U{2..12}, labelled by batched Adam",
                    "target": "plain run's best NLL (its convergence over the last 10% of steps reported)",
                    "start": "mtgp_propose with the exact-NLL judge over (p + 3 c) / 4 and c"},
