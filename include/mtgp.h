@@ -46,7 +46,7 @@ enum {
     MTGP_ERR_NOT_PD = 2,       /* a pivot / Schur complement <= 0 (Lambda not HPD numerically) */
     MTGP_ERR_NUMERIC = 3,      /* NaN or Inf in an input or an intermediate                */
     MTGP_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up                       */
-    MTGP_ERR_UNSUPPORTED = 5,  /* valid request outside what this build implements         */
+    MTGP_ERR_UNSUPPORTED = 5,  /* valid request outside what the library implements        */
     MTGP_ERR_CUDA = 6,         /* a CUDA runtime call failed                               */
     MTGP_ERR_STATE = 7         /* call order violated (e.g. NLL before mtgp_set_y)         */
 };
@@ -62,7 +62,7 @@ enum { MTGP_NOISE_PER_TASK = 16 };
  * frequency whose pivots leave the double-float range is solved in FP64); every other solve is FP64. */
 enum { MTGP_SOLVE_FP64 = 32 };
 
-/* Limits of this build. */
+/* Limits of the library. */
 #define MTGP_MAX_TASKS 8
 #define MTGP_MAX_M 24      /* n_t <= 2^24 */
 #define MTGP_MAX_DIM 32

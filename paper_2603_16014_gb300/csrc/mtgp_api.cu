@@ -803,7 +803,7 @@ int mtgp_gcv_grad(mtgp_t* hs, const double* eta, const double* W, int s, const d
                   cudaStream_t st) {
     if (!hs || !out || !g_eta || !g_W || !g_v || !g_sigma2) return fail(MTGP_ERR_INVALID_ARG, "NULL argument");
     Handle* h = &hs->h;
-    if (!h->equal) return fail(MTGP_ERR_UNSUPPORTED, "the GCV gradient needs equal task sizes in this build");
+    if (!h->equal) return fail(MTGP_ERR_UNSUPPORTED, "the GCV gradient needs equal task sizes");
     int rc = validate_theta(h, eta, W, s, v, sigma2);
     if (rc) return rc;
     if (!h->y_set) return fail(MTGP_ERR_STATE, "mtgp_set_y must be called first");
