@@ -118,7 +118,8 @@ def train(mlp: MLP, feats, targets, masks, steps: int, batch: int = 256, lr: flo
     training features.  With ``val_fraction`` > 0 a seeded share of the rows is held out: every
     ``eval_every`` steps the masked loss on it (mtgp_mlp_gradients) is taken, and the network ends with
     the parameters of the lowest held-out loss (early stopping: the network otherwise overfits the
-    few thousand labelled fits, and its proposals for unseen fits get worse).
+    few thousand labelled fits, and its proposals for unseen fits get worse).  The held-out rows and
+    the (step, loss) history stay on the network as ``val_rows`` and ``val_history``.
     """
     feats = _dev(feats, torch.float32)
     targets = _dev(targets, torch.float32)
@@ -141,11 +142,13 @@ def train(mlp: MLP, feats, targets, masks, steps: int, batch: int = 256, lr: flo
     mlp.fit_scaling(feats, stream)
     decay = (lr_final / lr) ** (1.0 / max(steps - 1, 1))
     best, best_params = np.inf, None
+    mlp.val_rows, mlp.val_history = val, []
     for k in range(steps):
         mlp.train_step(feats, targets, masks, rows[k * batch:(k + 1) * batch], lr * decay ** k, losses[k:k + 1], stream)
         if val is not None and ((k + 1) % eval_every == 0 or k == steps - 1):
             vl, _ = mlp.gradients(feats, targets, masks, rows=val, stream=stream)
             v = float(vl.item())
+            mlp.val_history.append((k + 1, v))
             if v < best:
                 best, best_params = v, mlp.get_params()
     if best_params is not None:

@@ -366,3 +366,32 @@ def test_judged_proposal_on_heldout_fits():
     net.close()
     bt.close()
     b.close()
+
+
+def test_training_early_stopping_keeps_lowest_held_out_loss():
+    """proposal.train with a held-out share: the held-out rows are not trained on, and the network ends
+    with the parameters whose held-out loss is the lowest of the checkpoints."""
+    from paper_2603_16014_gb300.mtgp import Batch
+    from paper_2603_16014_gb300.proposal import MLP, train
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    fits = _fits(23, 48)
+    b = Batch(fits, s=2, precision="auto")
+    b.set_y(torch.from_numpy(np.concatenate(_ys(fits))))
+    th0 = torch.from_numpy(b.pack([bench.default_theta(p) for p in fits])).cuda()
+    b.fit(th0, 100, 0.05, graph=True, final_nll=False)
+    tg, mk = b.targets()
+    feats = b.features()
+    net = MLP(max_batch=64)
+    net.set_params(net.init_params(0))
+    train(net, feats, tg, mk, steps=600, batch=16, lr=3e-3, seed=2, lr_final=1e-3, val_fraction=0.25, eval_every=50)
+    val = net.val_rows.cpu().numpy()
+    assert len(val) == 12 and len(np.unique(val)) == 12
+    hist = net.val_history
+    assert [s for s, _ in hist] == list(range(50, 601, 50))
+    vl, _ = net.gradients(feats, tg, mk, rows=net.val_rows)
+    assert float(vl.item()) == min(v for _, v in hist), (float(vl.item()), hist)
+    net.close()
+    b.close()
