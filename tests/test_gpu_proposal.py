@@ -381,7 +381,7 @@ def test_training_early_stopping_keeps_lowest_held_out_loss():
     b = Batch(fits, s=2, precision="auto")
     b.set_y(torch.from_numpy(np.concatenate(_ys(fits))))
     th0 = torch.from_numpy(b.pack([bench.default_theta(p) for p in fits])).cuda()
-    b.fit(th0, 100, 0.05, graph=True, final_nll=False)
+    b.fit(th0, 100, 0.05, graph=False, final_nll=False)
     tg, mk = b.targets()
     feats = b.features()
     net = MLP(max_batch=64)
