@@ -138,3 +138,27 @@ def test_spectral_mixture_gradient_matches_dense():
     got = np.concatenate([ge, gW.ravel(), gv, [gs], gb])
     exp = np.concatenate([re, rW.ravel(), rv, [rs], rb])
     assert np.allclose(got, exp, rtol=1e-8, atol=1e-9 * np.abs(exp).max())
+
+
+def test_dsi_order2_is_exact_dyadic():
+    """Eq. 2.6, order 2: with x = X / 2^32 and beta = -floor(log2 x), 2^33 K_2(x) = 2^33 (-1 - beta x +
+    5/2 (1 - 2^-beta)) = 3 2^32 - 2 beta X - 5 2^(32 - beta), an integer below 2^34 (3 2^32 at X = 0); the
+    oracle's floating-point evaluation agrees with it to FP64 rounding at every tested word (this exact form
+    is what lets the kernels evaluate K_2 without rounding)."""
+    import numpy as np
+    from oracle import design
+    rng = np.random.default_rng(9)
+    X = np.concatenate([[0, 1, 2, 3, (1 << 31) - 1, 1 << 31, (1 << 32) - 1],
+                        [1 << k for k in range(32)],
+                        rng.integers(0, 1 << 32, size=5000, dtype=np.uint64),
+                        rng.integers(0, 1 << 32, size=5000, dtype=np.uint64) >> rng.integers(0, 32, size=5000).astype(np.uint64)])
+    X = X.astype(np.uint64)
+    k = design.dsi_kernel_1d(X, alpha=2)
+    for x, kv in zip(X.tolist(), k.tolist()):
+        if x == 0:
+            exact = 3 << 32
+        else:
+            b = 33 - int(x).bit_length()
+            exact = (3 << 32) - 2 * b * int(x) - 5 * (1 << (32 - b))
+        assert abs(exact) < 1 << 34
+        assert abs(kv * 2.0 ** 33 - exact) <= 4.0 * 2.0 ** 33 * 2.0 ** -52, (x, kv, exact)
