@@ -338,6 +338,28 @@ def cpu_baseline(seconds: float = 10.0):
             "sample": f"{reps} full NLL+gradient evaluations of {WORKLOAD} (FP64 numpy spectral oracle), {el:.1f} s"}
 
 
+def dense_oracle_scaling(sizes=((2, 10), (2, 11), (2, 12))):
+    """The dense oracle (Gram matrix, Cholesky, FP64 numpy) on the host cores: NLL of the d = 2 lattice fit of
+    the small configuration at N = 2048 and of the same shape at N = 4096 and 8192, with the cubic
+    extrapolation to the benchmark fit's N = 262,144 (labelled as such: its Gram matrix alone would take
+    550 GB)."""
+    from oracle import dense
+    from paper_2603_16014_gb300 import inputs
+
+    rows = []
+    for T, m in sizes:
+        p = inputs.make_problem("lattice", 2, (m,) * T, seed=0, eta=0.5, v=0.1, sigma2=1e-6)
+        X = dense.all_points(p.kind, p.gen, p.shift, p.m)
+        y = inputs.synth_y(p, X)
+        t0 = time.perf_counter()
+        dense.nll(p.kind, X, y, p.eta, p.W, p.v, p.sigma2)
+        rows.append({"N": T << m, "nll_seconds": time.perf_counter() - t0})
+    big = rows[-1]
+    return {"runs": rows, "cores": os.cpu_count(),
+            "extrapolated_nll_seconds_at_N_262144": big["nll_seconds"] * (262144 / big["N"]) ** 3,
+            "note": "dense NLL only (no gradient); the N = 262,144 figure is a cubic extrapolation"}
+
+
 # ----------------------------------------------------------------------------- replicas
 
 def max_over_ranks(local_ms: float, dist, device: str) -> float:
@@ -484,6 +506,7 @@ def run_ours(args, rank, world, local_rank):
                                      "batched FP64 cholesky_ex, autograd gradient"}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"]["dense_oracle"] = dense_oracle_scaling()
     if world == 1 and not args.no_extras and pool is not None:
         # the other workloads of the method, each timed on the device (reduced proposal pipeline)
         del outs, flush
