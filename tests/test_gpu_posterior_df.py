@@ -63,3 +63,32 @@ def test_posterior_df_per_task_noise():
     assert np.all(np.abs(mean_only - mean_ref) <= scale)
     assert np.all(np.abs(mean - mean_ref) <= scale)
     assert np.all(np.abs(var - var_ref) <= scale)
+
+
+@pytest.mark.parametrize("m", [12, 14, 15, 18])
+def test_posterior_df_other_splits_vs_spectral_oracle(m):
+    """The other register-tile splits of the double-float posterior (n = 2^12: a = 5 and 7 high bits,
+    2^14: 6 and 8, 2^15: 7 and 8, 2^18: 9 and 9; 2^10, 2^11 and 2^16 are covered above), sampled mean and
+    variance against the per-frequency oracle."""
+    from oracle import spectral
+    from paper_2603_16014_gb300.mtgp import MTGP
+    d, T = 4, 2
+    p = inputs.make_problem("dnet", d, (m,) * T, seed=200 + m, eta=0.6, v=0.1, sigma2=1e-4,
+                            recipe="walshcos32", mmax=m)
+    X = dense.all_points(p.kind, p.gen, p.shift, p.m)
+    y = inputs.synth_y(p, X)
+    Xq, xq, tq = inputs.query_points(40, d, seed=m, tasks=T)
+    model = MTGP.from_problem(p, "fp32")
+    model.set_y(torch.from_numpy(y))
+    mean, var = model.posterior(p.eta, p.W, p.v, p.sigma2, torch.from_numpy(xq), torch.from_numpy(tq), variance=True)
+    model.sync()
+    model.close()
+    mean, var = mean.cpu().numpy(), var.cpu().numpy()
+    pick = np.array([0, 17, 39])
+    mref = spectral.posterior_mean_equal(p.kind, p.gen, p.shift, p.m, y, p.eta, p.W, p.v, p.sigma2, Xq[pick], tq[pick])
+    vref = spectral.posterior_var_equal(p.kind, p.gen, p.shift, p.m, p.eta, p.W, p.v, p.sigma2, Xq[pick], tq[pick])
+    from oracle import design
+    R = design.task_covariance(p.W, p.v)
+    prior = np.array([R[t, t] * design.product_kernel(p.kind, Xq[i], Xq[i], p.eta) for i, t in zip(pick, tq[pick])])
+    assert np.all(np.abs(mean[pick] - mref) <= TOL * prior), np.max(np.abs(mean[pick] - mref) / prior)
+    assert np.all(np.abs(var[pick] - vref) <= TOL * prior), np.max(np.abs(var[pick] - vref) / prior)
