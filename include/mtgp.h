@@ -80,10 +80,14 @@ enum { MTGP_SOLVE_FP64 = 32 };
  *   gen_cols  DNET: number of generating-matrix columns, >= max m[t], <= 32. Ignored for LATTICE.
  *   shift     host, T x d words (caller task order): lattice shift Delta_t (added mod 2^32) or
  *             digital shift (XOR).
- *   precision MTGP_FP64, or MTGP_FP32_TRANSFORM (kernel columns and their transforms in FP32;
- *             per-frequency factorisations, log-determinants and y transforms stay FP64), optionally
- *             OR MTGP_NOISE_PER_TASK (per-task noise variances; such handles use the general kernels,
- *             not the fused equal-size ones, and are refused by the batch and no-allocation calls).
+ *   precision MTGP_FP64 (FP64 throughout except the eta-gradient contractions of d <= 16, which run in
+ *             double-float: they feed only d(NLL)/d(eta)), or MTGP_FP32_TRANSFORM (kernel columns and
+ *             their transforms in FP32; y transforms and log-determinant sums in FP64 or double-float;
+ *             per-frequency solves of equal-size digital nets in double-float unless MTGP_SOLVE_FP64 is
+ *             OR-ed in, every other solve FP64; the posterior of equal-size digital nets in
+ *             double-float), optionally OR MTGP_NOISE_PER_TASK (per-task noise variances; such handles
+ *             use the general kernels, not the fused equal-size ones, and are refused by the batch and
+ *             no-allocation calls).
  * Allocates the handle's device workspace on the current device.
  */
 int mtgp_create(mtgp_t** out, int kind, int d, int T, const int* m, const uint32_t* gen,
@@ -154,6 +158,9 @@ int mtgp_nll_grad_host(mtgp_t* h, const double* theta, int s, double* out, cudaS
  *   mean   nq doubles (required); var nq doubles or NULL (NULL skips the variance).
  * Variance: equal sizes through per-frequency T x T factors; unequal nested sizes through the tree
  * solver's factor, class by class (queries in batches of the rows that fit in 64 M doubles).
+ * FP32-transform digital nets with equal sizes, the order-2 DSI kernel, d <= 16 and n = 2^10 .. 2^18
+ * evaluate both in double-float arithmetic from exact kernel values (the mean of a variance call comes
+ * from the same kernel rows); the first call on a handle allocates its posterior scratch.
  */
 int mtgp_posterior(mtgp_t* h, const double* eta, const double* W, int s, const double* v,
                    const double* sigma2, int nq, const double* xq, const int* task,
